@@ -1,0 +1,322 @@
+/*
+ * phia_oracle.c -- plain, slow FP64 CPU oracle for PHIA (arXiv 2407.10205).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this file:
+ * only the tests, the package's smoke check and the benchmark's CPU-baseline
+ * leg load it.  It shares no code, header, table or constant with the CUDA
+ * library; the only thing both sides share is the seeded input generators,
+ * which hold none of the method's arithmetic.
+ *
+ * Every function follows one passage of the paper, named in its comment:
+ *   Eq. 2        Ising energy E(s) = -sum_{i<j} J_ij s_i s_j - sum_i h_i s_i
+ *   Eq. 6        local field (quasi-gradient) I_i = sum_j J_ij sgn(x_j) + h_i
+ *   Eq. 4 / A6   H(x,v) = beta E(sgn x) + x.x/2 + v.v/2
+ *   Eq. 5, 7, 8  dv/dt = beta * gamma (1 - tanh^2(gamma x)) * I - x
+ *   Eq. A7, A8   x <- x + eps v ;  v <- v - eps grad H(x_new)
+ *   Table 3      state 5: keep the best state seen so far
+ *   Sec. 2.1     momentum drawn at random at the start of a trajectory;
+ *                position prior g(x) is a standard normal (Eq. A3)
+ *
+ * Fixed point (Sec. 2.2, coefficients held as fixed-point constants):
+ * J_ij = k_ij * q and h_i = kh_i * q with q = 2^-f, int8 k and int32 kh.
+ * Fields and energies are exact int64 integers in units of q.
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3", SC'11) written from its published definition,
+ * and the Box-Muller transform (Box & Muller, 1958) in FP64.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------- Philox */
+
+/* One Philox4x32-10 block: 10 rounds of the 4x32 S-box with the Weyl key
+ * schedule, as defined by Salmon et al. (SC'11, Sec. 3 and Table 2). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t mul0 = 0xD2511F53u, mul1 = 0xCD9E8D57u;
+    const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)mul0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)mul1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += weyl0;
+        k1 += weyl1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniforms on 24 bits, so that the same value is exact in FP32 and FP64. */
+double orc_u01_open(uint32_t a) { return (double)((a >> 8) + 1u) * (1.0 / 16777216.0); } /* (0,1] */
+double orc_u01_half(uint32_t a) { return (double)(a >> 8) * (1.0 / 16777216.0); }        /* [0,1) */
+
+/* Box-Muller: one standard normal from two uniforms (cosine branch). */
+double orc_box_muller(uint32_t a, uint32_t b)
+{
+    double u1 = orc_u01_open(a), u2 = orc_u01_half(b);
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+/* The draw for spin j of replica r, draw index d (0 = initial state, t = momentum refresh
+ * before iteration t) of instance `inst`: counter (j, r, d, inst), key = 64-bit seed.
+ * Words 0,1 give the position sample (g(x) of Eq. A3), words 2,3 the momentum sample. */
+void orc_draw(uint64_t seed, uint32_t inst, uint32_t r, uint32_t j, uint32_t d,
+              double *nx, double *nv)
+{
+    uint32_t ctr[4] = {j, r, d, inst};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    if (nx) *nx = orc_box_muller(o[0], o[1]);
+    if (nv) *nv = orc_box_muller(o[2], o[3]);
+}
+
+/* ------------------------------------------------------------- instance */
+
+/* One Ising instance: either a dense k matrix (n*n, row-major) or CSR
+ * (row_ptr[n+1], col[nnz], val[nnz]); kh has n entries. */
+typedef struct {
+    int32_t n;
+    const int8_t *k;        /* dense, or NULL */
+    const int32_t *row_ptr; /* CSR, used when k == NULL */
+    const int32_t *col;
+    const int8_t *val;
+    const int32_t *kh;
+} orc_inst;
+
+/* Eq. 2, literally: E = -sum_{i<j} J_ij s_i s_j - sum_i h_i s_i (units of q). */
+int64_t orc_energy_exact(const orc_inst *P, const int8_t *s)
+{
+    int64_t e = 0;
+    int n = P->n;
+    if (P->k) {
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j)
+                e -= (int64_t)P->k[(int64_t)i * n + j] * s[i] * s[j];
+    } else {
+        for (int i = 0; i < n; ++i)
+            for (int32_t p = P->row_ptr[i]; p < P->row_ptr[i + 1]; ++p) {
+                int j = P->col[p];
+                if (j > i) e -= (int64_t)P->val[p] * s[i] * s[j];
+            }
+    }
+    for (int i = 0; i < n; ++i) e -= (int64_t)P->kh[i] * s[i];
+    return e;
+}
+
+/* Eq. 6: I_i = sum_j J_ij s_j + h_i (units of q). */
+void orc_field(const orc_inst *P, const int8_t *s, int64_t *I)
+{
+    int n = P->n;
+    for (int i = 0; i < n; ++i) {
+        int64_t acc = 0;
+        if (P->k) {
+            for (int j = 0; j < n; ++j) acc += (int64_t)P->k[(int64_t)i * n + j] * s[j];
+        } else {
+            for (int32_t p = P->row_ptr[i]; p < P->row_ptr[i + 1]; ++p)
+                acc += (int64_t)P->val[p] * s[P->col[p]];
+        }
+        I[i] = acc + P->kh[i];
+    }
+}
+
+/* E from the field: Eq. 2 and Eq. 6 give E = -1/2 sum_i s_i (I_i + h_i). */
+int64_t orc_energy_from_field(const orc_inst *P, const int8_t *s, const int64_t *I)
+{
+    int64_t twice = 0;
+    for (int i = 0; i < P->n; ++i) twice += (int64_t)s[i] * (I[i] + P->kh[i]);
+    return -twice / 2;
+}
+
+/* Exhaustive minimum of Eq. 2 over all 2^n states (n <= 24).  State index b maps
+ * to s_i = +1 when bit i of b is set, else -1.  Returns the minimum; writes the
+ * number of minimisers and the lowest-index minimiser. */
+int64_t orc_brute_force(const orc_inst *P, int64_t *n_min, int8_t *argmin)
+{
+    int n = P->n;
+    int8_t *s = (int8_t *)malloc((size_t)n);
+    int64_t best = INT64_MAX, count = 0;
+    uint64_t total = 1ull << n;
+    for (uint64_t b = 0; b < total; ++b) {
+        for (int i = 0; i < n; ++i) s[i] = ((b >> i) & 1u) ? 1 : -1;
+        int64_t e = orc_energy_exact(P, s);
+        if (e < best) {
+            best = e;
+            count = 1;
+            if (argmin) memcpy(argmin, s, (size_t)n);
+        } else if (e == best) {
+            ++count;
+        }
+    }
+    free(s);
+    if (n_min) *n_min = count;
+    return best;
+}
+
+/* ----------------------------------------------------------------- update */
+
+/* sgn with sgn(0) = +1 (the paper leaves sgn(0) open). */
+static int8_t orc_sgn(double x) { return x >= 0.0 ? 1 : -1; }
+
+/* One iteration of Eq. A7 with the gradient of Eq. A8 under the tanh surrogate
+ * (Eqs. 7-8):
+ *   x <- x + eps v
+ *   s  = sgn x
+ *   I  = J s + h                                  (Eq. 6)
+ *   dH/dx_i = -beta * gamma (1 - tanh^2(gamma x_i)) * q * I_i + x_i   (Eqs. 4, 5, 8)
+ *   v <- v - eps dH/dx
+ * Writes s and I (units of q); returns E(s) in units of q. */
+int64_t orc_step(const orc_inst *P, double q, double beta, double eps, double gamma,
+                 double *x, double *v, int8_t *s, int64_t *I)
+{
+    int n = P->n;
+    for (int i = 0; i < n; ++i) x[i] = x[i] + eps * v[i];
+    for (int i = 0; i < n; ++i) s[i] = orc_sgn(x[i]);
+    orc_field(P, s, I);
+    for (int i = 0; i < n; ++i) {
+        double t = tanh(gamma * x[i]);
+        double grad = -beta * gamma * (1.0 - t * t) * q * (double)I[i] + x[i];
+        v[i] = v[i] - eps * grad;
+    }
+    return orc_energy_from_field(P, s, I);
+}
+
+/* Annealing schedule (Table 3, state 4: the temperature is adjusted as the run
+ * proceeds).  beta goes linearly from beta0 at iteration 0 to beta1 at the last
+ * iteration; eps and gamma are constant; refresh > 0 redraws the momentum at the
+ * start of every iteration t with t % refresh == 0, t > 0 (a new HMC trajectory
+ * from the previous end point, Fig. 1b). */
+typedef struct {
+    double beta0, beta1, eps, gamma;
+    int64_t refresh;
+    int32_t has_target;
+    int32_t stop_at_target;
+    int64_t target;
+} orc_sched;
+
+double orc_beta_at(const orc_sched *S, int64_t t, int64_t T)
+{
+    if (T <= 1) return S->beta0;
+    return S->beta0 + (S->beta1 - S->beta0) * (double)t / (double)(T - 1);
+}
+
+/* Per-replica result. */
+typedef struct {
+    int64_t best_e;     /* lowest E seen (units of q) */
+    int64_t best_step;  /* first iteration at which it was seen */
+    int64_t hit_step;   /* first iteration with E <= target, or -1 */
+    int64_t steps_run;  /* iterations executed */
+} orc_replica_out;
+
+/* One replica of a PHIA run: initial draw (d = 0), then T iterations of
+ * orc_step with the momentum redrawn at trajectory starts; the best state is
+ * kept with strict improvement (Table 3, state 5).  x0/v0, when given, replace
+ * the initial draw.  x/v out (optional) receive the final state. */
+void orc_anneal_replica(const orc_inst *P, int32_t frac_bits, const orc_sched *S, int64_t T,
+                        uint64_t seed, uint32_t inst_id, uint32_t r,
+                        const double *x0, const double *v0,
+                        orc_replica_out *out, int8_t *best_s, double *x_out, double *v_out,
+                        int64_t *energy_trace)
+{
+    int n = P->n;
+    double q = ldexp(1.0, -frac_bits);
+    double *x = (double *)malloc(sizeof(double) * (size_t)n);
+    double *v = (double *)malloc(sizeof(double) * (size_t)n);
+    int8_t *s = (int8_t *)malloc((size_t)n);
+    int64_t *I = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    for (int j = 0; j < n; ++j) {
+        if (x0 && v0) {
+            x[j] = x0[j];
+            v[j] = v0[j];
+        } else {
+            orc_draw(seed, inst_id, r, (uint32_t)j, 0u, &x[j], &v[j]);
+        }
+    }
+    out->best_e = INT64_MAX;
+    out->best_step = -1;
+    out->hit_step = -1;
+    out->steps_run = 0;
+    for (int64_t t = 0; t < T; ++t) {
+        if (S->refresh > 0 && t > 0 && t % S->refresh == 0)
+            for (int j = 0; j < n; ++j) orc_draw(seed, inst_id, r, (uint32_t)j, (uint32_t)t, NULL, &v[j]);
+        double beta = orc_beta_at(S, t, T);
+        int64_t e = orc_step(P, q, beta, S->eps, S->gamma, x, v, s, I);
+        if (energy_trace) energy_trace[t] = e;
+        out->steps_run = t + 1;
+        int frozen = S->stop_at_target && out->hit_step >= 0;
+        if (!frozen && e < out->best_e) {
+            out->best_e = e;
+            out->best_step = t;
+            if (best_s) memcpy(best_s, s, (size_t)n);
+        }
+        if (S->has_target && out->hit_step < 0 && e <= S->target) {
+            out->hit_step = t;
+            if (S->stop_at_target) break;
+        }
+    }
+    if (x_out) memcpy(x_out, x, sizeof(double) * (size_t)n);
+    if (v_out) memcpy(v_out, v, sizeof(double) * (size_t)n);
+    free(x); free(v); free(s); free(I);
+}
+
+/* ------------------------------------------------------ threaded replicas */
+
+typedef struct {
+    const orc_inst *P;
+    int32_t frac_bits;
+    const orc_sched *S;
+    int64_t T;
+    uint64_t seed;
+    uint32_t inst_id;
+    int32_t R;
+    int32_t next;  /* protected by mu */
+    pthread_mutex_t mu;
+    orc_replica_out *outs;
+    int8_t *best_s;   /* R*n or NULL */
+    int32_t r0;       /* replica index offset */
+} orc_pool;
+
+static void *orc_worker(void *arg)
+{
+    orc_pool *pool = (orc_pool *)arg;
+    for (;;) {
+        pthread_mutex_lock(&pool->mu);
+        int r = pool->next++;
+        pthread_mutex_unlock(&pool->mu);
+        if (r >= pool->R) break;
+        int8_t *bs = pool->best_s ? pool->best_s + (int64_t)r * pool->P->n : NULL;
+        orc_anneal_replica(pool->P, pool->frac_bits, pool->S, pool->T, pool->seed, pool->inst_id,
+                           (uint32_t)(pool->r0 + r), NULL, NULL, &pool->outs[r], bs, NULL, NULL, NULL);
+    }
+    return NULL;
+}
+
+/* Replicas r0 .. r0+R-1 of one instance, spread over `threads` POSIX threads. */
+void orc_anneal_replicas(const orc_inst *P, int32_t frac_bits, const orc_sched *S, int64_t T,
+                         uint64_t seed, uint32_t inst_id, int32_t r0, int32_t R, int32_t threads,
+                         orc_replica_out *outs, int8_t *best_s)
+{
+    orc_pool pool;
+    pool.P = P; pool.frac_bits = frac_bits; pool.S = S; pool.T = T; pool.seed = seed;
+    pool.inst_id = inst_id; pool.R = R; pool.next = 0; pool.outs = outs; pool.best_s = best_s;
+    pool.r0 = r0;
+    pthread_mutex_init(&pool.mu, NULL);
+    if (threads < 1) threads = 1;
+    if (threads > R) threads = R;
+    pthread_t *tid = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)threads);
+    for (int t = 0; t < threads; ++t) pthread_create(&tid[t], NULL, orc_worker, &pool);
+    for (int t = 0; t < threads; ++t) pthread_join(tid[t], NULL);
+    free(tid);
+    pthread_mutex_destroy(&pool.mu);
+}

@@ -1,0 +1,297 @@
+"""Pins for the FP64 oracle against what the paper and mathematics fix (no GPU).
+
+Each test pins one function of oracle/ to something other than itself:
+published known-answer vectors, closed forms, a hand-worked example, exact
+discrete invariants, symmetries and exhaustive enumeration.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2407_10205_gb300 import instances as ins
+from conftest import GOLDEN, read_golden
+
+
+def _dense(k, kh, f=0):
+    return o.Instance(np.asarray(kh, dtype=np.int32), k=np.asarray(k, dtype=np.int8), frac_bits=f)
+
+
+# ------------------------------------------------------------------ Philox
+
+def test_philox_known_answers():
+    """Philox4x32-10 against the Random123 known-answer vectors (Salmon et al., SC'11)."""
+    n = 0
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            w = [int(t, 16) for t in line.split()]
+            assert o.philox4x32_10(w[0:4], w[4:6]) == w[6:10]
+            n += 1
+    assert n == 3
+
+
+def test_uniform_and_box_muller_closed_forms():
+    # u in (0,1] on 24 bits: all-ones maps to exactly 1, zero to 2^-24
+    assert o.u01_open(0xFFFFFFFF) == 1.0
+    assert o.u01_open(0) == 2.0 ** -24
+    assert o.u01_half(0) == 0.0
+    assert o.u01_half(0x80000000) == 0.5
+    # u1 = 1 -> radius 0
+    assert o.box_muller(0xFFFFFFFF, 12345) == 0.0
+    # u1 = 2^-24, u2 = 0 -> sqrt(-2 ln 2^-24) = sqrt(48 ln 2)
+    assert o.box_muller(0, 0) == pytest.approx(math.sqrt(48 * math.log(2)), rel=1e-15)
+    # u2 = 1/2 -> cos(pi) = -1
+    assert o.box_muller(0, 0x80000000) == pytest.approx(-math.sqrt(48 * math.log(2)), rel=1e-15)
+    # u2 = 1/4 -> cos(pi/2) = 0
+    assert abs(o.box_muller(0, 0x40000000)) < 1e-14
+
+
+def test_draws_are_standard_normal():
+    from scipy import stats
+    X, V = o.draw_grid(seed=7, inst=3, R=40, n=250, d=0)
+    for a in (X.ravel(), V.ravel()):
+        assert abs(a.mean()) < 0.03
+        assert abs(a.var() - 1) < 0.04
+        assert stats.kstest(a, "norm").pvalue > 1e-3
+    # position and momentum draws are different words of the same block
+    assert np.corrcoef(X.ravel(), V.ravel())[0, 1] < 0.05
+    # the counter separates replicas, spins, draw indices and instances
+    a = o.draw(7, 3, 0, 0, 0)
+    assert a != o.draw(7, 3, 1, 0, 0) and a != o.draw(7, 3, 0, 1, 0)
+    assert a != o.draw(7, 3, 0, 0, 1) and a != o.draw(7, 4, 0, 0, 0) and a != o.draw(8, 3, 0, 0, 0)
+
+
+# ------------------------------------------------------------------ energy
+
+def test_three_spin_energy_table():
+    g = read_golden("three_spin_step.txt")
+    k = np.array(g["J"].split(), dtype=np.int8).reshape(3, 3)
+    kh = np.array(g["h"].split(), dtype=np.int32)
+    P = _dense(k, kh)
+    for item in g["energies_by_state"].split():
+        st, e = item.split(":")
+        s = np.array([1 if c == "+" else -1 for c in st], dtype=np.int8)
+        assert o.energy_exact(P, s) == int(e)
+    emin, cnt, arg = o.brute_force(P)
+    assert emin == int(g["ground_energy"])
+    assert cnt == int(g["ground_count"])
+    assert list(arg) == [int(t) for t in g["ground_state"].split()]
+
+
+@pytest.mark.parametrize("n", [2, 5, 9, 12])
+def test_ferromagnet_closed_form(n):
+    """All J_ij = +1, h = 0: ground energy -n(n-1)/2, reached only by the two aligned states."""
+    k = np.ones((n, n), dtype=np.int8) - np.eye(n, dtype=np.int8)
+    P = _dense(k, np.zeros(n))
+    emin, cnt, _ = o.brute_force(P)
+    assert emin == -n * (n - 1) // 2 and cnt == 2
+    assert o.energy_exact(P, np.ones(n)) == -n * (n - 1) // 2
+
+
+def test_antiferromagnetic_triangle():
+    """J = -1 on a triangle: frustrated, ground energy -1 with six ground states."""
+    k = -(np.ones((3, 3), dtype=np.int8) - np.eye(3, dtype=np.int8))
+    emin, cnt, _ = o.brute_force(_dense(k, np.zeros(3)))
+    assert (emin, cnt) == (-1, 6)
+
+
+@pytest.mark.parametrize("n", [4, 10, 15])
+def test_open_chain(n):
+    k = np.zeros((n, n), dtype=np.int8)
+    for i in range(n - 1):
+        k[i, i + 1] = k[i + 1, i] = 1
+    emin, cnt, _ = o.brute_force(_dense(k, np.zeros(n)))
+    assert (emin, cnt) == (-(n - 1), 2)
+
+
+def test_independent_spins():
+    """J = 0: the ground state is s = sgn h with E = -sum |h|, unique when no h is 0."""
+    g = np.random.default_rng(1)
+    kh = g.integers(1, 50, size=11) * np.where(g.random(11) < 0.5, -1, 1)
+    P = _dense(np.zeros((11, 11)), kh)
+    emin, cnt, arg = o.brute_force(P)
+    assert emin == -np.abs(kh).sum() and cnt == 1
+    assert np.array_equal(arg, np.sign(kh))
+
+
+def test_field_is_minus_energy_gradient():
+    """Eq. 6 as a discrete derivative of Eq. 2: flipping spin k changes E by 2 s_k I_k."""
+    d = ins.dense_int(23, 9, 20, seed=5)
+    P = _dense(d.k, d.kh)
+    s = ins.random_spins(1, 23, seed=6)[0]
+    I = o.field(P, s)
+    e0 = o.energy_exact(P, s)
+    for kidx in range(23):
+        t = s.copy(); t[kidx] = -t[kidx]
+        assert o.energy_exact(P, t) - e0 == 2 * int(s[kidx]) * int(I[kidx])
+
+
+def test_energy_identity_and_csr_agree():
+    """E = -1/2 sum s (I + h) equals Eq. 2; the CSR and dense forms agree."""
+    c = ins.erdos_renyi(120, 0.08, 127, 31, 4, seed=2)
+    dd = c.to_dense()
+    Pc = o.Instance(c.kh, row_ptr=c.row_ptr, col=c.col, val=c.val, frac_bits=4)
+    Pd = o.Instance(dd.kh, k=dd.k, frac_bits=4)
+    S = ins.random_spins(20, 120, seed=3)
+    for s in S:
+        Ic, Id = o.field(Pc, s), o.field(Pd, s)
+        assert np.array_equal(Ic, Id)
+        e = o.energy_exact(Pd, s)
+        assert o.energy_exact(Pc, s) == e
+        assert o.energy_from_field(Pd, s, Id) == e
+
+
+def test_flip_symmetry_without_field():
+    d = ins.sk_pm1(40, seed=4)
+    P = _dense(d.k, d.kh)
+    for s in ins.random_spins(10, 40, seed=5):
+        assert o.energy_exact(P, s) == o.energy_exact(P, -s)
+
+
+# ------------------------------------------------------------------ update
+
+def test_three_spin_step_matches_hand_derivation():
+    g = read_golden("three_spin_step.txt")
+    k = np.array(g["J"].split(), dtype=np.int8).reshape(3, 3)
+    kh = np.array(g["h"].split(), dtype=np.int32)
+    P = _dense(k, kh)
+    f = lambda key: np.array(g[key].split(), dtype=np.float64)
+    x, v, s, I, e = o.step(P, f("x"), f("v"), float(g["beta"]), float(g["eps"]), float(g["gamma"]))
+    assert np.allclose(x, f("x_new"), rtol=0, atol=1e-15)
+    assert list(s) == [int(t) for t in g["s"].split()]
+    assert list(I) == [int(t) for t in g["I"].split()]
+    assert e == int(g["E"])
+    assert np.allclose(v, f("v_new"), rtol=1e-14, atol=0)
+
+
+def test_beta_zero_discrete_invariant():
+    """With beta = 0 the update is symplectic Euler on a unit oscillator per spin;
+    x^2 + v^2 + eps x v is then exactly conserved (up to FP64 rounding)."""
+    d = ins.dense_int(8, 5, 5, seed=9)
+    P = _dense(d.k, d.kh)
+    g = np.random.default_rng(0)
+    x, v, eps = g.standard_normal(8), g.standard_normal(8), 0.3
+    inv0 = x * x + v * v + eps * x * v
+    for _ in range(10000):
+        x, v, *_ = o.step(P, x, v, 0.0, eps, 2.0)
+    assert np.allclose(x * x + v * v + eps * x * v, inv0, rtol=1e-11)
+
+
+def test_mirror_symmetry_without_field():
+    """h = 0: the dynamics are odd, (x, v) -> (-x, -v) maps a step onto its mirror."""
+    d = ins.sk_pm1(30, seed=10)
+    P = _dense(d.k, d.kh)
+    x, v = ins.random_state(1, 30, seed=11, min_abs=0.05)
+    x = x[0].astype(np.float64); v = v[0].astype(np.float64) * 0.1
+    a = o.step(P, x, v, 0.7, 0.1, 3.0)
+    b = o.step(P, -x, -v, 0.7, 0.1, 3.0)
+    assert np.array_equal(a[0], -b[0]) and np.array_equal(a[1], -b[1])
+    assert np.array_equal(a[2], -b[2]) and a[4] == b[4]
+
+
+def test_fixed_point_scale_invariance():
+    """J = k 2^-f: doubling k and h while adding one fractional bit leaves the step unchanged."""
+    d = ins.dense_int(25, 30, 30, seed=12)
+    P1 = _dense(d.k, d.kh, f=3)
+    P2 = _dense(d.k.astype(np.int16) * 2, d.kh * 2, f=4)
+    x, v = ins.random_state(1, 25, seed=13, min_abs=0.05)
+    x = x[0].astype(np.float64); v = v[0].astype(np.float64)
+    a = o.step(P1, x, v, 0.4, 0.1, 2.0)
+    b = o.step(P2, x, v, 0.4, 0.1, 2.0)
+    assert np.array_equal(a[0], b[0]) and np.allclose(a[1], b[1], rtol=1e-15)
+    assert np.array_equal(a[2], b[2]) and np.array_equal(2 * a[3], b[3]) and 2 * a[4] == b[4]
+
+
+def test_permutation_equivariance():
+    d = ins.dense_int(17, 7, 7, seed=14)
+    perm = np.random.default_rng(15).permutation(17)
+    P = _dense(d.k, d.kh)
+    Pp = _dense(d.k[np.ix_(perm, perm)], d.kh[perm])
+    x, v = ins.random_state(1, 17, seed=16, min_abs=0.05)
+    x = x[0].astype(np.float64); v = v[0].astype(np.float64)
+    a = o.step(P, x, v, 0.3, 0.1, 2.0)
+    b = o.step(Pp, x[perm], v[perm], 0.3, 0.1, 2.0)
+    assert np.array_equal(a[0][perm], b[0]) and np.array_equal(a[1][perm], b[1])
+    assert np.array_equal(a[3][perm], b[3]) and a[4] == b[4]
+
+
+def test_sign_of_zero_is_plus():
+    P = _dense(np.zeros((2, 2)), [0, 0])
+    _, _, s, _, _ = o.step(P, [0.0, -0.0], [0.0, 0.0], 1.0, 0.1, 1.0)
+    assert list(s) == [1, 1]
+
+
+# ------------------------------------------------------------------ schedule and runs
+
+def test_linear_beta_schedule():
+    assert o.beta_at(0, 100, 0.1, 2.0) == 0.1
+    assert o.beta_at(99, 100, 0.1, 2.0) == 2.0
+    assert o.beta_at(33, 67, 0.0, 1.0) == pytest.approx(0.5)
+    assert o.beta_at(0, 1, 0.3, 9.0) == 0.3
+
+
+def test_run_is_composition_of_draws_and_steps():
+    """A run is: draw (x, v) with d = 0, then steps, with the momentum redrawn (d = t)
+    at every t % refresh == 0, t > 0."""
+    d = ins.dense_int(12, 4, 4, seed=20)
+    P = _dense(d.k, d.kh)
+    T, seed, inst, r, refresh = 7, 99, 5, 3, 3
+    res = o.anneal_replica(P, T, seed, inst, r, 0.1, 0.9, 0.2, 2.0, refresh=refresh, trace=True)
+    x = np.array([o.draw(seed, inst, r, j, 0)[0] for j in range(12)])
+    v = np.array([o.draw(seed, inst, r, j, 0)[1] for j in range(12)])
+    es = []
+    for t in range(T):
+        if t > 0 and t % refresh == 0:
+            v = np.array([o.draw(seed, inst, r, j, t)[1] for j in range(12)])
+        x, v, s, I, e = o.step(P, x, v, o.beta_at(t, T, 0.1, 0.9), 0.2, 2.0)
+        es.append(e)
+    assert list(res["trace"]) == es
+    assert np.array_equal(res["x"], x) and np.array_equal(res["v"], v)
+
+
+def test_best_state_is_consistent():
+    d = ins.dense_int(30, 7, 7, seed=21)
+    P = _dense(d.k, d.kh)
+    for r in range(4):
+        res = o.anneal_replica(P, 300, 5, 0, r, 0.01, 1.0, 0.1, 2.0, refresh=20, trace=True)
+        tr = res["trace"]
+        assert res["best_e"] == tr.min()
+        assert res["best_step"] == int(np.argmin(tr))      # first occurrence: strict improvement
+        assert o.energy_exact(P, res["best_s"]) == res["best_e"]
+
+
+def test_small_sk_reaches_brute_force_ground_state():
+    """N = 16 SK (J in {-1,+1}, h = 0, seed 0): the best energy found never goes below
+    the exhaustive minimum, and the defaults reach it in most runs."""
+    d = ins.sk_pm1(16, 0)
+    P = _dense(d.k, d.kh)
+    emin, cnt, _ = o.brute_force(P)
+    res = o.anneal(P, 64, 1000, 1, 0, 0.05, 2.0, 0.2, 2.0)
+    assert (res["best_e"] >= emin).all()
+    assert np.mean(res["best_e"] == emin) > 0.8
+    for r in range(64):
+        assert o.energy_exact(P, res["best_s"][r]) == res["best_e"][r]
+
+
+def test_stop_at_target_freezes_the_result():
+    d = ins.sk_pm1(16, 0)
+    P = _dense(d.k, d.kh)
+    emin, _, _ = o.brute_force(P)
+    full = o.anneal(P, 32, 1000, 1, 0, 0.05, 2.0, 0.2, 2.0, target=emin)
+    stop = o.anneal(P, 32, 1000, 1, 0, 0.05, 2.0, 0.2, 2.0, target=emin, stop_at_target=True)
+    hit = full["hit_step"] >= 0
+    assert np.array_equal(full["hit_step"], stop["hit_step"])
+    assert np.array_equal(stop["steps_run"][hit], stop["hit_step"][hit] + 1)
+    assert (stop["best_e"][hit] <= emin).all()
+
+
+def test_tts_definition():
+    """Eq. 9 with the brackets read as grouping."""
+    assert o.tts(2.0, 0.9) == pytest.approx(4.0)
+    assert o.tts(2.0, 0.99) == 2.0 and o.tts(2.0, 1.0) == 2.0
+    assert o.tts(1.0, 0.5) == pytest.approx(math.log(0.01) / math.log(0.5))
+    assert o.tts(1.0, 0.0) == math.inf
