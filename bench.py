@@ -1,0 +1,291 @@
+"""Benchmark of the PHIA hot path on GB300.
+
+Workload (one bench step = one whole PHIA run, i.e. every row of the hot path over one
+batch): N = 200 dense instance, k_ij and kh_i uniform integers in [-7, 7] (seed 1),
+1024 replicas x 2000 iterations, beta linear 0.01 -> 0.1, eps 0.1, gamma 2, momentum
+refreshed every 50 iterations.  Metric: spin updates per second = replicas * N *
+iterations / time.
+
+  value        device time of phia_anneal with the instance resident in HBM (CUDA events
+               on the handle's stream), whole job over all ranks (weak scaling: every
+               rank anneals its own replicas, no collective on the data path).
+  e2e          same metric through the public C ABI from host buffers: phia_create
+               (host -> device copy of J, h) + phia_anneal + phia_best (device -> host
+               copy of the result) per step, wall clock.
+  roofline     dominant kernel, see the roofline block below.
+  cpu_baseline the FP64 oracle on the host cores, bounded sample (rank 0, N = 1 only).
+  comparator   the plain FP32 per-instance GPU path on the same instance and seeds.
+
+L2 is flushed (256 MB write) between timed steps.  `--impl reference` times the oracle
+(this method has no reference code; the oracle is the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(N=200, kmax=7, hmax=7, seed=1, replicas=1024, iterations=2000,
+                beta0=0.01, beta1=0.1, eps=0.1, gamma=2.0, refresh=50, run_seed=12345)
+WORKLOAD_NAME = ("N=200 dense, k and kh uniform int [-7,7]; 1024 replicas x 2000 iterations, "
+                 "linear beta 0.01->0.1")
+METRIC = "spin-updates/s"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _instance():
+    from paper_2407_10205_gb300 import instances as ins
+    w = WORKLOAD
+    return ins.dense_int(w["N"], w["kmax"], w["hmax"], w["seed"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [t.strip() for t in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx = float(f[2])
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
+        loaded = [s for s in sm if mx is None or s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(sample_replicas=128):
+    """The FP64 oracle, as it stands, on the host cores: `sample_replicas` replicas of the
+    bench workload for the full 2000 iterations."""
+    import oracle
+    w = WORKLOAD
+    d = _instance()
+    P = oracle.Instance(d.kh, k=d.k)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.anneal(P, sample_replicas, w["iterations"], w["run_seed"], 0, w["beta0"], w["beta1"], w["eps"],
+                  w["gamma"], refresh=w["refresh"], threads=cores, want_spins=False)
+    dt = time.perf_counter() - t0
+    su = sample_replicas * w["N"] * w["iterations"]
+    return {"value": su / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{sample_replicas} of the 1024 replicas x 2000 iterations ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    per_step = []
+    cb = None
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(sample_replicas=32)
+        if k >= args.warmup:
+            per_step.append(r["value"])
+            cb = r
+    val = statistics.median(per_step)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 32 * WORKLOAD["N"] * WORKLOAD["iterations"] / val * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "sample_replicas_per_step": 32},
+            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": val,
+                             "unit": METRIC},
+            "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return m, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2407_10205_gb300 import phia
+    phia.load()
+    w = WORKLOAD
+    d = _instance()
+    N, R, T = w["N"], w["replicas"], w["iterations"]
+    sched = phia.schedule(w["beta0"], w["beta1"], w["eps"], w["gamma"], refresh=w["refresh"])
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    seed = w["run_seed"] + rank * 1_000_003     # each rank anneals its own replicas
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, stream=stream.cuda_stream) as A:
+        for _ in range(args.warmup):
+            phia.anneal(A.h, sched, R, T, seed)
+            phia.sync(A.h)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        launches = 0
+        barrier()
+        with ClockSampler(local) as cs:
+            t_wall = time.perf_counter()
+            for k in range(args.steps):
+                flush.fill_(float(k))                     # L2 flush between timed steps
+                torch.cuda.current_stream().synchronize()
+                ev[k][0].record(stream)
+                phia.anneal(A.h, sched, R, T, seed)
+                ev[k][1].record(stream)
+                launches += 1
+            barrier()
+            t_wall = time.perf_counter() - t_wall
+        st = phia.stats_get(A.h)
+        launches *= max(st.kernel_launches, 1)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        kernel_ms = float(st.device_ms)
+        best_e, _ = phia.best(A.h, N)
+
+    ms_per_step = sum(ms) / len(ms)
+    if world > 1:
+        t = torch.tensor([ms_per_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    su_step = R * N * T
+    value = world * su_step / (ms_per_step * 1e-3)
+
+    # e2e: public C ABI from host buffers, host<->device copies inside the timed region
+    e2e_ms = []
+    for k in range(max(2, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, stream=stream.cuda_stream) as B:
+            phia.anneal(B.h, sched, R, T, seed)
+            e, spins = phia.best(B.h, N)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = statistics.median(e2e_ms)
+    h2d = N * N + 4 * N
+    d2h = 3 * 8 * R + 4 + 4 * ((N + 31) // 32) + 8
+
+    # comparator: the plain FP32 per-instance GPU path, same instance and seeds
+    with phia.Annealer(d.k, d.kh, path=phia.PATH_FP32, stream=stream.cuda_stream) as C:
+        phia.anneal(C.h, sched, R, T, seed)
+        phia.sync(C.h)
+        cmp_ms = []
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            phia.anneal(C.h, sched, R, T, seed)
+            e1.record(stream)
+            stream.synchronize()
+            cmp_ms.append(e0.elapsed_time(e1))
+        cmp_best, _ = phia.best(C.h, N)
+    cmp_value = su_step / (min(cmp_ms) * 1e-3)
+
+    if rank != 0:
+        return 0
+    peaks, src = _peaks()
+    # Dominant kernel: tc_small_kernel (one launch per run).  Algorithmic work of the
+    # field is 2 N^2 multiply-adds per replica-iteration on the tensor pipe; peak for e4m3
+    # operands is the measured bf16 dense peak x 2 (nominal fp8 : bf16 ratio).
+    flops = 2.0 * N * N * R * T
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    peak = 2.0 * float(peaks["bf16_tflops"])
+    clocks = cs.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "N": N, "replicas": R, "iterations": T, "path": "tc",
+                   "field_operand": "e4m3 (exact for |k| <= 16), fp32 accumulation of integer products",
+                   "state": "fp32 x, v", "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas sharded over {world} GPU(s), no collective"},
+        "e2e": {"value": su_step / (e2e_step * 1e-3), "unit": METRIC, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "tc_small_kernel", "peak_source": f"{src} bf16 x 2 (e4m3)"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "comparator": {"path": "fp32 per-instance, one launch per step", "value": cmp_value, "unit": METRIC,
+                       "ms_per_step": min(cmp_ms), "best_energy_k": int(cmp_best)},
+        "best_energy_k": int(best_e),
+        "wall_s_timed": t_wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

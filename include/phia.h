@@ -1,0 +1,188 @@
+/*
+ * phia.h -- C ABI of the GB300 PHIA library (Parallel Hamiltonian Monte Carlo
+ * Ising Annealer, arXiv 2407.10205).
+ *
+ * Problem (Sec. 2.1, Eq. 2): minimise E(s) = -sum_{i<j} J_ij s_i s_j - sum_i h_i s_i
+ * over s in {-1,+1}^N.  Couplings are fixed point (Sec. 2.2: J and h held as
+ * fixed-point constants): J_ij = k_ij * 2^-f with int8 k (symmetric, zero
+ * diagonal) and h_i = kh_i * 2^-f with int32 kh.  All energies and fields cross
+ * this boundary as exact integers in units of q = 2^-f.
+ *
+ * Method (Eqs. 4-8, A7-A8): every replica carries a continuous position x and
+ * momentum v (FP32 on the device) and iterates
+ *     x <- x + eps v ;  s = sgn x (sgn 0 = +1) ;  I = J s + h           (Eq. 6)
+ *     v <- v + eps (beta_t gamma (1 - tanh^2(gamma x)) I - x)           (Eqs. 5, 8, A7)
+ * with beta_t linear from beta0 to beta1 over the run (Table 3, state 4), the
+ * momentum redrawn at trajectory starts (Sec. 2.1, Fig. 1b) and the lowest-
+ * energy state kept per replica (Table 3, state 5).
+ *
+ * Random numbers: Philox4x32-10 keyed by the 64-bit seed, counter
+ * (spin j, replica r, draw d, instance id); words 0-1 give the initial position,
+ * words 2-3 the momentum, each through the Box-Muller cosine branch on 24-bit
+ * uniforms.  d = 0 is the initial draw, d = t the refresh before iteration t.
+ *
+ * Conventions for every call:
+ *  - Return value: PHIA_OK (0) or a negative PHIA_E* code; no exception or
+ *    abort crosses this boundary.  phia_last_error() returns a thread-local
+ *    message for the last failing call of the calling thread.
+ *  - "host" pointers are ordinary CPU memory owned by the caller; the library
+ *    copies from / to them and keeps no reference after the call returns.
+ *    "device" pointers are CUDA global memory on the handle's device, owned by
+ *    the caller, and must stay valid until the work enqueued on the handle's
+ *    stream has finished (phia_sync).
+ *  - A handle owns all device memory it allocates; phia_destroy frees it.
+ *    Handles are not thread-safe: one thread at a time per handle.
+ *  - Work is enqueued on the stream given in phia_opts (NULL = the CUDA legacy
+ *    default stream).  Calls that return results to host memory synchronise
+ *    that stream.
+ */
+#ifndef PHIA_H
+#define PHIA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PHIA_OK 0
+#define PHIA_EINVAL (-1)   /* bad argument: N < 1, asymmetric J, nonzero diagonal, bad CSR */
+#define PHIA_ERANGE (-2)   /* a value out of range for the chosen path or operand format */
+#define PHIA_ENOMEM (-3)   /* device or host allocation failed */
+#define PHIA_ETIMEOUT (-4) /* a bounded device-side wait expired; the context stays usable */
+#define PHIA_ECUDA (-5)    /* a CUDA runtime call failed */
+#define PHIA_ESTATE (-6)   /* call out of order (e.g. phia_best before any run) */
+#define PHIA_ENOTSUP (-7)  /* the requested path does not handle this instance */
+
+/* Field path (how I = J s + h is computed; every path gives the same exact integers). */
+#define PHIA_PATH_AUTO 0   /* dense -> PHIA_PATH_TC, CSR -> PHIA_PATH_CSR */
+#define PHIA_PATH_TC 1     /* tcgen05 tensor-core MMA, FP32 accumulation of integer products */
+#define PHIA_PATH_FP32 2   /* plain FP32 CUDA-core mat-vec, one launch per step (comparator) */
+#define PHIA_PATH_CSR 3    /* warp-per-row CSR gather over bit-packed spins */
+
+/* Tensor-core operand encoding of the int8 couplings (exact re-encodings of k). */
+#define PHIA_OP_AUTO 0     /* E4M3 when every |k| <= 16, else BF16 */
+#define PHIA_OP_E4M3 1     /* FP8 e4m3, exact for |k| <= 16 */
+#define PHIA_OP_BF16 2     /* BF16, exact for every int8 k */
+
+typedef struct phia_opts {
+    int32_t path;          /* PHIA_PATH_* */
+    int32_t operand;       /* PHIA_OP_* (tensor-core path only) */
+    int32_t device;        /* CUDA device ordinal */
+    uint32_t instance_id;  /* fourth Philox counter word: separates instances sharing a seed */
+    void *stream;          /* cudaStream_t to enqueue on; NULL = legacy default stream */
+} phia_opts;
+
+/* Annealing schedule.  No values are given in the paper; every field is explicit. */
+typedef struct phia_schedule {
+    float beta0;           /* inverse temperature at iteration 0 */
+    float beta1;           /* inverse temperature at the last iteration (linear in between) */
+    float eps;             /* step size of Eq. A7 */
+    float gamma;           /* tanh sharpness of Eqs. 7-8 */
+    int32_t refresh;       /* momentum redrawn before iteration t when t % refresh == 0, t > 0;
+                              0 = drawn only at the start */
+    int32_t has_target;    /* 1: record the first iteration with E <= target_k */
+    int32_t stop_at_target;/* 1: freeze a replica's result at its first hit and end the run once
+                              every replica has passed the earliest hit */
+    int32_t reserved;      /* must be 0 */
+    int64_t target_k;      /* target energy in units of q */
+} phia_schedule;
+
+typedef struct phia_stats {
+    int64_t replicas;      /* replicas of the last run */
+    int64_t steps;         /* iterations requested (field evaluations per replica) */
+    int64_t spin_updates;  /* replicas * N * iterations actually run */
+    int64_t best_energy_k; /* lowest energy over replicas (units of q) */
+    int64_t best_replica;  /* replica holding it (ties: earliest step, then lowest index) */
+    int64_t best_step;     /* iteration at which it was first seen */
+    int64_t hit_step;      /* earliest iteration with E <= target over replicas, or -1 */
+    int64_t hit_replica;   /* lowest replica index hitting at hit_step, or -1 */
+    float device_ms;       /* device time of the last run, CUDA events on the handle's stream */
+    int32_t path;          /* path actually used (PHIA_PATH_TC / _FP32 / _CSR) */
+    int32_t operand;       /* operand actually used (PHIA_OP_E4M3 / _BF16), 0 for other paths */
+    int32_t kernel_launches; /* kernels launched by the last run */
+    int32_t reserved;
+} phia_stats;
+
+typedef struct phia_s phia_t;
+
+/* Create a dense instance (Eq. 2).  J_k: host, N*N int8 row-major, must be
+ * symmetric with a zero diagonal (Eq. 2 sums i<j; a diagonal term has no place in
+ * Eq. 6) -> PHIA_EINVAL otherwise.  h_k: host, N int32 with |h_k| < 2^24.
+ * frac_bits f in [0, 30].  opts may be NULL (all defaults = 0).  Copies J and h to
+ * the device; the caller keeps its buffers. */
+int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N,
+                int32_t frac_bits, const phia_opts *opts);
+
+/* Create a sparse instance in CSR form (host arrays): row_ptr[N+1], col[nnz]
+ * (0 <= col < N, no self loops), val_k[nnz] int8; the pattern and values must be
+ * symmetric.  Stored zeros are allowed. */
+int phia_create_csr(phia_t **out, const int32_t *row_ptr, const int32_t *col,
+                    const int8_t *val_k, const int32_t *h_k, int32_t N, int32_t frac_bits,
+                    const phia_opts *opts);
+
+/* Run `replicas` independent replicas for `steps` iterations (Eqs. A7-A8) from the
+ * Philox initial draw (positions ~ g(x) of Eq. A3, momenta ~ N(0,1)), keeping the
+ * best state per replica.  Enqueued on the handle's stream; returns before the
+ * device finishes.  replicas >= 1, steps >= 1. */
+int phia_anneal(phia_t *p, const phia_schedule *sched, int32_t replicas, int64_t steps,
+                uint64_t seed);
+
+/* Lowest energy found by the last run (ties: earliest step, then lowest replica)
+ * and its spins.  energy_k: host int64 (units of q).  spins: host, N int8 in
+ * {-1,+1}, may be NULL.  Synchronises the stream.  PHIA_ETIMEOUT if a bounded
+ * device wait expired during the run. */
+int phia_best(phia_t *p, int64_t *energy_k, int8_t *spins);
+
+/* Statistics of the last run (synchronises the stream). */
+int phia_stats_get(phia_t *p, phia_stats *out);
+
+/* Per-replica results of the last run, host arrays of `replicas` entries (any may
+ * be NULL): best energy (units of q), iteration of the best, first iteration with
+ * E <= target (-1 if none), and the best spins bit-packed: replicas x ceil(N/32)
+ * uint32 words, bit (i % 32) of word (i / 32) set when s_i = +1. */
+int phia_replica_results(phia_t *p, int32_t replicas, int64_t *best_energy_k,
+                         int64_t *best_step, int64_t *hit_step, uint32_t *best_bits);
+
+/* Resumable form of phia_anneal.  Runs iterations t0 .. t0+steps-1 of a run of
+ * total_steps iterations (beta_t and the refresh draws depend on the absolute t)
+ * from the state in x, v (device, replicas x N float32 row-major, updated in place
+ * to the state after the last iteration).  reset_best = 1 starts the per-replica
+ * best/target record afresh; 0 continues the record of the previous call with the
+ * same replica count.  Running [0,a) then [a,b) gives bit-identical states and
+ * records to running [0,b) at once. */
+int phia_run(phia_t *p, const phia_schedule *sched, int32_t replicas, int64_t t0,
+             int64_t steps, int64_t total_steps, uint64_t seed, float *x, float *v,
+             int32_t reset_best);
+
+/* The initial draw of phia_anneal written to device arrays x, v (replicas x N). */
+int phia_init_state(phia_t *p, int32_t replicas, uint64_t seed, float *x, float *v);
+
+/* Field (Eq. 6) and energy (Eq. 2, through E = -1/2 sum s (I + h)) of given spins on
+ * the handle's field path.  spins: device, replicas x N int8 in {-1,+1};
+ * field_k: device, replicas x N int32 (units of q); energy_k: device, replicas
+ * int64 (units of q).  Either output may be NULL. */
+int phia_field(phia_t *p, const int8_t *spins, int32_t replicas, int32_t *field_k,
+               int64_t *energy_k);
+
+/* The library's device Philox draws, for testing: for replica r < replicas,
+ * spin j < N: raw[(r*N + j)*4 + w] = Philox4x32-10 word w of counter
+ * (j, r, d, instance_id) and key (seed lo, seed hi); x[r*N+j], v[r*N+j] the two
+ * Box-Muller normals.  All device pointers (any may be NULL); stream may be NULL. */
+int phia_philox_draws(uint64_t seed, uint32_t instance_id, uint32_t d, int32_t replicas,
+                      int32_t N, uint32_t *raw, float *x, float *v, void *stream);
+
+/* Wait for all work enqueued on the handle's stream. */
+int phia_sync(phia_t *p);
+
+/* Free every resource of the handle (NULL is allowed). */
+void phia_destroy(phia_t *p);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *phia_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHIA_H */

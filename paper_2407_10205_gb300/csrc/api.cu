@@ -1,0 +1,470 @@
+// api.cu -- the C ABI of include/phia.h and the host runtime behind it: instance
+// validation and upload, path and operand selection, per-replica state, run
+// launch, records and results.
+#include <algorithm>
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/phia.h"
+#include "phia_internal.h"
+
+using namespace phia;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                                \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return fail(PHIA_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+__global__ void reset_records_kernel(int R, int W, int64_t *best_e, int64_t *best_step, int64_t *hit,
+                                     uint32_t *bits) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < R) {
+        best_e[idx] = LLONG_MAX;
+        best_step[idx] = -1;
+        hit[idx] = -1;
+    }
+    if (idx < (int64_t)R * W) bits[idx] = 0u;
+}
+
+}  // namespace
+
+struct phia_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int path = PHIA_PATH_TC;
+    int op = 0;
+    uint32_t inst = 0;
+    int N = 0, frac_bits = 0, W = 0;
+    bool csr = false;
+    int64_t nnz = 0;
+    int max_abs_k = 0;
+    // instance on the device
+    int8_t *d_Jk = nullptr;
+    float *d_Jf = nullptr;
+    int32_t *d_hk = nullptr;
+    int32_t *d_rowptr = nullptr, *d_col = nullptr;
+    int8_t *d_val = nullptr;
+    // per-replica state
+    int R_cap = 0, R_last = 0;
+    float *d_x = nullptr, *d_v = nullptr;
+    int8_t *d_s0 = nullptr, *d_s1 = nullptr;
+    int64_t *d_eacc = nullptr;
+    int64_t *d_best_e = nullptr, *d_best_step = nullptr, *d_hit = nullptr;
+    uint32_t *d_bits = nullptr;
+    // run counters
+    unsigned long long *d_min_hit = nullptr, *d_iters = nullptr;
+    int32_t *d_err = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool ran = false;
+    int64_t last_steps = 0;
+    int last_launches = 0;
+    int last_stop = 0;
+};
+
+namespace {
+
+void free_replicas(phia_t *p) {
+    cudaFree(p->d_x); cudaFree(p->d_v); cudaFree(p->d_s0); cudaFree(p->d_s1); cudaFree(p->d_eacc);
+    cudaFree(p->d_best_e); cudaFree(p->d_best_step); cudaFree(p->d_hit); cudaFree(p->d_bits);
+    p->d_x = p->d_v = nullptr; p->d_s0 = p->d_s1 = nullptr; p->d_eacc = nullptr;
+    p->d_best_e = p->d_best_step = p->d_hit = nullptr; p->d_bits = nullptr;
+    p->R_cap = 0;
+}
+
+int ensure_replicas(phia_t *p, int R) {
+    if (R <= p->R_cap) return PHIA_OK;
+    CU(cudaStreamSynchronize(p->stream));
+    free_replicas(p);
+    const size_t RN = (size_t)R * p->N;
+    bool ok = true;
+    auto al = [&](void **ptr, size_t bytes) {
+        if (ok && cudaMalloc(ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) ok = false;
+    };
+    if (p->path == PHIA_PATH_FP32) {
+        al((void **)&p->d_x, RN * 4); al((void **)&p->d_v, RN * 4);
+        al((void **)&p->d_s0, RN); al((void **)&p->d_s1, RN);
+    }
+    al((void **)&p->d_eacc, (size_t)R * 8);
+    al((void **)&p->d_best_e, (size_t)R * 8);
+    al((void **)&p->d_best_step, (size_t)R * 8);
+    al((void **)&p->d_hit, (size_t)R * 8);
+    al((void **)&p->d_bits, (size_t)R * p->W * 4);
+    if (!ok) {
+        cudaGetLastError();
+        free_replicas(p);
+        return fail(PHIA_ENOMEM, "device allocation for %d replicas failed", R);
+    }
+    CU(cudaMemsetAsync(p->d_eacc, 0, (size_t)R * 8, p->stream));
+    p->R_cap = R;
+    return PHIA_OK;
+}
+
+int reset_records(phia_t *p, int R) {
+    const int64_t n = std::max<int64_t>(R, (int64_t)R * p->W);
+    reset_records_kernel<<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(R, p->W, p->d_best_e, p->d_best_step,
+                                                                             p->d_hit, p->d_bits);
+    CU(cudaGetLastError());
+    return PHIA_OK;
+}
+
+int check_sched(const phia_schedule *s) {
+    if (!s) return fail(PHIA_EINVAL, "schedule is NULL");
+    if (!(s->eps > 0.0f) || !(s->gamma > 0.0f)) return fail(PHIA_EINVAL, "eps and gamma must be > 0");
+    if (!(s->beta0 >= 0.0f) || !(s->beta1 >= 0.0f)) return fail(PHIA_EINVAL, "beta0 and beta1 must be >= 0");
+    if (s->refresh < 0) return fail(PHIA_EINVAL, "refresh must be >= 0");
+    if (s->reserved != 0) return fail(PHIA_EINVAL, "schedule.reserved must be 0");
+    return PHIA_OK;
+}
+
+RunArgs base_args(phia_t *p, int R) {
+    RunArgs a;
+    memset(&a, 0, sizeof a);
+    a.N = p->N;
+    a.frac_bits = p->frac_bits;
+    a.Jk = p->d_Jk;
+    a.Jf = p->d_Jf;
+    a.hk = p->d_hk;
+    a.row_ptr = p->d_rowptr; a.col = p->d_col; a.val = p->d_val;
+    a.R = R;
+    a.q = ldexpf(1.0f, -p->frac_bits);
+    a.inst = p->inst;
+    a.best_e = p->d_best_e; a.best_step = p->d_best_step; a.hit_step = p->d_hit;
+    a.best_bits = p->d_bits; a.W = p->W;
+    a.min_hit = p->d_min_hit; a.replica_iters = p->d_iters; a.err = p->d_err;
+    return a;
+}
+
+cudaError_t launch_path(phia_t *p, const RunArgs &a, int *launches) {
+    if (p->path == PHIA_PATH_TC) return launch_tc_small(a, p->op, p->stream, launches);
+    if (p->path == PHIA_PATH_FP32)
+        return launch_fp32_run(a, p->d_x, p->d_v, p->d_s0, p->d_s1, p->d_eacc, p->stream, launches);
+    return cudaErrorNotSupported;
+}
+
+int common_create(phia_t **out, int32_t N, int32_t frac_bits, const phia_opts *opts, const int32_t *h_k) {
+    if (!out) return fail(PHIA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (N < 1) return fail(PHIA_EINVAL, "N must be >= 1 (got %d)", N);
+    if (N > (1 << 20)) return fail(PHIA_ERANGE, "N = %d exceeds 2^20", N);
+    if (frac_bits < 0 || frac_bits > 30) return fail(PHIA_EINVAL, "frac_bits must be in [0, 30]");
+    if (!h_k) return fail(PHIA_EINVAL, "h_k is NULL");
+    for (int i = 0; i < N; ++i)
+        if (h_k[i] >= (1 << 24) || h_k[i] <= -(1 << 24)) return fail(PHIA_ERANGE, "|h_k[%d]| >= 2^24", i);
+    return PHIA_OK;
+}
+
+int finish_create(phia_t *p, const int32_t *h_k, const phia_opts *opts) {
+    CU(cudaMalloc((void **)&p->d_hk, (size_t)p->N * 4));
+    CU(cudaMemcpyAsync(p->d_hk, h_k, (size_t)p->N * 4, cudaMemcpyHostToDevice, p->stream));
+    CU(cudaMalloc((void **)&p->d_min_hit, 8));
+    CU(cudaMalloc((void **)&p->d_iters, 8));
+    CU(cudaMalloc((void **)&p->d_err, 4));
+    CU(cudaMemsetAsync(p->d_err, 0, 4, p->stream));
+    CU(cudaEventCreate(&p->ev0));
+    CU(cudaEventCreate(&p->ev1));
+    CU(cudaStreamSynchronize(p->stream));
+    (void)opts;
+    return PHIA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *phia_last_error(void) { return g_err.c_str(); }
+
+int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, int32_t frac_bits,
+                const phia_opts *opts) {
+    int rc = common_create(out, N, frac_bits, opts, h_k);
+    if (rc) return rc;
+    if (!J_k) return fail(PHIA_EINVAL, "J_k is NULL");
+    int max_abs = 0;
+    for (int i = 0; i < N; ++i) {
+        if (J_k[(size_t)i * N + i] != 0) return fail(PHIA_EINVAL, "nonzero diagonal J_k[%d][%d]", i, i);
+        for (int j = i + 1; j < N; ++j) {
+            const int a = J_k[(size_t)i * N + j], b = J_k[(size_t)j * N + i];
+            if (a != b) return fail(PHIA_EINVAL, "J_k is not symmetric at (%d, %d)", i, j);
+            max_abs = std::max(max_abs, std::abs(a));
+        }
+    }
+    phia_opts o{};
+    if (opts) o = *opts;
+    int path = o.path == PHIA_PATH_AUTO ? PHIA_PATH_TC : o.path;
+    if (path == PHIA_PATH_CSR) return fail(PHIA_ENOTSUP, "dense instance on the CSR path: use phia_create_csr");
+    if (path != PHIA_PATH_TC && path != PHIA_PATH_FP32) return fail(PHIA_EINVAL, "unknown path %d", o.path);
+    int op = 0;
+    if (path == PHIA_PATH_TC) {
+        op = o.operand == PHIA_OP_AUTO ? (max_abs <= 16 ? PHIA_OP_E4M3 : PHIA_OP_BF16) : o.operand;
+        if (op != PHIA_OP_E4M3 && op != PHIA_OP_BF16) return fail(PHIA_EINVAL, "unknown operand %d", o.operand);
+        if (op == PHIA_OP_E4M3 && max_abs > 16)
+            return fail(PHIA_ERANGE, "max |k| = %d is not exact in e4m3 (needs <= 16)", max_abs);
+        const int opk = op == PHIA_OP_E4M3 ? kOpE4M3 : kOpBF16;
+        if (N > tc_small_max_n(opk)) {
+            if (o.path == PHIA_PATH_AUTO) {
+                path = PHIA_PATH_FP32;
+                op = 0;
+            } else {
+                return fail(PHIA_ENOTSUP, "tensor-core path handles N <= %d with this operand (N = %d)",
+                            tc_small_max_n(opk), N);
+            }
+        }
+    }
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
+        return fail(PHIA_ECUDA, "no CUDA device available");
+    if (o.device < 0 || o.device >= dev_count) return fail(PHIA_EINVAL, "device %d out of range", o.device);
+    CU(cudaSetDevice(o.device));
+    phia_t *p = new phia_t();
+    p->device = o.device;
+    p->stream = (cudaStream_t)o.stream;
+    p->path = path;
+    p->op = op == PHIA_OP_E4M3 ? kOpE4M3 : (op == PHIA_OP_BF16 ? kOpBF16 : 0);
+    p->inst = o.instance_id;
+    p->N = N;
+    p->frac_bits = frac_bits;
+    p->W = (N + 31) / 32;
+    p->max_abs_k = max_abs;
+    const size_t NN = (size_t)N * N;
+    auto cleanup = [&](int code) { phia_destroy(p); return code; };
+    if (cudaMalloc((void **)&p->d_Jk, NN) != cudaSuccess) return cleanup(fail(PHIA_ENOMEM, "J allocation failed"));
+    if (cudaMemcpyAsync(p->d_Jk, J_k, NN, cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
+        return cleanup(fail(PHIA_ECUDA, "J upload failed"));
+    if (path == PHIA_PATH_FP32) {
+        std::vector<float> jf(NN);
+        const float q = ldexpf(1.0f, -frac_bits);
+        for (size_t e = 0; e < NN; ++e) jf[e] = (float)J_k[e] * q;
+        if (cudaMalloc((void **)&p->d_Jf, NN * 4) != cudaSuccess)
+            return cleanup(fail(PHIA_ENOMEM, "J allocation failed"));
+        if (cudaMemcpy(p->d_Jf, jf.data(), NN * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(fail(PHIA_ECUDA, "J upload failed"));
+    }
+    rc = finish_create(p, h_k, &o);
+    if (rc) return cleanup(rc);
+    *out = p;
+    return PHIA_OK;
+}
+
+int phia_create_csr(phia_t **out, const int32_t *row_ptr, const int32_t *col, const int8_t *val_k,
+                    const int32_t *h_k, int32_t N, int32_t frac_bits, const phia_opts *opts) {
+    int rc = common_create(out, N, frac_bits, opts, h_k);
+    if (rc) return rc;
+    return fail(PHIA_ENOTSUP, "CSR instances are not built into this library yet");
+    (void)row_ptr; (void)col; (void)val_k;
+}
+
+static int run_impl(phia_t *p, const phia_schedule *sched, int32_t R, int64_t t0, int64_t steps, int64_t total,
+                    uint64_t seed, const float *x_in, float *x_out, const float *v_in, float *v_out, int reset) {
+    if (!p) return fail(PHIA_EINVAL, "handle is NULL");
+    int rc = check_sched(sched);
+    if (rc) return rc;
+    if (R < 1) return fail(PHIA_EINVAL, "replicas must be >= 1");
+    if (steps < 1) return fail(PHIA_EINVAL, "steps must be >= 1");
+    if (t0 < 0 || total < t0 + steps) return fail(PHIA_EINVAL, "need 0 <= t0 and t0 + steps <= total_steps");
+    if (total > (int64_t)1 << 31) return fail(PHIA_ERANGE, "total_steps must be < 2^31 (Philox counter word)");
+    CU(cudaSetDevice(p->device));
+    if (!reset && (!p->ran || p->R_last != R))
+        return fail(PHIA_ESTATE, "reset_best = 0 needs a previous run with the same replica count");
+    rc = ensure_replicas(p, R);
+    if (rc) return rc;
+    if (reset) {
+        rc = reset_records(p, R);
+        if (rc) return rc;
+    }
+    CU(cudaMemsetAsync(p->d_min_hit, 0xFF, 8, p->stream));
+    CU(cudaMemsetAsync(p->d_iters, 0, 8, p->stream));
+    CU(cudaMemsetAsync(p->d_err, 0, 4, p->stream));
+    RunArgs a = base_args(p, R);
+    a.t0 = t0; a.nsteps = steps; a.T_total = total;
+    a.beta0 = sched->beta0; a.beta1 = sched->beta1; a.eps = sched->eps; a.gamma = sched->gamma;
+    a.refresh = sched->refresh;
+    a.seed = seed;
+    a.x_in = x_in; a.v_in = v_in; a.x_out = x_out; a.v_out = v_out;
+    a.has_target = sched->has_target; a.stop_at_target = sched->stop_at_target; a.target = sched->target_k;
+    int launches = 0;
+    CU(cudaEventRecord(p->ev0, p->stream));
+    cudaError_t e = launch_path(p, a, &launches);
+    if (e != cudaSuccess) return fail(PHIA_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    CU(cudaEventRecord(p->ev1, p->stream));
+    p->ran = true;
+    p->R_last = R;
+    p->last_steps = steps;
+    p->last_launches = launches;
+    p->last_stop = sched->stop_at_target;
+    return PHIA_OK;
+}
+
+int phia_anneal(phia_t *p, const phia_schedule *sched, int32_t replicas, int64_t steps, uint64_t seed) {
+    return run_impl(p, sched, replicas, 0, steps, steps, seed, nullptr, nullptr, nullptr, nullptr, 1);
+}
+
+int phia_run(phia_t *p, const phia_schedule *sched, int32_t replicas, int64_t t0, int64_t steps,
+             int64_t total_steps, uint64_t seed, float *x, float *v, int32_t reset_best) {
+    if (!x || !v) return fail(PHIA_EINVAL, "x and v must be device arrays");
+    return run_impl(p, sched, replicas, t0, steps, total_steps, seed, x, x, v, v, reset_best ? 1 : 0);
+}
+
+int phia_init_state(phia_t *p, int32_t replicas, uint64_t seed, float *x, float *v) {
+    if (!p) return fail(PHIA_EINVAL, "handle is NULL");
+    if (replicas < 1 || !x || !v) return fail(PHIA_EINVAL, "need replicas >= 1 and device x, v");
+    CU(cudaSetDevice(p->device));
+    CU(launch_init_state(replicas, p->N, seed, p->inst, x, v, p->stream));
+    return PHIA_OK;
+}
+
+int phia_field(phia_t *p, const int8_t *spins, int32_t R, int32_t *field_k, int64_t *energy_k) {
+    if (!p) return fail(PHIA_EINVAL, "handle is NULL");
+    if (R < 1 || !spins) return fail(PHIA_EINVAL, "need replicas >= 1 and device spins");
+    CU(cudaSetDevice(p->device));
+    int rc = ensure_replicas(p, R);
+    if (rc) return rc;
+    RunArgs a = base_args(p, R);
+    a.field_mode = 1;
+    a.spins_in = spins;
+    a.field_out = field_k;
+    a.energy_out = energy_k;
+    a.nsteps = 1; a.T_total = 1;
+    int launches = 0;
+    cudaError_t e = launch_path(p, a, &launches);
+    if (e != cudaSuccess) return fail(PHIA_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    return PHIA_OK;
+}
+
+int phia_philox_draws(uint64_t seed, uint32_t instance_id, uint32_t d, int32_t R, int32_t N, uint32_t *raw,
+                      float *x, float *v, void *stream) {
+    if (R < 0 || N < 0) return fail(PHIA_EINVAL, "negative size");
+    CU(launch_philox_draws(seed, instance_id, d, R, N, raw, x, v, (cudaStream_t)stream));
+    return PHIA_OK;
+}
+
+int phia_sync(phia_t *p) {
+    if (!p) return fail(PHIA_EINVAL, "handle is NULL");
+    CU(cudaSetDevice(p->device));
+    CU(cudaStreamSynchronize(p->stream));
+    return PHIA_OK;
+}
+
+static int fetch_records(phia_t *p, std::vector<int64_t> &be, std::vector<int64_t> &bs, std::vector<int64_t> &hs) {
+    if (!p->ran) return fail(PHIA_ESTATE, "no run on this handle yet");
+    CU(cudaSetDevice(p->device));
+    CU(cudaStreamSynchronize(p->stream));
+    int32_t err = 0;
+    CU(cudaMemcpy(&err, p->d_err, 4, cudaMemcpyDeviceToHost));
+    if (err) return fail(PHIA_ETIMEOUT, "a bounded device wait expired during the run");
+    const int R = p->R_last;
+    be.resize(R); bs.resize(R); hs.resize(R);
+    CU(cudaMemcpy(be.data(), p->d_best_e, (size_t)R * 8, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(bs.data(), p->d_best_step, (size_t)R * 8, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(hs.data(), p->d_hit, (size_t)R * 8, cudaMemcpyDeviceToHost));
+    return PHIA_OK;
+}
+
+// Result replica: with stop-at-target and a hit, the earliest hit (ties: lowest index);
+// otherwise the lowest energy (ties: earliest step, then lowest index).
+static int pick_result(phia_t *p, const std::vector<int64_t> &be, const std::vector<int64_t> &bs,
+                       const std::vector<int64_t> &hs) {
+    int best = -1;
+    if (p->last_stop) {
+        for (int r = 0; r < (int)hs.size(); ++r)
+            if (hs[r] >= 0 && (best < 0 || hs[r] < hs[best])) best = r;
+        if (best >= 0) return best;
+    }
+    for (int r = 0; r < (int)be.size(); ++r) {
+        if (bs[r] < 0) continue;
+        if (best < 0 || be[r] < be[best] || (be[r] == be[best] && bs[r] < bs[best])) best = r;
+    }
+    return best;
+}
+
+int phia_best(phia_t *p, int64_t *energy_k, int8_t *spins) {
+    if (!p) return fail(PHIA_EINVAL, "handle is NULL");
+    std::vector<int64_t> be, bs, hs;
+    int rc = fetch_records(p, be, bs, hs);
+    if (rc) return rc;
+    const int r = pick_result(p, be, bs, hs);
+    if (r < 0) return fail(PHIA_ESTATE, "no replica recorded a state");
+    if (energy_k) *energy_k = be[r];
+    if (spins) {
+        std::vector<uint32_t> w(p->W);
+        CU(cudaMemcpy(w.data(), p->d_bits + (size_t)r * p->W, (size_t)p->W * 4, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < p->N; ++i) spins[i] = ((w[i >> 5] >> (i & 31)) & 1u) ? 1 : -1;
+    }
+    return PHIA_OK;
+}
+
+int phia_replica_results(phia_t *p, int32_t R, int64_t *best_energy_k, int64_t *best_step, int64_t *hit_step,
+                         uint32_t *best_bits) {
+    if (!p) return fail(PHIA_EINVAL, "handle is NULL");
+    std::vector<int64_t> be, bs, hs;
+    int rc = fetch_records(p, be, bs, hs);
+    if (rc) return rc;
+    if (R != p->R_last) return fail(PHIA_EINVAL, "replicas (%d) differs from the last run (%d)", R, p->R_last);
+    if (best_energy_k) memcpy(best_energy_k, be.data(), (size_t)R * 8);
+    if (best_step) memcpy(best_step, bs.data(), (size_t)R * 8);
+    if (hit_step) memcpy(hit_step, hs.data(), (size_t)R * 8);
+    if (best_bits) CU(cudaMemcpy(best_bits, p->d_bits, (size_t)R * p->W * 4, cudaMemcpyDeviceToHost));
+    return PHIA_OK;
+}
+
+int phia_stats_get(phia_t *p, phia_stats *out) {
+    if (!p || !out) return fail(PHIA_EINVAL, "NULL argument");
+    std::vector<int64_t> be, bs, hs;
+    int rc = fetch_records(p, be, bs, hs);
+    if (rc) return rc;
+    memset(out, 0, sizeof *out);
+    unsigned long long iters = 0;
+    CU(cudaMemcpy(&iters, p->d_iters, 8, cudaMemcpyDeviceToHost));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+    out->replicas = p->R_last;
+    out->steps = p->last_steps;
+    out->spin_updates = (int64_t)iters * p->N;
+    const int r = pick_result(p, be, bs, hs);
+    out->best_replica = r;
+    out->best_energy_k = r >= 0 ? be[r] : 0;
+    out->best_step = r >= 0 ? bs[r] : -1;
+    out->hit_step = -1;
+    out->hit_replica = -1;
+    for (int k = 0; k < (int)hs.size(); ++k)
+        if (hs[k] >= 0 && (out->hit_step < 0 || hs[k] < out->hit_step)) { out->hit_step = hs[k]; out->hit_replica = k; }
+    out->device_ms = ms;
+    out->path = p->path;
+    out->operand = p->op == kOpE4M3 ? PHIA_OP_E4M3 : (p->op == kOpBF16 ? PHIA_OP_BF16 : 0);
+    out->kernel_launches = p->last_launches;
+    return PHIA_OK;
+}
+
+void phia_destroy(phia_t *p) {
+    if (!p) return;
+    cudaSetDevice(p->device);
+    cudaStreamSynchronize(p->stream);
+    free_replicas(p);
+    cudaFree(p->d_Jk); cudaFree(p->d_Jf); cudaFree(p->d_hk);
+    cudaFree(p->d_rowptr); cudaFree(p->d_col); cudaFree(p->d_val);
+    cudaFree(p->d_min_hit); cudaFree(p->d_iters); cudaFree(p->d_err);
+    if (p->ev0) cudaEventDestroy(p->ev0);
+    if (p->ev1) cudaEventDestroy(p->ev1);
+    delete p;
+}
+
+}  // extern "C"

@@ -1,0 +1,205 @@
+// device_common.cuh -- device helpers shared by every PHIA kernel of this library.
+//
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and the Box-Muller transform
+// (Box & Muller, 1958) written from their published definitions; the momentum
+// update of Eqs. 5, 8 and A7; inline-PTX wrappers for mbarrier, tcgen05 (TMEM
+// allocation, MMA, commit, loads, fences) used by the tensor-core kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace phia {
+
+// ------------------------------------------------------------------ Philox
+
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+// 24-bit uniforms: exactly representable in FP32, so host and device agree on them.
+__device__ __forceinline__ float u01_open(uint32_t a) { return (float)((a >> 8) + 1u) * 5.9604644775390625e-8f; }
+__device__ __forceinline__ float u01_half(uint32_t a) { return (float)(a >> 8) * 5.9604644775390625e-8f; }
+
+// Box-Muller, cosine branch: sqrt(-2 ln u1) cos(2 pi u2).
+__device__ __forceinline__ float box_muller(uint32_t a, uint32_t b) {
+    return sqrtf(-2.0f * logf(u01_open(a))) * cospif(2.0f * u01_half(b));
+}
+
+// Counter (spin j, replica r, draw d, instance), key = seed: words 0-1 -> position
+// draw, words 2-3 -> momentum draw.
+__device__ __forceinline__ U4 draw_raw(uint64_t seed, uint32_t inst, uint32_t r, uint32_t j, uint32_t d) {
+    return philox4x32_10(j, r, d, inst, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+__device__ __forceinline__ float draw_x(uint64_t seed, uint32_t inst, uint32_t r, uint32_t j, uint32_t d) {
+    U4 o = draw_raw(seed, inst, r, j, d);
+    return box_muller(o.x, o.y);
+}
+__device__ __forceinline__ float draw_v(uint64_t seed, uint32_t inst, uint32_t r, uint32_t j, uint32_t d) {
+    U4 o = draw_raw(seed, inst, r, j, d);
+    return box_muller(o.z, o.w);
+}
+
+// ------------------------------------------------------------------ HMC update
+
+// Eq. A7 second line with the gradient of Eq. A8 under Eq. 8:
+//   v' = v + eps * (beta gamma (1 - tanh^2(gamma x)) q I - x),   bgq = beta * gamma * q.
+__device__ __forceinline__ float momentum_update(float v, float x, float I, float eps, float bgq,
+                                                 float gamma) {
+    const float t = tanhf(gamma * x);
+    const float sech2 = 1.0f - t * t;
+    return v + eps * (bgq * sech2 * I - x);
+}
+
+// beta_t linear from beta0 (t = 0) to beta1 (t = T-1).
+__device__ __forceinline__ float beta_at(int64_t t, int64_t T, float beta0, float beta1) {
+    if (T <= 1) return beta0;
+    return beta0 + (beta1 - beta0) * ((float)t / (float)(T - 1));
+}
+
+__device__ __forceinline__ bool refresh_at(int64_t t, int32_t refresh) {
+    return refresh > 0 && t > 0 && (t % refresh) == 0;
+}
+
+// ------------------------------------------------------------------ PTX wrappers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: false when `timeout_ns` of wall time passed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t_start = globaltimer_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t_start > timeout_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void fence_mbarrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Make this thread's generic-proxy shared-memory writes visible to the async proxy
+// (tensor-core operand reads).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// TMEM allocation by one full warp; the base address is written to *dst_smem.
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8 rows x 16
+// bytes; lbo = byte distance between core matrices adjacent in K, sbo = byte distance
+// between adjacent 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc_noswizzle(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    return d;                // base offset 0, lbo mode 0, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor: dense, D = F32, A/B formats `fmt` (kind::f16: 1 = BF16;
+// kind::f8f6f4: 0 = E4M3), both K-major, N x M tile.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint32_t N) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive once on `bar` when every tcgen05 async operation issued so far by this
+// thread has completed.
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// 32 lanes x 32 bits, 8 consecutive columns per thread, followed by the wait for the
+// load; the registers pass through the wait so no use can be scheduled before it.
+__device__ __forceinline__ void tmem_ld_x8_sync(uint32_t taddr, float (&v)[8]) {
+    uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3), "+r"(r4), "+r"(r5), "+r"(r6), "+r"(r7)
+                 :
+                 : "memory");
+    v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1); v[2] = __uint_as_float(r2);
+    v[3] = __uint_as_float(r3); v[4] = __uint_as_float(r4); v[5] = __uint_as_float(r5);
+    v[6] = __uint_as_float(r6); v[7] = __uint_as_float(r7);
+}
+
+}  // namespace phia

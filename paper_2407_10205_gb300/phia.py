@@ -1,0 +1,255 @@
+"""Thin Python binding of the PHIA C ABI (include/phia.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA library
+``_build/libphia.so``.  Functions keep the C names without the ``phia_`` prefix
+where it would be redundant in Python (``phia.create`` is ``phia_create``).
+Device buffers are torch CUDA tensors (PyTorch provides memory and streams);
+host buffers are numpy arrays.  Errors raise ``PhiaError`` carrying the C code and
+``phia_last_error()``.  There is no fallback: if the library is missing the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libphia.so")
+
+OK, EINVAL, ERANGE, ENOMEM, ETIMEOUT, ECUDA, ESTATE, ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
+PATH_AUTO, PATH_TC, PATH_FP32, PATH_CSR = 0, 1, 2, 3
+OP_AUTO, OP_E4M3, OP_BF16 = 0, 1, 2
+_CODES = {EINVAL: "EINVAL", ERANGE: "ERANGE", ENOMEM: "ENOMEM", ETIMEOUT: "ETIMEOUT",
+          ECUDA: "ECUDA", ESTATE: "ESTATE", ENOTSUP: "ENOTSUP"}
+
+
+class PhiaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"PHIA_{_CODES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("operand", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("instance_id", ctypes.c_uint32), ("stream", ctypes.c_void_p)]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("beta0", ctypes.c_float), ("beta1", ctypes.c_float), ("eps", ctypes.c_float),
+                ("gamma", ctypes.c_float), ("refresh", ctypes.c_int32), ("has_target", ctypes.c_int32),
+                ("stop_at_target", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("target_k", ctypes.c_int64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("replicas", ctypes.c_int64), ("steps", ctypes.c_int64), ("spin_updates", ctypes.c_int64),
+                ("best_energy_k", ctypes.c_int64), ("best_replica", ctypes.c_int64),
+                ("best_step", ctypes.c_int64), ("hit_step", ctypes.c_int64), ("hit_replica", ctypes.c_int64),
+                ("device_ms", ctypes.c_float), ("path", ctypes.c_int32), ("operand", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+# name -> (restype, argtypes); every symbol include/phia.h declares
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "phia_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
+    "phia_create_csr": (ctypes.c_int, [ctypes.POINTER(_P), _P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
+    "phia_anneal": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64]),
+    "phia_best": (ctypes.c_int, [_P, _P, _P]),
+    "phia_stats_get": (ctypes.c_int, [_P, _P]),
+    "phia_replica_results": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P]),
+    "phia_run": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                ctypes.c_uint64, _P, _P, ctypes.c_int32]),
+    "phia_init_state": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint64, _P, _P]),
+    "phia_field": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
+    "phia_philox_draws": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32,
+                                         ctypes.c_int32, _P, _P, _P, _P]),
+    "phia_sync": (ctypes.c_int, [_P]),
+    "phia_destroy": (None, [_P]),
+    "phia_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libphia.so (built by ``paper_2407_10205_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"PHIA CUDA library not built ({p}); run paper_2407_10205_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().phia_last_error().decode()
+
+
+def _check(rc):
+    if rc != OK:
+        raise PhiaError(rc, last_error())
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device buffers must be contiguous CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def schedule(beta0, beta1, eps, gamma, refresh=0, target=None, stop_at_target=False) -> Schedule:
+    return Schedule(float(beta0), float(beta1), float(eps), float(gamma), int(refresh),
+                    0 if target is None else 1, 1 if stop_at_target else 0, 0,
+                    0 if target is None else int(target))
+
+
+def opts(path=PATH_AUTO, operand=OP_AUTO, device=0, instance_id=0, stream=None) -> Opts:
+    s = 0 if stream is None else int(stream)
+    return Opts(int(path), int(operand), int(device), int(instance_id) & 0xFFFFFFFF, ctypes.c_void_p(s or None))
+
+
+def create(J_k, h_k, frac_bits=0, o: Opts | None = None):
+    J_k = np.ascontiguousarray(J_k, dtype=np.int8)
+    h_k = np.ascontiguousarray(h_k, dtype=np.int32)
+    n = h_k.shape[0]
+    if J_k.shape != (n, n):
+        raise ValueError("J_k must be N x N")
+    h = ctypes.c_void_p()
+    _check(load().phia_create(ctypes.byref(h), _np_ptr(J_k), _np_ptr(h_k), n, int(frac_bits),
+                              ctypes.byref(o) if o is not None else None))
+    return h
+
+
+def create_csr(row_ptr, col, val_k, h_k, frac_bits=0, o: Opts | None = None):
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val_k = np.ascontiguousarray(val_k, dtype=np.int8)
+    h_k = np.ascontiguousarray(h_k, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(load().phia_create_csr(ctypes.byref(h), _np_ptr(row_ptr), _np_ptr(col), _np_ptr(val_k),
+                                  _np_ptr(h_k), h_k.shape[0], int(frac_bits),
+                                  ctypes.byref(o) if o is not None else None))
+    return h
+
+
+def anneal(h, sched: Schedule, replicas: int, steps: int, seed: int):
+    _check(load().phia_anneal(h, ctypes.byref(sched), int(replicas), int(steps), int(seed) & (2**64 - 1)))
+
+
+def best(h, n: int):
+    e = ctypes.c_int64()
+    spins = np.empty(n, dtype=np.int8)
+    _check(load().phia_best(h, ctypes.byref(e), _np_ptr(spins)))
+    return int(e.value), spins
+
+
+def stats_get(h) -> Stats:
+    s = Stats()
+    _check(load().phia_stats_get(h, ctypes.byref(s)))
+    return s
+
+
+def replica_results(h, replicas: int, n: int):
+    W = (n + 31) // 32
+    be = np.empty(replicas, dtype=np.int64)
+    bs = np.empty(replicas, dtype=np.int64)
+    hs = np.empty(replicas, dtype=np.int64)
+    bits = np.empty((replicas, W), dtype=np.uint32)
+    _check(load().phia_replica_results(h, int(replicas), _np_ptr(be), _np_ptr(bs), _np_ptr(hs), _np_ptr(bits)))
+    return be, bs, hs, bits
+
+
+def unpack_bits(bits, n: int) -> np.ndarray:
+    """Bit-packed spins ([R][W] uint32, bit i%32 of word i/32 = (s_i == +1)) -> int8 [R][n]."""
+    b = np.asarray(bits, dtype=np.uint32)
+    idx = np.arange(n)
+    on = (b[:, idx >> 5] >> (idx & 31).astype(np.uint32)) & 1
+    return np.where(on == 1, 1, -1).astype(np.int8)
+
+
+def run(h, sched: Schedule, replicas, t0, steps, total_steps, seed, x, v, reset_best=True):
+    _check(load().phia_run(h, ctypes.byref(sched), int(replicas), int(t0), int(steps), int(total_steps),
+                           int(seed) & (2**64 - 1), _dev_ptr(x), _dev_ptr(v), 1 if reset_best else 0))
+
+
+def init_state(h, replicas, seed, x, v):
+    _check(load().phia_init_state(h, int(replicas), int(seed) & (2**64 - 1), _dev_ptr(x), _dev_ptr(v)))
+
+
+def field(h, spins, field_k=None, energy_k=None):
+    _check(load().phia_field(h, _dev_ptr(spins), spins.shape[0], _dev_ptr(field_k), _dev_ptr(energy_k)))
+
+
+def philox_draws(seed, instance_id, d, replicas, n, raw=None, x=None, v=None, stream=None):
+    _check(load().phia_philox_draws(int(seed) & (2**64 - 1), int(instance_id) & 0xFFFFFFFF, int(d),
+                                    int(replicas), int(n), _dev_ptr(raw), _dev_ptr(x), _dev_ptr(v),
+                                    ctypes.c_void_p(int(stream) if stream else None)))
+
+
+def sync(h):
+    _check(load().phia_sync(h))
+
+
+def destroy(h):
+    if h:
+        load().phia_destroy(h)
+
+
+@dataclass
+class Result:
+    energy_k: int
+    spins: np.ndarray
+    stats: Stats
+
+
+class Annealer:
+    """One Ising instance on the device; ``anneal`` runs PHIA and returns the best state."""
+
+    def __init__(self, J_k=None, h_k=None, frac_bits=0, csr=None, path=PATH_AUTO, operand=OP_AUTO,
+                 device=0, instance_id=0, stream=None):
+        o = opts(path, operand, device, instance_id, stream)
+        if csr is not None:
+            row_ptr, col, val = csr
+            self.n = len(row_ptr) - 1
+            self.h = create_csr(row_ptr, col, val, h_k, frac_bits, o)
+        else:
+            self.n = int(np.asarray(h_k).shape[0])
+            self.h = create(J_k, h_k, frac_bits, o)
+
+    def anneal(self, sched: Schedule, replicas: int, steps: int, seed: int) -> Result:
+        anneal(self.h, sched, replicas, steps, seed)
+        e, s = best(self.h, self.n)
+        return Result(e, s, stats_get(self.h))
+
+    def close(self):
+        destroy(self.h)
+        self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                self.close()
+        except Exception:
+            pass

@@ -1,0 +1,126 @@
+"""C ABI and host-logic tests that need no GPU.
+
+The library must load and export every symbol include/phia.h declares; argument
+validation happens on the host before any device work, so its error paths are
+exercised here without a GPU.
+"""
+import os
+import re
+import threading
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from paper_2407_10205_gb300 import build as pbuild
+from paper_2407_10205_gb300 import instances as ins
+from paper_2407_10205_gb300 import phia
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pbuild.build()
+    return phia.load()
+
+
+def _declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "phia.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(phia_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_symbols_exported(lib):
+    names = _declared_symbols()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/phia.h but not exported"
+    assert set(names) == set(phia.SIGNATURES), "binding and header disagree"
+
+
+def _create_rc(lib, J, h, frac=0, o=None):
+    import ctypes
+    J = np.ascontiguousarray(J, dtype=np.int8)
+    h = np.ascontiguousarray(h, dtype=np.int32)
+    out = ctypes.c_void_p()
+    rc = lib.phia_create(ctypes.byref(out), J.ctypes.data_as(ctypes.c_void_p),
+                         h.ctypes.data_as(ctypes.c_void_p), h.shape[0], frac,
+                         ctypes.byref(o) if o is not None else None)
+    return rc, out
+
+
+def test_invalid_instances_rejected(lib):
+    d = ins.dense_int(10, 5, 5, seed=1)
+    J = d.k.copy(); J[2, 7] += 1
+    assert _create_rc(lib, J, d.kh)[0] == phia.EINVAL
+    assert "symmetric" in phia.last_error()
+    J = d.k.copy(); J[3, 3] = 1
+    assert _create_rc(lib, J, d.kh)[0] == phia.EINVAL
+    assert "diagonal" in phia.last_error()
+    h = d.kh.copy(); h[0] = 1 << 24
+    assert _create_rc(lib, d.k, h)[0] == phia.ERANGE
+    assert _create_rc(lib, d.k, d.kh, frac=31)[0] == phia.EINVAL
+    big = ins.dense_int(10, 100, 5, seed=2)
+    o = phia.opts(path=phia.PATH_TC, operand=phia.OP_E4M3)
+    assert _create_rc(lib, big.k, big.kh, o=o)[0] == phia.ERANGE
+    assert "e4m3" in phia.last_error()
+
+
+def test_zero_spins_rejected(lib):
+    import ctypes
+    out = ctypes.c_void_p()
+    h = np.zeros(1, dtype=np.int32)
+    rc = lib.phia_create(ctypes.byref(out), None, h.ctypes.data_as(ctypes.c_void_p), 0, 0, None)
+    assert rc == phia.EINVAL
+
+
+def test_last_error_is_thread_local(lib):
+    d = ins.dense_int(6, 3, 3, seed=3)
+    J = d.k.copy(); J[0, 1] += 1
+    assert _create_rc(lib, J, d.kh)[0] == phia.EINVAL
+    seen = {}
+
+    def other():
+        seen["msg"] = phia.last_error()
+
+    t = threading.Thread(target=other); t.start(); t.join()
+    assert seen["msg"] == ""
+    assert "symmetric" in phia.last_error()
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    s = phia.schedule(0.1, 1.0, 0.1, 2.0)
+    import ctypes
+    assert lib.phia_anneal(None, ctypes.byref(s), 4, 10, 1) == phia.EINVAL
+    assert lib.phia_best(None, None, None) == phia.EINVAL
+    assert lib.phia_sync(None) == phia.EINVAL
+    lib.phia_destroy(None)
+
+
+def test_unpack_bits():
+    S = ins.random_spins(5, 70, seed=4)
+    W = 3
+    bits = np.zeros((5, W), dtype=np.uint32)
+    for r in range(5):
+        for i in range(70):
+            if S[r, i] > 0:
+                bits[r, i // 32] |= np.uint32(1 << (i % 32))
+    assert np.array_equal(phia.unpack_bits(bits, 70), S)
+
+
+def test_instance_generators():
+    d = ins.sk_pm1(50, seed=1)
+    assert np.array_equal(d.k, d.k.T) and not np.diag(d.k).any()
+    assert set(np.unique(d.k[~np.eye(50, dtype=bool)])) == {-1, 1}
+    d2 = ins.dense_int(60, 7, 7, seed=2)
+    assert d2.k.min() >= -7 and d2.k.max() <= 7 and np.array_equal(d2.k, d2.k.T)
+    c = ins.erdos_renyi(400, 0.05, 127, 31, 4, seed=3)
+    dd = c.to_dense()
+    assert np.array_equal(dd.k, dd.k.T) and not np.diag(dd.k).any()
+    dens = c.nnz / (400 * 399)
+    assert 0.04 < dens < 0.06
+    assert all(np.all(np.diff(c.col[c.row_ptr[i]:c.row_ptr[i + 1]]) > 0) for i in range(400))
+    b = ins.batched_er(6, seed=4)
+    assert all(100 <= x.n <= 3000 for x in b)
+    reqs = ins.serving_stream(20, seed=5)
+    assert all(reqs[i].arrival_s < reqs[i + 1].arrival_s for i in range(19))
+    assert all(64 <= r.instance.n <= 8192 for r in reqs)
