@@ -71,6 +71,9 @@ typedef struct phia_opts {
     int32_t device;        /* CUDA device ordinal */
     uint32_t instance_id;  /* fourth Philox counter word: separates instances sharing a seed */
     void *stream;          /* cudaStream_t to enqueue on; NULL = legacy default stream */
+    int32_t tile_replicas; /* tensor-core path: replicas per CTA, 4, 8 or 16; 0 = automatic */
+    int32_t coupling_mem;  /* tensor-core path, where J stays during a run: 1 = shared memory,
+                              2 = tensor memory; 0 = automatic */
 } phia_opts;
 
 /* Annealing schedule.  No values are given in the paper; every field is explicit. */

@@ -55,6 +55,7 @@ struct phia_s {
     int path = PHIA_PATH_TC;
     int op = 0;
     uint32_t inst = 0;
+    int tile_rl = 0, coupling_mem = 0;
     int N = 0, frac_bits = 0, W = 0;
     bool csr = false;
     int64_t nnz = 0;
@@ -152,6 +153,8 @@ RunArgs base_args(phia_t *p, int R) {
     a.best_e = p->d_best_e; a.best_step = p->d_best_step; a.hit_step = p->d_hit;
     a.best_bits = p->d_bits; a.W = p->W;
     a.min_hit = p->d_min_hit; a.replica_iters = p->d_iters; a.err = p->d_err;
+    a.tile_rl = p->tile_rl;
+    a.coupling_mem = p->coupling_mem;
     return a;
 }
 
@@ -210,6 +213,9 @@ int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, 
     }
     phia_opts o{};
     if (opts) o = *opts;
+    if (o.tile_replicas != 0 && o.tile_replicas != 4 && o.tile_replicas != 8 && o.tile_replicas != 16)
+        return fail(PHIA_EINVAL, "tile_replicas must be 0, 4, 8 or 16");
+    if (o.coupling_mem < 0 || o.coupling_mem > 2) return fail(PHIA_EINVAL, "coupling_mem must be 0, 1 or 2");
     int path = o.path == PHIA_PATH_AUTO ? PHIA_PATH_TC : o.path;
     if (path == PHIA_PATH_CSR) return fail(PHIA_ENOTSUP, "dense instance on the CSR path: use phia_create_csr");
     if (path != PHIA_PATH_TC && path != PHIA_PATH_FP32) return fail(PHIA_EINVAL, "unknown path %d", o.path);
@@ -241,6 +247,8 @@ int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, 
     p->path = path;
     p->op = op == PHIA_OP_E4M3 ? kOpE4M3 : (op == PHIA_OP_BF16 ? kOpBF16 : 0);
     p->inst = o.instance_id;
+    p->tile_rl = o.tile_replicas;
+    p->coupling_mem = o.coupling_mem;
     p->N = N;
     p->frac_bits = frac_bits;
     p->W = (N + 31) / 32;
@@ -301,7 +309,7 @@ static int run_impl(phia_t *p, const phia_schedule *sched, int32_t R, int64_t t0
     a.seed = seed;
     a.x_in = x_in; a.v_in = v_in; a.x_out = x_out; a.v_out = v_out;
     a.has_target = sched->has_target; a.stop_at_target = sched->stop_at_target; a.target = sched->target_k;
-    int launches = 0;
+    int launches = reset ? 1 : 0;
     CU(cudaEventRecord(p->ev0, p->stream));
     cudaError_t e = launch_path(p, a, &launches);
     if (e != cudaSuccess) return fail(PHIA_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));

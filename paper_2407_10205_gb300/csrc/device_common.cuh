@@ -53,20 +53,27 @@ __device__ __forceinline__ float draw_v(uint64_t seed, uint32_t inst, uint32_t r
 
 // ------------------------------------------------------------------ HMC update
 
+// Eq. 8's derivative factor 1 - tanh^2(y) = sech^2(y), evaluated through the identity
+// sech^2(y) = 4 e^{-2|y|} / (1 + e^{-2|y|})^2 with one fast exponential (relative error
+// a few 1e-6; it goes to 0 without cancellation for large |y|).
+__device__ __forceinline__ float sech2(float y) {
+    const float e = __expf(-2.0f * fabsf(y));
+    const float d = 1.0f + e;
+    return __fdividef(4.0f * e, d * d);
+}
+
 // Eq. A7 second line with the gradient of Eq. A8 under Eq. 8:
 //   v' = v + eps * (beta gamma (1 - tanh^2(gamma x)) q I - x),   bgq = beta * gamma * q.
 __device__ __forceinline__ float momentum_update(float v, float x, float I, float eps, float bgq,
                                                  float gamma) {
-    const float t = tanhf(gamma * x);
-    const float sech2 = 1.0f - t * t;
-    return v + eps * (bgq * sech2 * I - x);
+    return v + eps * (bgq * sech2(gamma * x) * I - x);
 }
 
-// beta_t linear from beta0 (t = 0) to beta1 (t = T-1).
-__device__ __forceinline__ float beta_at(int64_t t, int64_t T, float beta0, float beta1) {
-    if (T <= 1) return beta0;
-    return beta0 + (beta1 - beta0) * ((float)t / (float)(T - 1));
+// beta_t linear from beta0 (t = 0) to beta1 (t = T-1); inv_tm1 = 1 / (T - 1), 0 if T <= 1.
+__device__ __forceinline__ float beta_at(int64_t t, float inv_tm1, float beta0, float beta1) {
+    return beta0 + (beta1 - beta0) * ((float)t * inv_tm1);
 }
+__host__ __device__ inline float inv_tm1_of(int64_t T) { return T > 1 ? 1.0f / (float)(T - 1) : 0.0f; }
 
 __device__ __forceinline__ bool refresh_at(int64_t t, int32_t refresh) {
     return refresh > 0 && t > 0 && (t % refresh) == 0;
@@ -102,10 +109,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 
 // Bounded wait on an mbarrier phase: false when `timeout_ns` of wall time passed.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t timeout_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
+    for (int k = 0; k < 64; ++k)
+        if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t_start = globaltimer_ns();
     for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
+        for (int k = 0; k < 256; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
         if (globaltimer_ns() - t_start > timeout_ns) return false;
     }
 }
@@ -178,12 +187,61 @@ __device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
+// Same MMAs with the A operand read from tensor memory (lane = row of A, its K
+// elements packed little-endian into consecutive 32-bit columns).
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_e4m3_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 32 lanes x 32 bits, 8 consecutive columns per thread, from registers into TMEM.
+__device__ __forceinline__ void tmem_st_x8(uint32_t taddr, const uint32_t (&w)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+                 "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Arrive once on `bar` when every tcgen05 async operation issued so far by this
 // thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
                  : "memory");
+}
+
+// 32 lanes x 32 bits, 2 consecutive columns per thread, then the wait for the load.
+__device__ __forceinline__ void tmem_ld_x2_sync(uint32_t taddr, float (&v)[2]) {
+    uint32_t r0, r1;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r0), "+r"(r1) : : "memory");
+    v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1);
+}
+
+// 32 lanes x 32 bits, 4 consecutive columns per thread, then the wait for the load.
+__device__ __forceinline__ void tmem_ld_x4_sync(uint32_t taddr, float (&v)[4]) {
+    uint32_t r0, r1, r2, r3;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3) : : "memory");
+    v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1); v[2] = __uint_as_float(r2);
+    v[3] = __uint_as_float(r3);
 }
 
 // 32 lanes x 32 bits, 8 consecutive columns per thread, followed by the wait for the

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) fp32_step(const RunArgs a, int64_t t, flo
     const int32_t hki = live_i ? a.hk[i] : 0;
     const float hf = (float)hki * a.q;
     const float scale = ldexpf(1.0f, a.frac_bits);
-    const float beta = beta_at(t, a.T_total, a.beta0, a.beta1);
+    const float beta = beta_at(t, inv_tm1_of(a.T_total), a.beta0, a.beta1);
     const float bgq = beta * a.gamma;   // J and h already carry q here
     const bool more = t + 1 < a.t0 + a.nsteps;
     const bool refresh_next = more && refresh_at(t + 1, a.refresh);

@@ -24,24 +24,32 @@ namespace phia {
 
 namespace {
 
-constexpr int kRB = 16;  // replicas per CTA = MMA N
+constexpr int kNB = 16;  // MMA N: replica columns per CTA (live ones first, the rest zero)
+
+constexpr int kMaxWarps = 48;   // 4 lane quadrants x up to 3 output tiles x up to 4 replica splits
+constexpr int kMaxRPT = 8;
 
 struct SmallShared {
     uint64_t mbar;
     uint32_t tmem_base;
-    int32_t stop;
-    unsigned long long e_acc[kRB];
-    long long best_e[kRB];
-    long long best_step[kRB];
-    long long hit[kRB];
-    int32_t improved[kRB];
+    int32_t stop[2];                       // by iteration parity
+    int32_t e_part[2][kMaxWarps][kMaxRPT]; // per-warp sums of s_i (I_i + h_i), by iteration parity
+    long long best_e[kNB];
+    long long best_step[kNB];
+    long long hit[kNB];
+    int32_t improved[2][kNB];              // by iteration parity
 };
 
 template <int OP>
-__device__ __forceinline__ void put_operand(uint8_t *base, int row, int col, uint32_t sbo, float value) {
+__device__ __forceinline__ uint8_t *operand_ptr(uint8_t *base, int row, int col, uint32_t sbo) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
     const int kb = col * ESZ;
-    uint8_t *p = base + (row >> 3) * sbo + (kb >> 4) * 128 + (row & 7) * 16 + (kb & 15);
+    return base + (row >> 3) * sbo + (kb >> 4) * 128 + (row & 7) * 16 + (kb & 15);
+}
+
+template <int OP>
+__device__ __forceinline__ void put_operand(uint8_t *base, int row, int col, uint32_t sbo, float value) {
+    uint8_t *p = operand_ptr<OP>(base, row, col, sbo);
     if constexpr (OP == kOpE4M3) {
         *p = __nv_fp8_e4m3(value).__x;
     } else {
@@ -50,10 +58,7 @@ __device__ __forceinline__ void put_operand(uint8_t *base, int row, int col, uin
 }
 
 template <int OP>
-__device__ __forceinline__ void put_spin(uint8_t *base, int row, int col, uint32_t sbo, bool plus) {
-    constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
-    const int kb = col * ESZ;
-    uint8_t *p = base + (row >> 3) * sbo + (kb >> 4) * 128 + (row & 7) * 16 + (kb & 15);
+__device__ __forceinline__ void put_spin(uint8_t *p, bool plus) {
     if constexpr (OP == kOpE4M3) {
         *p = plus ? 0x38 : 0xB8;  // e4m3 +1.0 / -1.0
     } else {
@@ -61,31 +66,52 @@ __device__ __forceinline__ void put_spin(uint8_t *base, int row, int col, uint32
     }
 }
 
-template <int MT>
-__host__ __device__ constexpr uint32_t tmem_cols() { return MT * kRB <= 32 ? 32 : (MT * kRB <= 64 ? 64 : 128); }
+// Two accumulators per output tile (even and odd K-steps) so the tensor core sees
+// independent MMA chains; their sum is exact (both are integers below 2^24).
+__host__ __device__ constexpr uint32_t pow2_cols(uint32_t c) {
+    return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512;
+}
 
-template <int MT, int OP>
-__global__ void __launch_bounds__(256 * MT, 1) tc_small_kernel(const RunArgs a, int Kpad) {
+template <int RPT>
+__device__ __forceinline__ void tmem_ld_sync(uint32_t taddr, float (&v)[RPT]) {
+    static_assert(RPT == 2 || RPT == 4 || RPT == 8, "unsupported replicas per thread");
+    if constexpr (RPT == 8) tmem_ld_x8_sync(taddr, v);
+    else if constexpr (RPT == 4) tmem_ld_x4_sync(taddr, v);
+    else tmem_ld_x2_sync(taddr, v);
+}
+
+// MT: 128-spin output tiles; OP: operand encoding; CH: warps sharing one TMEM lane
+// quadrant (split over replicas); RPT: replicas per thread.  Live replicas per CTA =
+// CH * RPT (8 or 16); the MMA always runs 16 replica columns.
+// AT: the couplings (A operand) live in tensor memory instead of shared memory, so
+// each MMA reads only the 16-replica spin tile from shared memory.
+template <int MT, int OP, int CH, int RPT, bool AT>
+__global__ void __launch_bounds__(128 * MT * CH, CH == 1 ? 2 : 1) tc_small_kernel(const RunArgs a, int Kpad) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
-    constexpr uint32_t IDESC = make_idesc(OP == kOpE4M3 ? 0u : 1u, 128, kRB);
-    constexpr uint32_t TCOLS = tmem_cols<MT>();
+    constexpr int RL = CH * RPT;
+    constexpr uint32_t IDESC = make_idesc(OP == kOpE4M3 ? 0u : 1u, 128, kNB);
+    constexpr uint32_t ACC_COLS = 2 * MT * kNB;
+    static_assert(RL <= kNB, "live replicas exceed the MMA width");
+    static_assert(4 * MT * CH <= kMaxWarps && RPT <= kMaxRPT, "shared energy slots too small");
     const int Kbytes = Kpad * ESZ;
     const int KS = Kbytes / 32;            // MMA K-steps (32 bytes of K each)
     const uint32_t SBO = (uint32_t)Kbytes * 8u;
+    const uint32_t A_COLS = AT ? (uint32_t)(Kbytes / 4) : 0u;   // TMEM columns per output tile of A
+    const uint32_t TCOLS = pow2_cols(ACC_COLS + MT * A_COLS);
 
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sA = smem;
-    uint8_t *sB = sA + MT * 128 * Kbytes;
-    SmallShared *sm = reinterpret_cast<SmallShared *>(sB + kRB * Kbytes);
+    uint8_t *sB = AT ? smem : sA + MT * 128 * Kbytes;
+    SmallShared *sm = reinterpret_cast<SmallShared *>(sB + kNB * Kbytes);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q4 = warp & 3;               // TMEM lane quadrant this warp may access
     const int mt = (warp >> 2) % MT;       // output-spin tile
-    const int ch = warp / (4 * MT);        // which 8 of the 16 replicas
+    const int ch = warp / (4 * MT);        // which RPT of the RL replicas
     const int N = a.N;
     const int i = mt * 128 + q4 * 32 + lane;
     const bool live_i = i < N;
-    const int rbase = blockIdx.x * kRB;
+    const int rbase = blockIdx.x * RL;
 
     if (warp == 0) {
         tmem_alloc(&sm->tmem_base, TCOLS);
@@ -96,38 +122,70 @@ __global__ void __launch_bounds__(256 * MT, 1) tc_small_kernel(const RunArgs a, 
         fence_mbarrier_init();
     }
     // Couplings into A (zero-padded to MT*128 rows x Kpad columns), B cleared.
-    for (int idx = tid; idx < MT * 128 * Kpad; idx += blockDim.x) {
-        const int row = idx / Kpad, col = idx - row * Kpad;
-        const float val = (row < N && col < N) ? (float)a.Jk[(size_t)row * N + col] : 0.0f;
-        put_operand<OP>(sA, row, col, SBO, val);
+    if constexpr (!AT) {
+        for (int idx = tid; idx < MT * 128 * Kpad; idx += blockDim.x) {
+            const int row = idx / Kpad, col = idx - row * Kpad;
+            const float val = (row < N && col < N) ? (float)a.Jk[(size_t)row * N + col] : 0.0f;
+            put_operand<OP>(sA, row, col, SBO, val);
+        }
     }
-    for (int idx = tid; idx < kRB * Kbytes / 16; idx += blockDim.x)
+    for (int idx = tid; idx < kNB * Kbytes / 16; idx += blockDim.x)
         reinterpret_cast<uint4 *>(sB)[idx] = make_uint4(0, 0, 0, 0);
-    if (tid < kRB) {
+    if (tid < kNB) {
         const int r = rbase + tid;
-        sm->e_acc[tid] = 0;
-        sm->improved[tid] = 0;
-        const bool rec = !a.field_mode && r < a.R;
+        sm->improved[0][tid] = 0;
+        sm->improved[1][tid] = 0;
+        const bool rec = !a.field_mode && tid < RL && r < a.R;
         sm->best_e[tid] = rec ? a.best_e[r] : LLONG_MAX;
         sm->best_step[tid] = rec ? a.best_step[r] : -1;
         sm->hit[tid] = rec ? a.hit_step[r] : -1;
     }
-    if (tid == 0) sm->stop = 0;
-    __syncthreads();  // B cleared before spins are written into it
-
-    const int32_t hki = live_i ? a.hk[i] : 0;
-    float x[8], v[8];
-    uint32_t smask = 0;  // bit k: spin i of replica ch*8+k is +1 in the current B
+    if (tid == 0) sm->stop[0] = sm->stop[1] = 0;
+    tc_fence_before();
+    __syncthreads();  // B cleared before spins are written into it; TMEM base published
+    tc_fence_after();
+    if constexpr (AT) {
+        // Row i of A (output spin i) into TMEM lane i % 128 of tile i / 128: 32 bytes of K
+        // (8 columns) per store.  One warp per (lane quadrant, tile) does it.
+        if (ch == 0) {
+            const uint32_t base = sm->tmem_base + ((uint32_t)(q4 * 32) << 16) + ACC_COLS + mt * A_COLS;
+            for (int c8 = 0; c8 < Kbytes / 32; ++c8) {
+                uint32_t w[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int c = ch * 8 + k, r = rbase + c;
+                for (int q = 0; q < 8; ++q) {
+                    uint32_t word = 0;
+#pragma unroll
+                    for (int b = 0; b < 4 / ESZ; ++b) {
+                        const int col = (c8 * 32 + q * 4) / ESZ + b;
+                        const float val = (live_i && col < N) ? (float)a.Jk[(size_t)i * N + col] : 0.0f;
+                        uint32_t enc;
+                        if constexpr (OP == kOpE4M3) enc = __nv_fp8_e4m3(val).__x;
+                        else enc = __bfloat16_as_ushort(__float2bfloat16_rn(val));
+                        word |= enc << (8 * ESZ * b);
+                    }
+                    w[q] = word;
+                }
+                tmem_st_x8(base + c8 * 8, w);
+            }
+            tmem_st_wait();
+        }
+    }
+
+    // This thread's spin slots in B: replica c = ch*RPT + k sits at row c, column i.
+    uint8_t *my_b = operand_ptr<OP>(sB, ch * RPT, live_i ? i : 0, SBO);
+    const int32_t hki = live_i ? a.hk[i] : 0;
+    float x[RPT], v[RPT];
+    uint32_t cur = 0;  // bit k: spin i of replica ch*RPT+k is +1 in the B of this iteration
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int c = ch * RPT + k, r = rbase + c;
         x[k] = 0.0f; v[k] = 0.0f;
         if (!live_i) continue;
         if (a.field_mode) {
             if (r < a.R) {
                 const bool plus = a.spins_in[(size_t)r * N + i] > 0;
-                put_spin<OP>(sB, c, i, SBO, plus);
-                smask |= (uint32_t)plus << k;
+                put_spin<OP>(my_b + k * 16, plus);
+                cur |= (uint32_t)plus << k;
             }
             continue;
         }
@@ -142,77 +200,105 @@ __global__ void __launch_bounds__(256 * MT, 1) tc_small_kernel(const RunArgs a, 
         if (refresh_at(a.t0, a.refresh)) v[k] = draw_v(a.seed, a.inst, (uint32_t)r, (uint32_t)i, (uint32_t)a.t0);
         x[k] = x[k] + a.eps * v[k];                 // position half of Eq. A7
         const bool plus = x[k] >= 0.0f;             // sgn with sgn(0) = +1
-        put_spin<OP>(sB, c, i, SBO, plus);
-        smask |= (uint32_t)plus << k;
+        put_spin<OP>(my_b + k * 16, plus);
+        cur |= (uint32_t)plus << k;
     }
     fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sm->tmem_base;
-    const uint32_t my_taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(mt * kRB + ch * 8);
+    const uint32_t my_taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(2 * mt * kNB + ch * RPT);
+    const int word = (mt * 128 + q4 * 32) >> 5;
 
-    const int64_t t_end = a.field_mode ? a.t0 + 1 : a.t0 + a.nsteps;
-    uint32_t phase = 0;
+    const int nit = a.field_mode ? 1 : (int)a.nsteps;
+    const float inv_tm1 = inv_tm1_of(a.T_total);
+    const float eps = a.eps, gamma = a.gamma, gq = a.gamma * a.q;
+    int rc = a.refresh > 0 ? (int)((a.t0 + 1) % a.refresh) : 1;   // (t + 1) mod refresh
+    uint32_t phase = 0, prv = 0;
     bool timed_out = false, stopped = false;
-    int64_t iters = 0;
-    for (int64_t t = a.t0; t < t_end; ++t) {
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+    int it = 0;
+    // Field MMAs of one iteration: D[m] = A[m] B^T over all K-steps (thread 0 only).
+    // Descriptors advance by adding (byte offset >> 4) to the start-address field.
+    const uint64_t adesc0 = smem_desc_noswizzle(smem_u32(sA), 128, SBO);
+    const uint64_t bdesc0 = smem_desc_noswizzle(smem_u32(sB), 128, SBO);
+    // K-step ks of tile m accumulates into D[m][ks & 1]; tiles interleaved per K-step.
+    auto issue_field = [&]() {
+        tc_fence_after();
 #pragma unroll 1
+        for (int ks = 0; ks < KS; ++ks) {
+            const uint64_t bd = bdesc0 + (uint64_t)(ks * 16);   // 256 bytes per K-step
+#pragma unroll
             for (int m = 0; m < MT; ++m) {
-#pragma unroll 1
-                for (int ks = 0; ks < KS; ++ks) {
-                    const uint64_t ad = smem_desc_noswizzle(a0 + m * 16 * SBO + ks * 256, 128, SBO);
-                    const uint64_t bd = smem_desc_noswizzle(b0 + ks * 256, 128, SBO);
-                    if constexpr (OP == kOpE4M3) mma_e4m3(tmem + m * kRB, ad, bd, IDESC, ks > 0);
-                    else mma_bf16(tmem + m * kRB, ad, bd, IDESC, ks > 0);
+                const uint32_t d = tmem + (uint32_t)((2 * m + (ks & 1)) * kNB);
+                if constexpr (AT) {
+                    const uint32_t at = tmem + ACC_COLS + m * A_COLS + ks * 8;   // 32 bytes = 8 columns
+                    if constexpr (OP == kOpE4M3) mma_e4m3_ta(d, at, bd, IDESC, ks > 1);
+                    else mma_bf16_ta(d, at, bd, IDESC, ks > 1);
+                } else {
+                    const uint64_t ad = adesc0 + (uint64_t)((m * 16 * SBO) >> 4) + (uint64_t)(ks * 16);
+                    if constexpr (OP == kOpE4M3) mma_e4m3(d, ad, bd, IDESC, ks > 1);
+                    else mma_bf16(d, ad, bd, IDESC, ks > 1);
                 }
             }
-            mma_commit(&sm->mbar);
         }
+        mma_commit(&sm->mbar);
+    };
+    const bool two_acc = KS > 1;
+    if (tid == 0) issue_field();
+    for (; it < nit; ++it) {
+        const int64_t t = a.t0 + it;
         const bool ok = mbar_wait_bounded(&sm->mbar, phase, kWaitTimeoutNs);
         phase ^= 1u;
         tc_fence_after();
-        float acc[8];
-        tmem_ld_x8_sync(my_taddr, acc);
-
-        const float beta = beta_at(t, a.T_total, a.beta0, a.beta1);
-        const float bgq = beta * a.gamma * a.q;
-        const bool more = t + 1 < t_end;
-        const bool refresh_next = more && refresh_at(t + 1, a.refresh);
-        uint32_t newmask = 0;
+        float acc[RPT];
+        tmem_ld_sync<RPT>(my_taddr, acc);
+        if (two_acc) {
+            float acc2[RPT];
+            tmem_ld_sync<RPT>(my_taddr + kNB, acc2);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int c = ch * 8 + k, r = rbase + c;
+            for (int k = 0; k < RPT; ++k) acc[k] += acc2[k];
+        }
+
+        const float bgq = beta_at(t, inv_tm1, a.beta0, a.beta1) * gq;
+        const bool more = it + 1 < nit;
+        const bool refresh_next = more && a.refresh > 0 && rc == 0;
+        uint32_t nxt = 0;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int c = ch * RPT + k, r = rbase + c;
             const int32_t Ik = __float2int_rn(acc[k]) + hki;       // Eq. 6, exact
-            const int32_t sk = ((smask >> k) & 1u) ? 1 : -1;
+            const int32_t sk = ((cur >> k) & 1u) ? 1 : -1;
             int32_t part = live_i ? sk * (Ik + hki) : 0;            // s_i (I_i + h_i)
             part = __reduce_add_sync(0xffffffffu, part);
-            if (lane == 0) atomicAdd(&sm->e_acc[c], (unsigned long long)(long long)part);
+            if (lane == 0) sm->e_part[it & 1][warp][k] = part;
             if (a.field_mode) {
                 if (live_i && r < a.R && a.field_out) a.field_out[(size_t)r * N + i] = Ik;
                 continue;
             }
             if (!live_i) continue;
-            v[k] = momentum_update(v[k], x[k], (float)Ik, a.eps, bgq, a.gamma);
+            v[k] = momentum_update(v[k], x[k], (float)Ik, eps, bgq, gamma);
             if (more) {
                 if (refresh_next) v[k] = draw_v(a.seed, a.inst, (uint32_t)r, (uint32_t)i, (uint32_t)(t + 1));
-                x[k] = x[k] + a.eps * v[k];
+                x[k] = x[k] + eps * v[k];
                 const bool plus = x[k] >= 0.0f;
-                put_spin<OP>(sB, c, i, SBO, plus);
-                newmask |= (uint32_t)plus << k;
+                put_spin<OP>(my_b + k * 16, plus);
+                nxt |= (uint32_t)plus << k;
             }
         }
         fence_proxy_async_smem();
         tc_fence_before();
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
+        // Next iteration's field first: B holds its spins and every TMEM read is done.
+        if (tid == 0 && it + 1 < nit) issue_field();
 
-        if (tid < kRB) {
+        // Records of iteration t (Table 3, state 5), one thread per replica column.
+        if (tid < RL) {
             const int c = tid, r = rbase + c;
-            const long long E = -((long long)sm->e_acc[c]) / 2;    // Eq. 2 via the field
-            sm->e_acc[c] = 0;
+            long long twice = 0;   // sum_i s_i (I_i + h_i) over the 4*MT warps holding replica c
+#pragma unroll
+            for (int j = 0; j < 4 * MT; ++j) twice += sm->e_part[it & 1][(c / RPT) * 4 * MT + j][c % RPT];
+            const long long E = -twice / 2;                                  // Eq. 2 via the field
             int imp = 0;
             if (a.field_mode) {
                 if (r < a.R && a.energy_out) a.energy_out[r] = E;
@@ -228,38 +314,54 @@ __global__ void __launch_bounds__(256 * MT, 1) tc_small_kernel(const RunArgs a, 
                     if (a.stop_at_target) atomicMin(a.min_hit, (unsigned long long)t);
                 }
             }
-            sm->improved[c] = imp;
+            sm->improved[it & 1][c] = imp;
         }
         if (tid == 0)
-            sm->stop = (a.stop_at_target && !a.field_mode)
-                           ? (*(volatile unsigned long long *)a.min_hit <= (unsigned long long)t)
-                           : 0;
-        __syncthreads();
-        ++iters;
+            sm->stop[it & 1] = (a.stop_at_target && !a.field_mode)
+                                   ? (*(volatile unsigned long long *)a.min_hit <= (unsigned long long)t)
+                                   : 0;
+        // Best spins of iteration t-1 (its records were settled before this barrier).
+        if (it > 0) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int c = ch * 8 + k;
-            if (sm->improved[c]) {
-                const uint32_t bits = __ballot_sync(0xffffffffu, live_i && ((smask >> k) & 1u));
-                const int word = (mt * 128 + q4 * 32) >> 5;
+            for (int k = 0; k < RPT; ++k) {
+                const int c = ch * RPT + k;
+                if (sm->improved[(it - 1) & 1][c]) {
+                    const uint32_t bits = __ballot_sync(0xffffffffu, live_i && ((prv >> k) & 1u));
+                    if (lane == 0 && word < a.W) a.best_bits[(size_t)(rbase + c) * a.W + word] = bits;
+                }
+            }
+        }
+        prv = cur;
+        cur = nxt;
+        rc = (a.refresh > 0 && rc + 1 == a.refresh) ? 0 : rc + 1;
+        if (it > 0 && sm->stop[(it - 1) & 1]) { stopped = true; ++it; break; }
+    }
+    // A field issued for an iteration that will not run (stop) must finish before TMEM is freed.
+    if (stopped && it < nit && tid == 0) mbar_wait_bounded(&sm->mbar, phase, kWaitTimeoutNs);
+
+    if (!timed_out) {
+        __syncthreads();  // records of the last iteration settled
+        const int last = it - 1;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int c = ch * RPT + k;
+            if (last >= 0 && sm->improved[last & 1][c]) {
+                const uint32_t bits = __ballot_sync(0xffffffffu, live_i && ((prv >> k) & 1u));
                 if (lane == 0 && word < a.W) a.best_bits[(size_t)(rbase + c) * a.W + word] = bits;
             }
         }
-        smask = newmask;
-        if (sm->stop) { stopped = true; break; }
     }
-
     if (!a.field_mode && !timed_out && !stopped && a.x_out && live_i) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int r = rbase + ch * 8 + k;
+        for (int k = 0; k < RPT; ++k) {
+            const int r = rbase + ch * RPT + k;
             if (r < a.R) {
                 a.x_out[(size_t)r * N + i] = x[k];
                 a.v_out[(size_t)r * N + i] = v[k];
             }
         }
     }
-    if (tid < kRB && !a.field_mode) {
+    if (tid < RL && !a.field_mode) {
         const int r = rbase + tid;
         if (r < a.R) {
             a.best_e[r] = sm->best_e[tid];
@@ -268,11 +370,12 @@ __global__ void __launch_bounds__(256 * MT, 1) tc_small_kernel(const RunArgs a, 
         }
     }
     if (tid == 0) {
-        const int valid = min(kRB, a.R - rbase);
-        if (!a.field_mode) atomicAdd(a.replica_iters, (unsigned long long)(valid * iters));
+        const int valid = min(RL, a.R - rbase);
+        const int done = timed_out ? it : it;
+        if (!a.field_mode) atomicAdd(a.replica_iters, (unsigned long long)((long long)valid * done));
         if (timed_out) {
             atomicExch(a.err, 1);
-            mbar_wait_bounded(&sm->mbar, phase, kWaitTimeoutNs);  // let an MMA in flight drain
+            mbar_wait_bounded(&sm->mbar, phase ^ 1u, kWaitTimeoutNs);  // let the MMA in flight drain
         }
     }
     tc_fence_before();
@@ -283,16 +386,49 @@ __global__ void __launch_bounds__(256 * MT, 1) tc_small_kernel(const RunArgs a, 
     }
 }
 
-template <int MT, int OP>
-cudaError_t launch_mt(const RunArgs &a, int Kpad, cudaStream_t st) {
+template <int MT, int OP, int CH, int RPT, bool AT = false>
+cudaError_t launch_cfg(const RunArgs &a, int Kpad, cudaStream_t st) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
-    const size_t smem = (size_t)(MT * 128 + kRB) * Kpad * ESZ + sizeof(SmallShared) + 16;
-    auto kern = tc_small_kernel<MT, OP>;
+    constexpr int RL = CH * RPT;
+    const size_t smem = (size_t)((AT ? 0 : MT * 128) + kNB) * Kpad * ESZ + sizeof(SmallShared) + 16;
+    auto kern = tc_small_kernel<MT, OP, CH, RPT, AT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = (a.R + kRB - 1) / kRB;
-    kern<<<grid, 256 * MT, smem, st>>>(a, Kpad);
+    const int grid = (a.R + RL - 1) / RL;
+    kern<<<grid, 128 * MT * CH, smem, st>>>(a, Kpad);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+// Live replicas per CTA: the requested variant (4, 8 or 16), else 16 when that already
+// gives one CTA per SM, else 8.
+int tc_small_tile_replicas(int R, int requested) {
+    if (requested == 4 || requested == 8 || requested == 16) return requested;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return (R + 15) / 16 >= sms ? 16 : 8;
+}
+
+namespace {
+
+template <int MT, int OP, bool AT>
+cudaError_t launch_at(const RunArgs &a, int Kpad, cudaStream_t st) {
+    const int rl = tc_small_tile_replicas(a.R, a.tile_rl);
+    if (rl == 16) return launch_cfg<MT, OP, 2, 8, AT>(a, Kpad, st);
+    if (rl == 8) return launch_cfg<MT, OP, 2, 4, AT>(a, Kpad, st);
+    return launch_cfg<MT, OP, 1, 4, AT>(a, Kpad, st);
+}
+
+template <int MT, int OP>
+cudaError_t launch_mt(const RunArgs &a, int Kpad, cudaStream_t st) {
+    if (a.coupling_mem == 2) return launch_at<MT, OP, true>(a, Kpad, st);
+    return launch_at<MT, OP, false>(a, Kpad, st);
 }
 
 }  // namespace

@@ -39,6 +39,8 @@ struct RunArgs {
     unsigned long long *min_hit;         // earliest hit over replicas (stop-at-target)
     unsigned long long *replica_iters;   // sum over replicas of iterations run
     int32_t *err;                        // nonzero: a bounded device wait expired
+    int32_t tile_rl;                     // tensor-core small path: live replicas per CTA (0 = auto)
+    int32_t coupling_mem;                // tensor-core small path: 1 = J in shared, 2 = in tensor memory
 };
 
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;  // 2 s bound on every device-side wait
@@ -47,6 +49,7 @@ constexpr int kOpBF16 = 2;
 
 // tcgen05 persistent kernel for small dense instances (J resident in shared memory).
 int tc_small_max_n(int op);
+int tc_small_tile_replicas(int R, int requested);
 cudaError_t launch_tc_small(const RunArgs &a, int op, cudaStream_t st, int *launches);
 
 // Plain FP32 per-step path (the comparator).

@@ -19,13 +19,16 @@ torch = pytest.importorskip("torch")
 
 TC_E4M3 = ("tc", 1)
 TC_BF16 = ("tc", 2)
+TC_E4M3_TM = ("tc", 1, 2)   # couplings kept in tensor memory
+TC_BF16_TM = ("tc", 2, 2)
 FP32 = ("fp32", 0)
 
 
 def _handle(phia, d, path, frac=0):
-    kind, op = path
+    kind, op = path[0], path[1]
+    mem = path[2] if len(path) > 2 else 0
     p = phia.PATH_TC if kind == "tc" else phia.PATH_FP32
-    return phia.Annealer(d.k, d.kh, frac_bits=frac, path=p, operand=op)
+    return phia.Annealer(d.k, d.kh, frac_bits=frac, path=p, operand=op, coupling_mem=mem)
 
 
 def _oinst(d, frac=0):
@@ -61,6 +64,8 @@ FIELD_CASES = [
     (TC_E4M3, 200, 64, 7, 7), (TC_E4M3, 257, 20, 16, 1000), (TC_E4M3, 384, 16, 16, 5),
     (TC_BF16, 5, 3, 127, 9), (TC_BF16, 100, 31, 127, 1 << 20), (TC_BF16, 256, 48, 127, 127),
     (FP32, 7, 5, 7, 7), (FP32, 200, 64, 7, 7), (FP32, 333, 19, 127, 50),
+    (TC_E4M3_TM, 3, 1, 1, 0), (TC_E4M3_TM, 200, 64, 7, 7), (TC_E4M3_TM, 384, 16, 16, 5),
+    (TC_BF16_TM, 5, 3, 127, 9), (TC_BF16_TM, 256, 48, 127, 127),
 ]
 
 
@@ -80,7 +85,8 @@ def test_field_and_energy_bit_exact(gpu_lib, path, N, R, kmax, hmax):
 
 
 @pytest.mark.parametrize("path,N,kval", [(TC_E4M3, 384, 16), (TC_E4M3, 384, -16), (TC_BF16, 256, 127),
-                                         (TC_BF16, 256, -127), (FP32, 384, 127)])
+                                         (TC_BF16, 256, -127), (FP32, 384, 127), (TC_E4M3_TM, 384, 16),
+                                         (TC_BF16_TM, 256, -127)])
 def test_field_extreme_magnitudes(gpu_lib, path, N, kval):
     """Every product of one sign at the largest exact |k|: the accumulator's largest
     partial sums (|I| = |k| (N - 1)) must stay exact; alternating states as well."""
@@ -267,3 +273,26 @@ def test_stop_at_target(gpu_lib):
     assert res.energy_k <= emin and o.energy_exact(P, res.spins) == res.energy_k
     assert res.stats.hit_step == hs_full[hs_full >= 0].min()
     assert res.stats.spin_updates < res_full.stats.spin_updates
+
+
+@pytest.mark.parametrize("N,op", [(200, 1), (333, 1), (100, 2)])
+def test_tile_variants_bit_identical(gpu_lib, N, op):
+    """Replicas per CTA (4, 8, 16) and where J is kept (shared or tensor memory) change
+    only the work split and the operand source: every replica's arithmetic is the same,
+    so per-replica records and final states must be bit-identical."""
+    phia = gpu_lib
+    R, T = 50, 150
+    kmax = 7 if op == 1 else 100
+    d = ins.dense_int(N, kmax, 7, seed=N)
+    sched = phia.schedule(0.01, 0.2, 0.1, 2.0, refresh=40)
+    outs = []
+    for tile, mem in ((4, 1), (8, 1), (16, 1), (4, 2), (8, 2), (16, 2)):
+        with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, operand=op, tile_replicas=tile, coupling_mem=mem) as A:
+            x = torch.empty((R, N), device="cuda"); v = torch.empty((R, N), device="cuda")
+            phia.init_state(A.h, R, 17, x, v)
+            phia.run(A.h, sched, R, 0, T, T, 17, x, v)
+            outs.append((phia.replica_results(A.h, R, N), x.cpu().numpy(), v.cpu().numpy()))
+    for rec, x, v in outs[1:]:
+        for u, w in zip(outs[0][0], rec):
+            assert np.array_equal(u, w)
+        assert np.array_equal(outs[0][1], x) and np.array_equal(outs[0][2], v)
