@@ -74,6 +74,10 @@ typedef struct phia_opts {
     int32_t tile_replicas; /* tensor-core path: replicas per CTA, 4, 8 or 16; 0 = automatic */
     int32_t coupling_mem;  /* tensor-core path, where J stays during a run: 1 = shared memory,
                               2 = tensor memory; 0 = automatic */
+    int32_t tc_kernel;     /* tensor-core path: 1 = resident kernel (all iterations in one launch,
+                              J on chip; N <= 384 e4m3 / 256 bf16), 2 = one launch per iteration
+                              (J streamed by TMA; any N); 0 = automatic */
+    int32_t reserved;      /* must be 0 */
 } phia_opts;
 
 /* Annealing schedule.  No values are given in the paper; every field is explicit. */
@@ -104,7 +108,7 @@ typedef struct phia_stats {
     int32_t path;          /* path actually used (PHIA_PATH_TC / _FP32 / _CSR) */
     int32_t operand;       /* operand actually used (PHIA_OP_E4M3 / _BF16), 0 for other paths */
     int32_t kernel_launches; /* kernels launched by the last run */
-    int32_t reserved;
+    int32_t tc_kernel;     /* tensor-core kernel used (1 resident, 2 per iteration), 0 for other paths */
 } phia_stats;
 
 typedef struct phia_s phia_t;

@@ -56,6 +56,13 @@ struct phia_s {
     int op = 0;
     uint32_t inst = 0;
     int tile_rl = 0, coupling_mem = 0;
+    bool large = false;                 // tensor-core path through the per-iteration kernel
+    void *d_Jop = nullptr;              // couplings in the operand encoding (per-iteration kernel)
+    int Mpad = 0, Kbytes = 0;
+    uint8_t *d_S = nullptr;             // [4][Rpad][Kbytes]
+    int64_t *d_Epart = nullptr;
+    int8_t *d_flags = nullptr;
+    float *d_X = nullptr, *d_V = nullptr;
     int N = 0, frac_bits = 0, W = 0;
     bool csr = false;
     int64_t nnz = 0;
@@ -86,6 +93,8 @@ struct phia_s {
 namespace {
 
 void free_replicas(phia_t *p) {
+    cudaFree(p->d_S); cudaFree(p->d_Epart); cudaFree(p->d_flags); cudaFree(p->d_X); cudaFree(p->d_V);
+    p->d_S = nullptr; p->d_Epart = nullptr; p->d_flags = nullptr; p->d_X = p->d_V = nullptr;
     cudaFree(p->d_x); cudaFree(p->d_v); cudaFree(p->d_s0); cudaFree(p->d_s1); cudaFree(p->d_eacc);
     cudaFree(p->d_best_e); cudaFree(p->d_best_step); cudaFree(p->d_hit); cudaFree(p->d_bits);
     p->d_x = p->d_v = nullptr; p->d_s0 = p->d_s1 = nullptr; p->d_eacc = nullptr;
@@ -106,6 +115,13 @@ int ensure_replicas(phia_t *p, int R) {
         al((void **)&p->d_x, RN * 4); al((void **)&p->d_v, RN * 4);
         al((void **)&p->d_s0, RN); al((void **)&p->d_s1, RN);
     }
+    if (p->large) {
+        const size_t Rp = (size_t)round_up(R, 128);
+        al((void **)&p->d_S, 4 * Rp * p->Kbytes);
+        al((void **)&p->d_Epart, 2 * (size_t)(p->Mpad / 128) * Rp * 8);
+        al((void **)&p->d_flags, 2 * Rp);
+        al((void **)&p->d_X, RN * 4); al((void **)&p->d_V, RN * 4);
+    }
     al((void **)&p->d_eacc, (size_t)R * 8);
     al((void **)&p->d_best_e, (size_t)R * 8);
     al((void **)&p->d_best_step, (size_t)R * 8);
@@ -117,6 +133,11 @@ int ensure_replicas(phia_t *p, int R) {
         return fail(PHIA_ENOMEM, "device allocation for %d replicas failed", R);
     }
     CU(cudaMemsetAsync(p->d_eacc, 0, (size_t)R * 8, p->stream));
+    if (p->large) {
+        const size_t Rp = (size_t)round_up(R, 128);
+        CU(cudaMemsetAsync(p->d_S, 0, 4 * Rp * p->Kbytes, p->stream));   // K and replica padding stay 0
+        CU(cudaMemsetAsync(p->d_flags, 0, 2 * Rp, p->stream));
+    }
     p->R_cap = R;
     return PHIA_OK;
 }
@@ -159,6 +180,12 @@ RunArgs base_args(phia_t *p, int R) {
 }
 
 cudaError_t launch_path(phia_t *p, const RunArgs &a, int *launches) {
+    if (p->path == PHIA_PATH_TC && p->large) {
+        LargeBuffers B;
+        B.Jop = p->d_Jop; B.S = p->d_S; B.Epart = p->d_Epart; B.flags = p->d_flags;
+        B.X = p->d_X; B.V = p->d_V; B.Kbytes = p->Kbytes; B.Mpad = p->Mpad; B.Rpad = round_up(a.R, 128);
+        return launch_tc_large(B, a, p->op, p->stream, launches);
+    }
     if (p->path == PHIA_PATH_TC) return launch_tc_small(a, p->op, p->stream, launches);
     if (p->path == PHIA_PATH_FP32)
         return launch_fp32_run(a, p->d_x, p->d_v, p->d_s0, p->d_s1, p->d_eacc, p->stream, launches);
@@ -226,16 +253,12 @@ int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, 
         if (op == PHIA_OP_E4M3 && max_abs > 16)
             return fail(PHIA_ERANGE, "max |k| = %d is not exact in e4m3 (needs <= 16)", max_abs);
         const int opk = op == PHIA_OP_E4M3 ? kOpE4M3 : kOpBF16;
-        if (N > tc_small_max_n(opk)) {
-            if (o.path == PHIA_PATH_AUTO) {
-                path = PHIA_PATH_FP32;
-                op = 0;
-            } else {
-                return fail(PHIA_ENOTSUP, "tensor-core path handles N <= %d with this operand (N = %d)",
-                            tc_small_max_n(opk), N);
-            }
-        }
+        if (o.tc_kernel == 1 && N > tc_small_max_n(opk))
+            return fail(PHIA_ENOTSUP, "the resident kernel handles N <= %d with this operand (N = %d)",
+                        tc_small_max_n(opk), N);
     }
+    if (o.tc_kernel < 0 || o.tc_kernel > 2) return fail(PHIA_EINVAL, "tc_kernel must be 0, 1 or 2");
+    if (o.reserved != 0) return fail(PHIA_EINVAL, "opts.reserved must be 0");
     int dev_count = 0;
     if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
         return fail(PHIA_ECUDA, "no CUDA device available");
@@ -253,11 +276,21 @@ int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, 
     p->frac_bits = frac_bits;
     p->W = (N + 31) / 32;
     p->max_abs_k = max_abs;
+    if (path == PHIA_PATH_TC)
+        p->large = o.tc_kernel == 2 || (o.tc_kernel == 0 && N > tc_small_max_n(p->op));
     const size_t NN = (size_t)N * N;
     auto cleanup = [&](int code) { phia_destroy(p); return code; };
     if (cudaMalloc((void **)&p->d_Jk, NN) != cudaSuccess) return cleanup(fail(PHIA_ENOMEM, "J allocation failed"));
     if (cudaMemcpyAsync(p->d_Jk, J_k, NN, cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
         return cleanup(fail(PHIA_ECUDA, "J upload failed"));
+    if (p->large) {
+        p->Mpad = round_up(N, 128);
+        p->Kbytes = large_kbytes(N, p->op);
+        if (cudaMalloc(&p->d_Jop, (size_t)p->Mpad * p->Kbytes) != cudaSuccess)
+            return cleanup(fail(PHIA_ENOMEM, "J operand allocation failed"));
+        if (launch_convert_operand(p->d_Jk, N, p->d_Jop, p->Mpad, p->Kbytes, p->op, p->stream) != cudaSuccess)
+            return cleanup(fail(PHIA_ECUDA, "J operand conversion failed"));
+    }
     if (path == PHIA_PATH_FP32) {
         std::vector<float> jf(NN);
         const float q = ldexpf(1.0f, -frac_bits);
@@ -459,6 +492,7 @@ int phia_stats_get(phia_t *p, phia_stats *out) {
     out->path = p->path;
     out->operand = p->op == kOpE4M3 ? PHIA_OP_E4M3 : (p->op == kOpBF16 ? PHIA_OP_BF16 : 0);
     out->kernel_launches = p->last_launches;
+    out->tc_kernel = p->path == PHIA_PATH_TC ? (p->large ? 2 : 1) : 0;
     return PHIA_OK;
 }
 
@@ -467,7 +501,7 @@ void phia_destroy(phia_t *p) {
     cudaSetDevice(p->device);
     cudaStreamSynchronize(p->stream);
     free_replicas(p);
-    cudaFree(p->d_Jk); cudaFree(p->d_Jf); cudaFree(p->d_hk);
+    cudaFree(p->d_Jk); cudaFree(p->d_Jf); cudaFree(p->d_hk); cudaFree(p->d_Jop);
     cudaFree(p->d_rowptr); cudaFree(p->d_col); cudaFree(p->d_val);
     cudaFree(p->d_min_hit); cudaFree(p->d_iters); cudaFree(p->d_err);
     if (p->ev0) cudaEventDestroy(p->ev0);

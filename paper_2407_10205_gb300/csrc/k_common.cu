@@ -1,5 +1,8 @@
 // k_common.cu -- small kernels shared by every path: the Philox draws exposed for
 // testing and the initial state (position and momentum draws, Sec. 2.1 and Eq. A3).
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
 #include "device_common.cuh"
 #include "phia_internal.h"
 
@@ -18,7 +21,27 @@ __global__ void philox_draws_kernel(uint64_t seed, uint32_t inst, uint32_t d, in
     if (v) v[idx] = box_muller(o.z, o.w);
 }
 
+// Couplings k -> exact operand encoding (e4m3 byte or bf16), zero-padded to
+// [Mpad rows][Kbytes], row-major (K contiguous).
+__global__ void convert_operand_kernel(const int8_t *Jk, int N, uint8_t *Jop, int Mpad, int Kbytes, int op) {
+    const int esz = op == kOpE4M3 ? 1 : 2;
+    const int Kel = Kbytes / esz;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)Mpad * Kel) return;
+    const int row = (int)(idx / Kel), col = (int)(idx - (int64_t)row * Kel);
+    const float v = (row < N && col < N) ? (float)Jk[(size_t)row * N + col] : 0.0f;
+    if (op == kOpE4M3) Jop[idx] = __nv_fp8_e4m3(v).__x;
+    else reinterpret_cast<uint16_t *>(Jop)[idx] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
 }  // namespace
+
+cudaError_t launch_convert_operand(const int8_t *Jk, int N, void *Jop, int Mpad, int Kbytes, int op, cudaStream_t st) {
+    const int esz = op == kOpE4M3 ? 1 : 2;
+    const int64_t n = (int64_t)Mpad * (Kbytes / esz);
+    convert_operand_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Jk, N, (uint8_t *)Jop, Mpad, Kbytes, op);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_philox_draws(uint64_t seed, uint32_t inst, uint32_t d, int R, int N, uint32_t *raw, float *x,
                                 float *v, cudaStream_t st) {

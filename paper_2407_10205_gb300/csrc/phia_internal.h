@@ -52,6 +52,20 @@ int tc_small_max_n(int op);
 int tc_small_tile_replicas(int R, int requested);
 cudaError_t launch_tc_small(const RunArgs &a, int op, cudaStream_t st, int *launches);
 
+// tcgen05 per-iteration kernel for dense instances of any size (TMA-staged J and spins).
+struct LargeBuffers {
+    const void *Jop;      // [Mpad][Kbytes] couplings in the operand encoding
+    uint8_t *S;           // [4][Rpad][Kbytes] spin operand buffers (zero padding)
+    int64_t *Epart;       // [2][Mpad/128][Rpad]
+    int8_t *flags;        // [2][Rpad]
+    float *X, *V;         // [R][N] state when the caller gives none
+    int32_t Kbytes, Mpad, Rpad;
+};
+cudaError_t launch_tc_large(const LargeBuffers &B, const RunArgs &a, int op, cudaStream_t st, int *launches);
+cudaError_t launch_convert_operand(const int8_t *Jk, int N, void *Jop, int Mpad, int Kbytes, int op, cudaStream_t st);
+inline int large_kbytes(int N, int op) { return ((N * (op == kOpE4M3 ? 1 : 2)) + 127) / 128 * 128; }
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
 // Plain FP32 per-step path (the comparator).
 cudaError_t launch_fp32_run(const RunArgs &a, float *x, float *v, int8_t *s0, int8_t *s1,
                             int64_t *e_acc, cudaStream_t st, int *launches);

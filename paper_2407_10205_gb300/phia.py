@@ -35,7 +35,8 @@ class PhiaError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("operand", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("instance_id", ctypes.c_uint32), ("stream", ctypes.c_void_p),
-                ("tile_replicas", ctypes.c_int32), ("coupling_mem", ctypes.c_int32)]
+                ("tile_replicas", ctypes.c_int32), ("coupling_mem", ctypes.c_int32),
+                ("tc_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Schedule(ctypes.Structure):
@@ -50,7 +51,7 @@ class Stats(ctypes.Structure):
                 ("best_energy_k", ctypes.c_int64), ("best_replica", ctypes.c_int64),
                 ("best_step", ctypes.c_int64), ("hit_step", ctypes.c_int64), ("hit_replica", ctypes.c_int64),
                 ("device_ms", ctypes.c_float), ("path", ctypes.c_int32), ("operand", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("kernel_launches", ctypes.c_int32), ("tc_kernel", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); every symbol include/phia.h declares
@@ -121,13 +122,14 @@ def schedule(beta0, beta1, eps, gamma, refresh=0, target=None, stop_at_target=Fa
 
 
 MEM_AUTO, MEM_SHARED, MEM_TENSOR = 0, 1, 2
+KERNEL_AUTO, KERNEL_RESIDENT, KERNEL_PER_STEP = 0, 1, 2
 
 
 def opts(path=PATH_AUTO, operand=OP_AUTO, device=0, instance_id=0, stream=None, tile_replicas=0,
-         coupling_mem=MEM_AUTO) -> Opts:
+         coupling_mem=MEM_AUTO, tc_kernel=KERNEL_AUTO) -> Opts:
     s = 0 if stream is None else int(stream)
     return Opts(int(path), int(operand), int(device), int(instance_id) & 0xFFFFFFFF, ctypes.c_void_p(s or None),
-                int(tile_replicas), int(coupling_mem))
+                int(tile_replicas), int(coupling_mem), int(tc_kernel), 0)
 
 
 def create(J_k, h_k, frac_bits=0, o: Opts | None = None):
@@ -228,8 +230,9 @@ class Annealer:
     """One Ising instance on the device; ``anneal`` runs PHIA and returns the best state."""
 
     def __init__(self, J_k=None, h_k=None, frac_bits=0, csr=None, path=PATH_AUTO, operand=OP_AUTO,
-                 device=0, instance_id=0, stream=None, tile_replicas=0, coupling_mem=MEM_AUTO):
-        o = opts(path, operand, device, instance_id, stream, tile_replicas, coupling_mem)
+                 device=0, instance_id=0, stream=None, tile_replicas=0, coupling_mem=MEM_AUTO,
+                 tc_kernel=KERNEL_AUTO):
+        o = opts(path, operand, device, instance_id, stream, tile_replicas, coupling_mem, tc_kernel)
         if csr is not None:
             row_ptr, col, val = csr
             self.n = len(row_ptr) - 1

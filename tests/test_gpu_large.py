@@ -1,0 +1,136 @@
+"""GPU parity tests of the per-iteration tensor-core kernel (TMA-staged J, any N),
+through the C ABI against the oracle and against the resident kernel."""
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2407_10205_gb300 import instances as ins
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _large(phia, d, op, frac=0):
+    return phia.Annealer(d.k, d.kh, frac_bits=frac, path=phia.PATH_TC, operand=op, tc_kernel=phia.KERNEL_PER_STEP)
+
+
+def _field(phia, A, S):
+    R, N = S.shape
+    f = torch.empty((R, N), dtype=torch.int32, device="cuda")
+    e = torch.empty(R, dtype=torch.int64, device="cuda")
+    phia.field(A.h, torch.from_numpy(S).cuda(), f, e)
+    torch.cuda.synchronize()
+    return f.cpu().numpy(), e.cpu().numpy()
+
+
+@pytest.mark.parametrize("N,R,kmax,hmax,op", [
+    (5, 1, 7, 7, 1), (130, 129, 16, 100, 1), (257, 260, 7, 7, 1), (700, 40, 16, 1 << 20, 1),
+    (2000, 130, 1, 0, 1), (150, 3, 127, 127, 2), (640, 129, 127, 31, 2)])
+def test_large_field_bit_exact(gpu_lib, N, R, kmax, hmax, op):
+    phia = gpu_lib
+    d = ins.dense_int(N, kmax, hmax, seed=N + R)
+    S = ins.random_spins(R, N, seed=N * 3 + R)
+    with _large(phia, d, op) as A:
+        f, e = _field(phia, A, S)
+    I, E = o.field_batch(o.Instance(d.kh, k=d.k), S)
+    assert np.array_equal(f, I) and np.array_equal(e, E)
+
+
+@pytest.mark.parametrize("N,kval,op", [(2048, 16, 1), (2048, -16, 1), (8192, 127, 2)])
+def test_large_field_extreme_magnitudes(gpu_lib, N, kval, op):
+    """All products of one sign at the largest exact |k|, N up to 8192: partial sums
+    reach |k| (N - 1) = 1.04e6 in FP32 TMEM accumulation and must stay exact."""
+    phia = gpu_lib
+    k = np.full((N, N), kval, dtype=np.int8)
+    np.fill_diagonal(k, 0)
+    d = ins.Dense(k, np.full(N, (1 << 24) - 1, dtype=np.int32))
+    S = np.ones((3, N), dtype=np.int8)
+    S[1] = -1
+    S[2, ::3] = -1
+    with _large(phia, d, op) as A:
+        f, e = _field(phia, A, S)
+    I, E = o.field_batch(o.Instance(d.kh, k=d.k), S)
+    assert np.array_equal(f, I) and np.array_equal(e, E)
+
+
+def test_large_single_step_matches_oracle(gpu_lib):
+    phia = gpu_lib
+    N, R, eps, gamma, beta = 600, 30, 0.1, 2.0, 0.21
+    d = ins.dense_int(N, 7, 7, seed=11)
+    P = o.Instance(d.kh, k=d.k)
+    x, v = ins.random_state(R, N, seed=12)
+    xn = x.astype(np.float64) + eps * v.astype(np.float64)
+    bad = np.abs(xn) < 1e-3
+    x[bad] = np.where(xn[bad] >= 0, 0.01, -0.01).astype(np.float32)
+    v[bad] = 0.0
+    with _large(phia, d, 1) as A:
+        xt, vt = torch.from_numpy(x).cuda(), torch.from_numpy(v).cuda()
+        phia.run(A.h, phia.schedule(beta, beta, eps, gamma), R, 0, 1, 1, 5, xt, vt)
+        be, bs, _, bits = phia.replica_results(A.h, R, N)
+        xg, vg = xt.cpu().numpy(), vt.cpu().numpy()
+    S = phia.unpack_bits(bits, N)
+    for r in range(R):
+        xo, vo, so, Io, eo = o.step(P, x[r].astype(np.float64), v[r].astype(np.float64), beta, eps, gamma)
+        assert np.array_equal(S[r], so) and be[r] == eo and bs[r] == 0
+        assert np.allclose(xg[r], xo, rtol=1e-6, atol=1e-7)
+        scale = np.abs(v[r]) + eps * (beta * gamma * np.abs(Io) + np.abs(xo))
+        assert np.all(np.abs(vg[r] - vo) <= 1e-5 * np.maximum(scale, 1e-3))
+
+
+@pytest.mark.parametrize("N,op,R", [(200, 1, 50), (130, 2, 140)])
+def test_large_equals_resident_kernel(gpu_lib, N, op, R):
+    """The per-iteration and the resident kernel do the same arithmetic per replica:
+    records and final states are bit-identical."""
+    phia = gpu_lib
+    T = 120
+    d = ins.dense_int(N, 7 if op == 1 else 90, 7, seed=N)
+    sched = phia.schedule(0.01, 0.2, 0.1, 2.0, refresh=30)
+    outs = []
+    for kern in (phia.KERNEL_RESIDENT, phia.KERNEL_PER_STEP):
+        with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, operand=op, tc_kernel=kern) as A:
+            x = torch.empty((R, N), device="cuda"); v = torch.empty((R, N), device="cuda")
+            phia.init_state(A.h, R, 21, x, v)
+            phia.run(A.h, sched, R, 0, T, T, 21, x, v)
+            outs.append((phia.replica_results(A.h, R, N), x.cpu().numpy(), v.cpu().numpy(),
+                         phia.stats_get(A.h).tc_kernel))
+    assert outs[0][3] == 1 and outs[1][3] == 2
+    for u, w in zip(outs[0][0], outs[1][0]):
+        assert np.array_equal(u, w)
+    assert np.array_equal(outs[0][1], outs[1][1]) and np.array_equal(outs[0][2], outs[1][2])
+
+
+def test_large_resume_bit_identical(gpu_lib):
+    phia = gpu_lib
+    N, R, T, a = 700, 130, 60, 23
+    d = ins.sk_pm1(N, 3)
+    sched = phia.schedule(0.01, 0.15, 0.1, 2.0, refresh=10)
+    with _large(phia, d, 1) as A:
+        x1 = torch.empty((R, N), device="cuda"); v1 = torch.empty((R, N), device="cuda")
+        phia.init_state(A.h, R, 9, x1, v1)
+        x2, v2 = x1.clone(), v1.clone()
+        phia.run(A.h, sched, R, 0, T, T, 9, x1, v1)
+        one = phia.replica_results(A.h, R, N)
+        phia.run(A.h, sched, R, 0, a, T, 9, x2, v2, reset_best=True)
+        phia.run(A.h, sched, R, a, 1, T, 9, x2, v2, reset_best=False)
+        phia.run(A.h, sched, R, a + 1, T - a - 1, T, 9, x2, v2, reset_best=False)
+        two = phia.replica_results(A.h, R, N)
+        torch.cuda.synchronize()
+        assert torch.equal(x1, x2) and torch.equal(v1, v2)
+        for u, w in zip(one, two):
+            assert np.array_equal(u, w)
+
+
+def test_large_run_invariants(gpu_lib):
+    """Every returned energy equals Eq. 2 recomputed exactly on the returned spins."""
+    phia = gpu_lib
+    N, R = 520, 140
+    d = ins.dense_int(N, 16, 50, seed=4)
+    P = o.Instance(d.kh, k=d.k)
+    with _large(phia, d, 1) as A:
+        res = A.anneal(phia.schedule(0.005, 0.1, 0.1, 2.0, refresh=40), R, 300, seed=3)
+        be, bs, _, bits = phia.replica_results(A.h, R, N)
+    S = phia.unpack_bits(bits, N)
+    for r in range(R):
+        assert o.energy_exact(P, S[r]) == be[r]
+    assert res.energy_k == be.min() and o.energy_exact(P, res.spins) == res.energy_k
+    assert res.stats.tc_kernel == 2 and res.stats.spin_updates == R * N * 300
