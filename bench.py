@@ -34,19 +34,30 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(N=200, kmax=7, hmax=7, seed=1, replicas=1024, iterations=2000,
-                beta0=0.01, beta1=0.1, eps=0.1, gamma=2.0, refresh=50, run_seed=12345)
-WORKLOAD_NAME = ("N=200 dense, k and kh uniform int [-7,7]; 1024 replicas x 2000 iterations, "
-                 "linear beta 0.01->0.1")
+WORKLOADS = {
+    # configs[1] of the benchmark plan: the default bench workload
+    "dense200": dict(N=200, kind="int", kmax=7, hmax=7, seed=1, replicas=1024, iterations=2000,
+                     beta0=0.01, beta1=0.1, eps=0.1, gamma=2.0, refresh=50, run_seed=12345,
+                     name="N=200 dense, k and kh uniform int [-7,7]; 1024 replicas x 2000 iterations, "
+                          "linear beta 0.01->0.1",
+                     cmp_iters=2000, cpu_replicas=128, cpu_iters=2000),
+    # configs[2]: complete graph N=2000, J in {-1,+1}, h = 0
+    "dense2000": dict(N=2000, kind="pm1", seed=3, replicas=4096, iterations=5000,
+                      beta0=0.005, beta1=0.134, eps=0.1, gamma=2.0, refresh=50, run_seed=777,
+                      name="N=2000 complete graph, J uniform {-1,+1}, h=0; 4096 replicas x 5000 iterations",
+                      cmp_iters=20, cpu_replicas=64, cpu_iters=20),
+}
+WORKLOAD = WORKLOADS["dense200"]
+WORKLOAD_NAME = WORKLOAD["name"]
 METRIC = "spin-updates/s"
 # FP32 operations the update of one spin needs by its formulas (Eqs. 5-8, A7, Eq. 2 via the
 # field): position FMA, sign, field conversion, energy term and accumulate (2), gamma*x,
 # sech^2 via one exp (exp, add, square, divide, scale: 5), beta*gamma*q*sech^2*I (2), -x,
 # *eps, +v.
 ALGO_OPS_PER_UPDATE = 16
-# dram__bytes_read.sum + dram__bytes_write.sum of one tc_small_kernel launch from the
-# committed ncu summary, or None when the kernel changed after the capture.
-KERNEL_TRAFFIC_BYTES = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of each kernel, from the
+# committed ncu summaries under profiles/; absent once a kernel changed after its capture.
+KERNEL_TRAFFIC_BYTES = {}
 
 
 def _dist():
@@ -56,9 +67,11 @@ def _dist():
     return rank, world, local
 
 
-def _instance():
+def _instance(w=None):
     from paper_2407_10205_gb300 import instances as ins
-    w = WORKLOAD
+    w = w or WORKLOAD
+    if w["kind"] == "pm1":
+        return ins.sk_pm1(w["N"], w["seed"])
     return ins.dense_int(w["N"], w["kmax"], w["hmax"], w["seed"])
 
 
@@ -113,21 +126,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(sample_replicas=128):
-    """The FP64 oracle, as it stands, on the host cores: `sample_replicas` replicas of the
-    bench workload for the full 2000 iterations."""
+def cpu_baseline(w=None, sample_replicas=None):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of the workload
+    (`sample_replicas` replicas x the workload's sample iterations)."""
     import oracle
-    w = WORKLOAD
-    d = _instance()
+    w = w or WORKLOAD
+    R = sample_replicas or w["cpu_replicas"]
+    T = w["cpu_iters"]
+    d = _instance(w)
     P = oracle.Instance(d.kh, k=d.k)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    oracle.anneal(P, sample_replicas, w["iterations"], w["run_seed"], 0, w["beta0"], w["beta1"], w["eps"],
+    oracle.anneal(P, R, T, w["run_seed"], 0, w["beta0"], w["beta1"], w["eps"],
                   w["gamma"], refresh=w["refresh"], threads=cores, want_spins=False)
     dt = time.perf_counter() - t0
-    su = sample_replicas * w["N"] * w["iterations"]
+    su = R * w["N"] * T
     return {"value": su / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": f"{sample_replicas} of the 1024 replicas x 2000 iterations ({dt:.1f} s)"}
+            "sample": f"{R} of the {w['replicas']} replicas x {T} of {w['iterations']} iterations ({dt:.1f} s)"}
 
 
 def run_reference(args):
@@ -163,6 +178,38 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def _roofline(w, kernel_ms, stats, peaks, src, clocks):
+    """Roofline of the dominant kernel of the workload (see the design doc for the derivations)."""
+    N, R, T = w["N"], w["replicas"], w["iterations"]
+    su = R * N * T
+    tensor_peak = 2.0 * float(peaks["bf16_tflops"])
+    tensor_achieved = 2.0 * N * su / (kernel_ms * 1e-3) / 1e12
+    tensor = {"achieved": tensor_achieved, "peak": tensor_peak, "unit": "TFLOP/s",
+              "frac": tensor_achieved / tensor_peak, "peak_source": f"{src} bf16 x 2 (nominal e4m3 : bf16 ratio)"}
+    if stats.tc_kernel == 1:
+        # Resident kernel: one launch per run.  The 2N field flops per spin update take a
+        # few hundred tensor cycles per iteration; the time goes to the per-spin FP32
+        # update and the per-iteration dependency chain, so the bound quoted is the FP32
+        # lane-op rate.
+        sm_mhz = clocks.get("sm_max_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+        alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e9
+        achieved = ALGO_OPS_PER_UPDATE * su / (kernel_ms * 1e-3) / 1e9
+        return {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
+                "frac": achieved / alu_peak, "traffic": KERNEL_TRAFFIC_BYTES.get("tc_small_kernel"),
+                "kernel": "tc_small_kernel",
+                "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (derived)", "tensor": tensor}
+    # Per-iteration kernel: per launch it must move x and v in and out (16 B per spin
+    # update), write the next spins (1 B per spin update) and read the spins and J once.
+    launch_ms = kernel_ms / T
+    bytes_per_launch = R * N * 17 + R * N + N * N
+    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": KERNEL_TRAFFIC_BYTES.get("tc_large_step"), "kernel": "tc_large_step",
+            "launch_ms": launch_ms, "algorithmic_bytes_per_launch": bytes_per_launch,
+            "peak_source": f"{src} HBM copy bandwidth", "tensor": tensor}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -173,8 +220,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_2407_10205_gb300 import phia
     phia.load()
-    w = WORKLOAD
-    d = _instance()
+    w = WORKLOADS[args.workload]
+    d = _instance(w)
     N, R, T = w["N"], w["replicas"], w["iterations"]
     sched = phia.schedule(w["beta0"], w["beta1"], w["eps"], w["gamma"], refresh=w["refresh"])
     stream = torch.cuda.Stream()
@@ -201,11 +248,10 @@ def run_ours(args):
                 ev[k][0].record(stream)
                 phia.anneal(A.h, sched, R, T, seed)
                 ev[k][1].record(stream)
-                launches += 1
             barrier()
             t_wall = time.perf_counter() - t_wall
         st = phia.stats_get(A.h)
-        launches *= max(st.kernel_launches, 1)
+        launches = args.steps * st.kernel_launches
         ms = [a.elapsed_time(b) for a, b in ev]
         kernel_ms = float(st.device_ms)
         best_e, _ = phia.best(A.h, N)
@@ -220,7 +266,7 @@ def run_ours(args):
 
     # e2e: public C ABI from host buffers, host<->device copies inside the timed region
     e2e_ms = []
-    for k in range(max(2, min(args.steps, 5))):
+    for k in range(max(2, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, stream=stream.cuda_stream) as B:
@@ -231,62 +277,53 @@ def run_ours(args):
     h2d = N * N + 4 * N
     d2h = 3 * 8 * R + 4 + 4 * ((N + 31) // 32) + 8
 
-    # comparator: the plain FP32 per-instance GPU path, same instance and seeds
+    # comparator: the plain FP32 per-instance GPU path, same instance and seeds; long runs
+    # are timed on their first cmp_iters iterations and scaled (labelled).
+    Tc = min(T, w["cmp_iters"])
     with phia.Annealer(d.k, d.kh, path=phia.PATH_FP32, stream=stream.cuda_stream) as C:
-        phia.anneal(C.h, sched, R, T, seed)
+        sched_c = sched
+        phia.anneal(C.h, sched_c, R, Tc, seed)
         phia.sync(C.h)
         cmp_ms = []
         for _ in range(2):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            phia.anneal(C.h, sched, R, T, seed)
+            phia.anneal(C.h, sched_c, R, Tc, seed)
             e1.record(stream)
             stream.synchronize()
             cmp_ms.append(e0.elapsed_time(e1))
         cmp_best, _ = phia.best(C.h, N)
-    cmp_value = su_step / (min(cmp_ms) * 1e-3)
+    cmp_run_ms = min(cmp_ms) * T / Tc
+    cmp_value = su_step / (cmp_run_ms * 1e-3)
 
     if rank != 0:
         return 0
     peaks, src = _peaks()
     clocks = cs.summary()
-    # Dominant kernel: tc_small_kernel (one launch per run, >99.9% of the step's device
-    # time).  At N = 200 its 2N field flops per spin update run on the tensor pipe in a
-    # few hundred cycles per iteration; the kernel's time goes to the per-spin FP32
-    # update arithmetic and to the per-iteration dependency chain.  The roofline used is
-    # therefore the FP32 lane-op rate: ALGO_OPS_PER_UPDATE algorithmic operations per
-    # spin update (enumerated in the design doc) against 152 SMs x 128 FP32 lanes x SM clock.
-    sm_mhz = clocks.get("sm_max_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e9            # Gop/s
-    achieved = ALGO_OPS_PER_UPDATE * su_step / (kernel_ms * 1e-3) / 1e9
-    tensor_achieved = 2.0 * N * su_step / (kernel_ms * 1e-3) / 1e12
-    tensor_peak = 2.0 * float(peaks["bf16_tflops"])
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "N": N, "replicas": R, "iterations": T, "path": "tc",
-                   "field_operand": "e4m3 (exact for |k| <= 16), fp32 accumulation of integer products",
+        "config": {"workload": w["name"], "N": N, "replicas": R, "iterations": T, "path": "tc",
+                   "tc_kernel": "resident" if st.tc_kernel == 1 else "per-iteration",
+                   "field_operand": ("e4m3" if st.operand == 1 else "bf16")
+                   + " (exact re-encoding of int8 k), fp32 accumulation of integer products",
                    "state": "fp32 x, v", "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas sharded over {world} GPU(s), no collective"},
         "e2e": {"value": su_step / (e2e_step * 1e-3), "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
-                     "frac": achieved / alu_peak, "traffic": KERNEL_TRAFFIC_BYTES,
-                     "kernel": "tc_small_kernel",
-                     "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (derived, see DESIGN.md)",
-                     "tensor": {"achieved": tensor_achieved, "peak": tensor_peak, "unit": "TFLOP/s",
-                                "frac": tensor_achieved / tensor_peak,
-                                "peak_source": f"{src} bf16 x 2 (nominal e4m3 : bf16 ratio)"}},
+        "roofline": _roofline(w, kernel_ms, st, peaks, src, clocks),
         "gpu_launches": launches,
         "clocks": clocks,
         "comparator": {"path": "fp32 per-instance, one launch per step", "value": cmp_value, "unit": METRIC,
-                       "ms_per_step": min(cmp_ms), "best_energy_k": int(cmp_best)},
+                       "ms_per_run": cmp_run_ms,
+                       "timed_iterations": Tc, "scaled": Tc != T,
+                       "best_energy_k_of_timed_iterations": int(cmp_best)},
         "best_energy_k": int(best_e),
         "wall_s_timed": t_wall,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line))
     return 0
 
@@ -297,6 +334,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dense200", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile-replicas", type=int, default=0, help="tensor-core replicas per CTA (0 = auto)")
     ap.add_argument("--profile-only", action="store_true",
@@ -313,8 +351,8 @@ def run_profile(args):
     import torch
     from paper_2407_10205_gb300 import phia
     phia.load()
-    w = WORKLOAD
-    d = _instance()
+    w = WORKLOADS[args.workload]
+    d = _instance(w)
     sched = phia.schedule(w["beta0"], w["beta1"], w["eps"], w["gamma"], refresh=w["refresh"])
     with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, tile_replicas=args.tile_replicas) as A:
         for _ in range(args.warmup + args.steps):

@@ -118,7 +118,7 @@ int ensure_replicas(phia_t *p, int R) {
     if (p->large) {
         const size_t Rp = (size_t)round_up(R, 128);
         al((void **)&p->d_S, 4 * Rp * p->Kbytes);
-        al((void **)&p->d_Epart, 2 * (size_t)(p->Mpad / 128) * Rp * 8);
+        al((void **)&p->d_Epart, 2 * Rp * 8);
         al((void **)&p->d_flags, 2 * Rp);
         al((void **)&p->d_X, RN * 4); al((void **)&p->d_V, RN * 4);
     }
@@ -137,6 +137,7 @@ int ensure_replicas(phia_t *p, int R) {
         const size_t Rp = (size_t)round_up(R, 128);
         CU(cudaMemsetAsync(p->d_S, 0, 4 * Rp * p->Kbytes, p->stream));   // K and replica padding stay 0
         CU(cudaMemsetAsync(p->d_flags, 0, 2 * Rp, p->stream));
+        CU(cudaMemsetAsync(p->d_Epart, 0, 2 * Rp * 8, p->stream));
     }
     p->R_cap = R;
     return PHIA_OK;

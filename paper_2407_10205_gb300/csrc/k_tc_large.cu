@@ -53,7 +53,7 @@ constexpr size_t kSmemBytes = 1024 + kStages * (kStageA + kStageB) + sizeof(Larg
 struct LargeArgs {
     RunArgs a;
     uint8_t *S;         // [4][Rpad][Kbytes] spin operand buffers
-    int64_t *Epart;     // [2][mtiles][Rpad] energy partials by iteration parity
+    int64_t *Epart;     // [2][Rpad] sums of s (I + h) over output tiles, by iteration parity
     int8_t *flags;      // [2][Rpad] improved at an iteration, by parity
     float *X, *V;       // [R][N] state
     int32_t Kbytes, Rpad, mtiles;
@@ -77,13 +77,14 @@ __device__ __forceinline__ bool spin_is_plus(const uint8_t *row, int i) {
     else return (row[2 * i + 1] & 0x80) == 0;
 }
 
-// Record step for replica r at iteration tt (Table 3, state 5): E from the per-tile
-// partials, best/target records, improved flag.
+// Record step for replica r at iteration tt (Table 3, state 5): E from the sum the
+// output tiles accumulated, best/target records, improved flag; the sum slot is cleared
+// for iteration tt + 2.
 __device__ __forceinline__ void settle_replica(const LargeArgs &L, int r, int64_t tt) {
     const RunArgs &a = L.a;
-    const int64_t *ep = L.Epart + (size_t)(tt & 1) * L.mtiles * L.Rpad + r;
-    long long twice = 0;
-    for (int mm = 0; mm < L.mtiles; ++mm) twice += ep[(size_t)mm * L.Rpad];
+    unsigned long long *slot = reinterpret_cast<unsigned long long *>(L.Epart) + (size_t)(tt & 1) * L.Rpad + r;
+    const long long twice = (long long)*slot;
+    *slot = 0ull;
     const long long E = -twice / 2;
     int imp = 0;
     const bool frozen = a.stop_at_target && a.hit_step[r] >= 0;
@@ -195,18 +196,27 @@ __global__ void __launch_bounds__(kThreads, 2)
             const uint8_t *Sb = L.S + (size_t)((t - 2) & 3) * L.Rpad * L.Kbytes;
             const int word = (m * kBM + q4 * 32) >> 5;
             while (todo) {
-                const int j = __ffsll((long long)todo) - 1;
-                todo &= todo - 1;
-                const int r = rb + j;
-                const bool plus = live_i && spin_is_plus<OP>(Sb + (size_t)r * L.Kbytes, i);
-                const uint32_t bits = __ballot_sync(0xffffffffu, plus);
-                if (lane == 0 && word < a.W) a.best_bits[(size_t)r * a.W + word] = bits;
+                // Up to 8 replicas per round, their loads in flight together.
+                int js[8];
+                bool plus[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    js[u] = todo ? __ffsll((long long)todo) - 1 : -1;
+                    if (todo) todo &= todo - 1;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    plus[u] = js[u] >= 0 && live_i && spin_is_plus<OP>(Sb + (size_t)(rb + js[u]) * L.Kbytes, i);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (js[u] < 0) break;
+                    const uint32_t bits = __ballot_sync(0xffffffffu, plus[u]);
+                    if (lane == 0 && word < a.W) a.best_bits[(size_t)(rb + js[u]) * a.W + word] = bits;
+                }
             }
         }
-        // (c) the field of this iteration.
-        const bool ok = mbar_wait_bounded(&sh->accf, 0, kWaitTimeoutNs);
-        if (!ok) sh->timed_out = 1;
-        tc_fence_after();
+        // (c) the field of this iteration.  x and v of a 16-replica chunk are loaded
+        // together (predicated, all in flight at once); chunk 0 before the MMAs finish.
         const int32_t hki = live_i ? a.hk[i] : 0;
         const float bgq = beta_at(t, inv_tm1_of(a.T_total), a.beta0, a.beta1) * (a.gamma * a.q);
         const float eps = a.eps, gamma = a.gamma;
@@ -214,43 +224,73 @@ __global__ void __launch_bounds__(kThreads, 2)
         const bool refresh_next = more && refresh_at(t + 1, a.refresh);
         uint8_t *Sn = L.S + (size_t)((t + 1) & 3) * L.Rpad * L.Kbytes;
         const uint32_t tbase = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(half * 64);
+        const int rc0 = n * kBN + half * 64;   // first replica of this warp's columns
+        float xs[16], vs[16];
+        auto load_chunk = [&](int c) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int r = rc0 + c * 16 + j;
+                const bool lv = live_i && r < R;
+                const size_t idx = (size_t)r * N + i;
+                xs[j] = lv ? L.X[idx] : 0.0f;
+                vs[j] = lv ? L.V[idx] : 0.0f;
+            }
+        };
+        if (!a.field_mode) load_chunk(0);
+        const bool ok = mbar_wait_bounded(&sh->accf, 0, kWaitTimeoutNs);
+        if (!ok) sh->timed_out = 1;
+        tc_fence_after();
 #pragma unroll 1
         for (int c = 0; c < 4; ++c) {
             float acc[16];
             tmem_ld_x16_sync(tbase + c * 16, acc);
+            if (a.field_mode) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int col = half * 64 + c * 16 + j;
-                const int r = n * kBN + col;
-                int32_t part = 0;
-                if (live_i && r < R && ok) {
-                    const size_t idx = (size_t)r * N + i;
-                    const int32_t Ik = __float2int_rn(acc[j]) + hki;        // Eq. 6, exact
-                    if (a.field_mode) {
+                for (int j = 0; j < 16; ++j) {
+                    const int r = rc0 + c * 16 + j;
+                    int32_t part = 0;
+                    if (live_i && r < R && ok) {
+                        const size_t idx = (size_t)r * N + i;
+                        const int32_t Ik = __float2int_rn(acc[j]) + hki;
                         part = (a.spins_in[idx] > 0 ? 1 : -1) * (Ik + hki);
                         if (a.field_out) a.field_out[idx] = Ik;
-                    } else {
-                    float x = L.X[idx], v = L.V[idx];
-                    part = (x >= 0.0f ? 1 : -1) * (Ik + hki);
-                    v = momentum_update(v, x, (float)Ik, eps, bgq, gamma);
+                    }
+                    part = __reduce_add_sync(0xffffffffu, part);
+                    if (lane == 0) sh->part[q4][half * 64 + c * 16 + j] = part;
+                }
+                continue;
+            }
+            if (c > 0) load_chunk(c);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int r = rc0 + c * 16 + j;
+                const bool lv = live_i && r < R && ok;
+                const int32_t Ik = __float2int_rn(acc[j]) + hki;            // Eq. 6, exact
+                float x = xs[j], v = vs[j];
+                int32_t part = lv ? (x >= 0.0f ? 1 : -1) * (Ik + hki) : 0;
+                v = momentum_update(v, x, (float)Ik, eps, bgq, gamma);
+                if (more) {
+                    if (refresh_next && lv) v = draw_v(a.seed, a.inst, (uint32_t)r, (uint32_t)i, (uint32_t)(t + 1));
+                    x = x + eps * v;
+                }
+                if (lv) {
+                    const size_t idx = (size_t)r * N + i;
                     if (more) {
-                        if (refresh_next) v = draw_v(a.seed, a.inst, (uint32_t)r, (uint32_t)i, (uint32_t)(t + 1));
-                        x = x + eps * v;
                         L.X[idx] = x;
                         put_spin_byte<OP>(Sn + (size_t)r * L.Kbytes, i, x >= 0.0f);
                     }
                     L.V[idx] = v;
-                    }
                 }
                 part = __reduce_add_sync(0xffffffffu, part);
-                if (lane == 0) sh->part[q4][col] = part;
+                if (lane == 0) sh->part[q4][half * 64 + c * 16 + j] = part;
             }
         }
         named_barrier_sync(1, 32 * kEpiWarps);
         if (et < kBN) {
             const int r = n * kBN + et;
             const long long s4 = (long long)sh->part[0][et] + sh->part[1][et] + sh->part[2][et] + sh->part[3][et];
-            L.Epart[(size_t)(t & 1) * L.mtiles * L.Rpad + (size_t)m * L.Rpad + r] = s4;
+            atomicAdd(reinterpret_cast<unsigned long long *>(L.Epart) + (size_t)(t & 1) * L.Rpad + r,
+                      (unsigned long long)s4);
         }
     }
     tc_fence_before();
@@ -324,9 +364,9 @@ __global__ void tc_large_field_out(const LargeArgs L) {
     const RunArgs &a = L.a;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= a.R) return;
-    long long twice = 0;
-    for (int mm = 0; mm < L.mtiles; ++mm) twice += L.Epart[(size_t)mm * L.Rpad + r];
-    if (a.energy_out) a.energy_out[r] = -twice / 2;
+    unsigned long long *slot = reinterpret_cast<unsigned long long *>(L.Epart) + r;
+    if (a.energy_out) a.energy_out[r] = -((long long)*slot) / 2;
+    *slot = 0ull;
 }
 
 __global__ void tc_large_count(const LargeArgs L) {
@@ -382,6 +422,8 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
     cudaError_t e = cudaFuncSetAttribute(step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
     const dim3 grid(B.Mpad / kBM, B.Rpad / kBN);
+    e = cudaMemsetAsync(B.Epart, 0, 2 * (size_t)B.Rpad * sizeof(int64_t), st);   // energy sums start at 0
+    if (e != cudaSuccess) return e;
     const int64_t RN = (int64_t)a.R * a.N;
     const unsigned eg = (unsigned)((RN + 255) / 256);
     int n = 0;

@@ -56,7 +56,7 @@ cudaError_t launch_tc_small(const RunArgs &a, int op, cudaStream_t st, int *laun
 struct LargeBuffers {
     const void *Jop;      // [Mpad][Kbytes] couplings in the operand encoding
     uint8_t *S;           // [4][Rpad][Kbytes] spin operand buffers (zero padding)
-    int64_t *Epart;       // [2][Mpad/128][Rpad]
+    int64_t *Epart;       // [2][Rpad], zero between uses
     int8_t *flags;        // [2][Rpad]
     float *X, *V;         // [R][N] state when the caller gives none
     int32_t Kbytes, Mpad, Rpad;
