@@ -179,6 +179,38 @@ int phia_field(phia_t *p, const int8_t *spins, int32_t replicas, int32_t *field_
 int phia_philox_draws(uint64_t seed, uint32_t instance_id, uint32_t d, int32_t replicas,
                       int32_t N, uint32_t *raw, float *x, float *v, void *stream);
 
+/* Run without allocating: the paper has no counterpart to this entry point; it exists
+ * for callers that cannot allocate device memory.  Some programs hand the whole device
+ * to their own memory pool at start-up, so a cudaMalloc from a library would fail or
+ * break the pool's accounting; others run a latency-critical loop in which cudaMalloc
+ * and cudaFree are forbidden because they can synchronise the device and take unbounded
+ * time.  Such callers own every input and output buffer, and this call takes its
+ * scratch (the operand copy of J, the spin buffers, the energy sums) from one array of
+ * 16 MiB compiled into the library, which every GPU that loads the library holds until
+ * the process exits.
+ *
+ * It runs the tensor-core path with one launch per iteration, exactly as phia_run does
+ * on a handle created with tc_kernel = 2, and gives the same results.  All pointers are
+ * device memory on the current CUDA device except sched (host): J_k N*N int8 (symmetric,
+ * zero diagonal -- not checked here), h_k N int32, x and v replicas*N float32 updated in
+ * place, and the records best_energy_k, best_step, hit_step (replicas each) and
+ * best_bits (replicas * ceil(N/32)), which reset_best = 1 initialises.  operand:
+ * PHIA_OP_E4M3 (every |k| <= 16) or PHIA_OP_BF16 (AUTO means BF16).  stream: cudaStream_t
+ * or NULL.  Sizes that need more scratch than the array holds (for example N = 2000 with
+ * e4m3 and more than 1024 replicas) return PHIA_ERANGE.  The call allocates nothing:
+ * no cudaMalloc, cudaFree or allocating library routine.  The first call on a device
+ * looks up the array's device address once (cudaGetSymbolAddress), so make that first
+ * call before any stream capture.  It returns after the work has finished (it
+ * synchronises the stream), with PHIA_ETIMEOUT if a bounded device wait expired.  All
+ * calls share the one array, whose contents the next call overwrites: calls that
+ * overlap on the GPU (other threads, other streams) race and must be serialised by the
+ * caller. */
+int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N, int32_t frac_bits, int32_t operand,
+                     const phia_schedule *sched, int32_t replicas, int64_t t0, int64_t steps,
+                     int64_t total_steps, uint64_t seed, uint32_t instance_id, float *x, float *v,
+                     int64_t *best_energy_k, int64_t *best_step, int64_t *hit_step, uint32_t *best_bits,
+                     int32_t reset_best, void *stream);
+
 /* Wait for all work enqueued on the handle's stream. */
 int phia_sync(phia_t *p);
 

@@ -49,6 +49,11 @@ __global__ void reset_records_kernel(int R, int W, int64_t *best_e, int64_t *bes
 
 }  // namespace
 
+namespace phia {
+// Sets the calling thread's phia_last_error() message (for entry points in other files).
+int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace phia
+
 struct phia_s {
     int device = 0;
     cudaStream_t stream = nullptr;

@@ -66,6 +66,9 @@ cudaError_t launch_convert_operand(const int8_t *Jk, int N, void *Jop, int Mpad,
 inline int large_kbytes(int N, int op) { return ((N * (op == kOpE4M3 ? 1 : 2)) + 127) / 128 * 128; }
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// Thread-local error message of the C ABI.
+int set_last_error(int code, const char *msg);
+
 // Plain FP32 per-step path (the comparator).
 cudaError_t launch_fp32_run(const RunArgs &a, float *x, float *v, int8_t *s0, int8_t *s1,
                             int64_t *e_acc, cudaStream_t st, int *launches);

@@ -69,6 +69,9 @@ SIGNATURES = {
     "phia_field": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
     "phia_philox_draws": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32,
                                          ctypes.c_int32, _P, _P, _P, _P]),
+    "phia_run_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
+                                        ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
+                                        ctypes.c_uint32, _P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
     "phia_sync": (ctypes.c_int, [_P]),
     "phia_destroy": (None, [_P]),
     "phia_last_error": (ctypes.c_char_p, []),
@@ -208,6 +211,17 @@ def philox_draws(seed, instance_id, d, replicas, n, raw=None, x=None, v=None, st
     _check(load().phia_philox_draws(int(seed) & (2**64 - 1), int(instance_id) & 0xFFFFFFFF, int(d),
                                     int(replicas), int(n), _dev_ptr(raw), _dev_ptr(x), _dev_ptr(v),
                                     ctypes.c_void_p(int(stream) if stream else None)))
+
+
+def run_noalloc(J_k, h_k, frac_bits, operand, sched: Schedule, replicas, t0, steps, total_steps, seed, instance_id,
+                x, v, best_energy_k, best_step, hit_step, best_bits, reset_best=True, stream=None):
+    """phia_run_noalloc: every argument a device tensor the caller owns; no allocation."""
+    n = int(h_k.shape[0])
+    _check(load().phia_run_noalloc(_dev_ptr(J_k), _dev_ptr(h_k), n, int(frac_bits), int(operand), ctypes.byref(sched),
+                                   int(replicas), int(t0), int(steps), int(total_steps), int(seed) & (2**64 - 1),
+                                   int(instance_id) & 0xFFFFFFFF, _dev_ptr(x), _dev_ptr(v), _dev_ptr(best_energy_k),
+                                   _dev_ptr(best_step), _dev_ptr(hit_step), _dev_ptr(best_bits),
+                                   1 if reset_best else 0, ctypes.c_void_p(int(stream) if stream else None)))
 
 
 def sync(h):
