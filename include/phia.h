@@ -123,7 +123,8 @@ int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N,
 
 /* Create a sparse instance in CSR form (host arrays): row_ptr[N+1], col[nnz]
  * (0 <= col < N, no self loops), val_k[nnz] int8; the pattern and values must be
- * symmetric.  Stored zeros are allowed. */
+ * symmetric.  Stored zeros are allowed.  Runs on the CSR path (a batch of one); its
+ * replicas run in groups of 256, smaller counts padded with unreported replicas. */
 int phia_create_csr(phia_t **out, const int32_t *row_ptr, const int32_t *col,
                     const int8_t *val_k, const int32_t *h_k, int32_t N, int32_t frac_bits,
                     const phia_opts *opts);
@@ -210,6 +211,52 @@ int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N, int32_t f
                      int64_t total_steps, uint64_t seed, uint32_t instance_id, float *x, float *v,
                      int64_t *best_energy_k, int64_t *best_step, int64_t *hit_step, uint32_t *best_bits,
                      int32_t reset_best, void *stream);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent instances of uneven N annealed together: one launch per iteration
+ * covers every instance (the sparse CSR path; dense descriptors are converted to CSR).
+ * Each instance keeps its own couplings, replicas, records and Philox instance id, so
+ * its result does not depend on the rest of the batch. */
+typedef struct phia_instance_desc {
+    int32_t N;                 /* spins */
+    int32_t frac_bits;         /* J = k 2^-f, h = kh 2^-f */
+    const int8_t *J_k;         /* host, dense N*N (symmetric, zero diagonal), or NULL for CSR */
+    const int32_t *row_ptr;    /* host CSR (used when J_k is NULL): row_ptr[N+1], col, val_k */
+    const int32_t *col;
+    const int8_t *val_k;
+    const int32_t *h_k;        /* host, N int32, |h_k| < 2^24 */
+    uint32_t instance_id;      /* Philox counter word of this instance */
+    int32_t has_target;        /* 1: this instance's own target energy (units of q) */
+    int64_t target_k;
+} phia_instance_desc;
+
+typedef struct phia_batch_s phia_batch_t;
+
+/* Validate and upload `count` instances (copied; the caller keeps its arrays).  opts
+ * may be NULL; opts->path must be PHIA_PATH_AUTO or PHIA_PATH_CSR. */
+int phia_batch_create(phia_batch_t **out, int32_t count, const phia_instance_desc *descs,
+                      const phia_opts *opts);
+
+/* Anneal `replicas` replicas of every instance for `steps` iterations (as phia_anneal
+ * per instance).  The sparse path runs replicas in groups of 256; other counts are
+ * padded with extra replicas that are run but never reported.  Asynchronous. */
+int phia_batch_anneal(phia_batch_t *b, const phia_schedule *sched, int32_t replicas, int64_t steps,
+                      uint64_t seed);
+
+/* Best state of one instance (as phia_best). */
+int phia_batch_best(phia_batch_t *b, int32_t instance, int64_t *energy_k, int8_t *spins);
+
+/* Per-replica records of one instance (as phia_replica_results). */
+int phia_batch_replica_results(phia_batch_t *b, int32_t instance, int32_t replicas,
+                               int64_t *best_energy_k, int64_t *best_step, int64_t *hit_step,
+                               uint32_t *best_bits);
+
+/* Statistics of the last batch run: spin_updates counts every instance; the best and
+ * hit fields describe instance 0. */
+int phia_batch_stats_get(phia_batch_t *b, phia_stats *out);
+
+int phia_batch_sync(phia_batch_t *b);
+void phia_batch_destroy(phia_batch_t *b);
 
 /* Wait for all work enqueued on the handle's stream. */
 int phia_sync(phia_t *p);

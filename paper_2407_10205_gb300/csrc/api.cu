@@ -61,6 +61,7 @@ struct phia_s {
     int op = 0;
     uint32_t inst = 0;
     int tile_rl = 0, coupling_mem = 0;
+    phia_batch_s *batch = nullptr;      // CSR instances: a batch of one
     bool large = false;                 // tensor-core path through the per-iteration kernel
     void *d_Jop = nullptr;              // couplings in the operand encoding (per-iteration kernel)
     int Mpad = 0, Kbytes = 0;
@@ -316,8 +317,29 @@ int phia_create_csr(phia_t **out, const int32_t *row_ptr, const int32_t *col, co
                     const int32_t *h_k, int32_t N, int32_t frac_bits, const phia_opts *opts) {
     int rc = common_create(out, N, frac_bits, opts, h_k);
     if (rc) return rc;
-    return fail(PHIA_ENOTSUP, "CSR instances are not built into this library yet");
-    (void)row_ptr; (void)col; (void)val_k;
+    if (!row_ptr || !col || !val_k) return fail(PHIA_EINVAL, "CSR arrays must not be NULL");
+    phia_opts o{};
+    if (opts) o = *opts;
+    if (o.path != PHIA_PATH_AUTO && o.path != PHIA_PATH_CSR)
+        return fail(PHIA_ENOTSUP, "CSR instances run on the CSR path");
+    phia_instance_desc d{};
+    d.N = N; d.frac_bits = frac_bits; d.row_ptr = row_ptr; d.col = col; d.val_k = val_k; d.h_k = h_k;
+    d.instance_id = o.instance_id;
+    phia_batch_s *b = nullptr;
+    rc = batch_create(&b, 1, &d, &o);
+    if (rc) return rc;
+    phia_t *p = new phia_t();
+    p->device = o.device;
+    p->stream = (cudaStream_t)o.stream;
+    p->path = PHIA_PATH_CSR;
+    p->inst = o.instance_id;
+    p->N = N;
+    p->frac_bits = frac_bits;
+    p->W = (N + 31) / 32;
+    p->csr = true;
+    p->batch = b;
+    *out = p;
+    return PHIA_OK;
 }
 
 static int run_impl(phia_t *p, const phia_schedule *sched, int32_t R, int64_t t0, int64_t steps, int64_t total,
@@ -325,6 +347,8 @@ static int run_impl(phia_t *p, const phia_schedule *sched, int32_t R, int64_t t0
     if (!p) return fail(PHIA_EINVAL, "handle is NULL");
     int rc = check_sched(sched);
     if (rc) return rc;
+    if (p->batch) return batch_run(p->batch, sched, R, t0, steps, total, seed, x_in, x_out, v_in, v_out, reset,
+                                   nullptr, nullptr, nullptr);
     if (R < 1) return fail(PHIA_EINVAL, "replicas must be >= 1");
     if (steps < 1) return fail(PHIA_EINVAL, "steps must be >= 1");
     if (t0 < 0 || total < t0 + steps) return fail(PHIA_EINVAL, "need 0 <= t0 and t0 + steps <= total_steps");
@@ -382,6 +406,8 @@ int phia_init_state(phia_t *p, int32_t replicas, uint64_t seed, float *x, float 
 int phia_field(phia_t *p, const int8_t *spins, int32_t R, int32_t *field_k, int64_t *energy_k) {
     if (!p) return fail(PHIA_EINVAL, "handle is NULL");
     if (R < 1 || !spins) return fail(PHIA_EINVAL, "need replicas >= 1 and device spins");
+    if (p->batch) return batch_run(p->batch, nullptr, R, 0, 1, 1, 0, nullptr, nullptr, nullptr, nullptr, 1, spins,
+                                   field_k, energy_k);
     CU(cudaSetDevice(p->device));
     int rc = ensure_replicas(p, R);
     if (rc) return rc;
@@ -445,6 +471,7 @@ static int pick_result(phia_t *p, const std::vector<int64_t> &be, const std::vec
 
 int phia_best(phia_t *p, int64_t *energy_k, int8_t *spins) {
     if (!p) return fail(PHIA_EINVAL, "handle is NULL");
+    if (p->batch) return batch_best(p->batch, 0, energy_k, spins);
     std::vector<int64_t> be, bs, hs;
     int rc = fetch_records(p, be, bs, hs);
     if (rc) return rc;
@@ -462,6 +489,7 @@ int phia_best(phia_t *p, int64_t *energy_k, int8_t *spins) {
 int phia_replica_results(phia_t *p, int32_t R, int64_t *best_energy_k, int64_t *best_step, int64_t *hit_step,
                          uint32_t *best_bits) {
     if (!p) return fail(PHIA_EINVAL, "handle is NULL");
+    if (p->batch) return batch_replica_results(p->batch, 0, R, best_energy_k, best_step, hit_step, best_bits);
     std::vector<int64_t> be, bs, hs;
     int rc = fetch_records(p, be, bs, hs);
     if (rc) return rc;
@@ -475,6 +503,7 @@ int phia_replica_results(phia_t *p, int32_t R, int64_t *best_energy_k, int64_t *
 
 int phia_stats_get(phia_t *p, phia_stats *out) {
     if (!p || !out) return fail(PHIA_EINVAL, "NULL argument");
+    if (p->batch) return batch_stats(p->batch, 0, out);
     std::vector<int64_t> be, bs, hs;
     int rc = fetch_records(p, be, bs, hs);
     if (rc) return rc;
@@ -504,6 +533,7 @@ int phia_stats_get(phia_t *p, phia_stats *out) {
 
 void phia_destroy(phia_t *p) {
     if (!p) return;
+    if (p->batch) phia_batch_destroy(p->batch);
     cudaSetDevice(p->device);
     cudaStreamSynchronize(p->stream);
     free_replicas(p);

@@ -1,0 +1,336 @@
+// k_csr.cu -- sparse PHIA path: many instances of uneven N in one launch per iteration,
+// the field I = J s + h (Eq. 6) gathered warp-per-row from CSR couplings over
+// bit-packed spins, fused with the update of Eqs. 5, 8 and A7.
+//
+// Layout per instance b (N_b spins, R replicas, R a multiple of 256):
+//   spins   4 rotating buffers of uint32 [N_b][R/32]: bit r%32 of word r/32 of row j is
+//           (s_j of replica r = +1); iteration t reads buffer t%4, writes t+1%4.
+//   x, v    float32 [N_b][R] (spin-major, so a row's 256 replicas are 1 KB contiguous)
+//   best    uint32 [R][ceil(N_b/32)] bit-packed over spins (as on every path)
+// Work unit: a block of 64 consecutive rows of one instance and 256 replicas; a warp
+// takes 8 rows, a lane 8 replicas (one byte of each spin row).
+// For a row i and its entries (j, k): acc_r = sum k [s_j^r = +1], ksum = sum k, so
+// I_r = 2 acc_r - ksum + kh_i (exact integers).  Energy partials s_i (I_i + h_i) are
+// reduced per block in shared memory and added to a per-(instance, replica) int64 sum.
+// Records are lagged as in the dense per-iteration kernel: the launch for iteration t
+// settles t-1 (block 0 of each instance) and copies the spins of t-2 for the replicas
+// that improved then (every block, its 64 rows).
+#include "device_common.cuh"
+#include "phia_internal.h"
+
+namespace phia {
+
+namespace {
+
+constexpr int kRowsPerBlock = 64;
+constexpr int kWarps = 8;
+constexpr int kRowsPerWarp = kRowsPerBlock / kWarps;
+constexpr int kGroup = 256;          // replicas per block (8 per lane)
+
+__device__ __forceinline__ void settle_csr(const CsrArgs &C, const CsrInst &in, int b, int r, int64_t tt) {
+    const RunArgs &a = C.a;
+    const size_t rec = (size_t)in.rec_off + r;
+    unsigned long long *slot =
+        reinterpret_cast<unsigned long long *>(C.Esum) + (size_t)(tt & 1) * C.total_reps + rec;
+    const long long twice = (long long)*slot;
+    *slot = 0ull;
+    const long long E = -twice / 2;
+    int imp = 0;
+    const bool frozen = a.stop_at_target && a.hit_step[rec] >= 0;
+    if (!frozen && E < a.best_e[rec]) {
+        a.best_e[rec] = E;
+        a.best_step[rec] = tt;
+        imp = 1;
+    }
+    const long long target = C.targets ? C.targets[b] : a.target;
+    if (a.has_target && a.hit_step[rec] < 0 && E <= target) a.hit_step[rec] = tt;
+    C.flags[(size_t)(tt & 1) * C.total_reps + rec] = (int8_t)imp;
+    (void)b;
+}
+
+__device__ __forceinline__ const uint32_t *spin_buf(const CsrArgs &C, const CsrInst &in, int64_t tt) {
+    return C.S + (size_t)(tt & 3) * C.total_swords + in.s_off;
+}
+
+__global__ void __launch_bounds__(32 * kWarps) csr_step(const CsrArgs C) {
+    __shared__ int32_t part[kWarps][kGroup];
+    __shared__ uint32_t sbits[kRowsPerBlock][kGroup / 32];
+    const RunArgs &a = C.a;
+    const CsrBlock blk = C.blocks[blockIdx.x];
+    const CsrInst in = C.inst[blk.inst];
+    const int b = blk.inst;
+    const int g = blockIdx.y;                     // replica group of 256
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = in.N, R = C.R, RW = R / 32;
+    const int64_t t = C.t;
+
+    // (a) records of iteration t-1 (block 0 of each instance).
+    if (blk.i0 == 0 && t - 1 >= C.t_first) settle_csr(C, in, b, g * kGroup + tid, t - 1);
+    // (b) best spins of iteration t-2 for the replicas that improved then: this block's
+    //     64 rows of spin bits go through shared memory, one thread per replica.
+    if (t - 2 >= C.t_first) {
+        const int rows = min(kRowsPerBlock, N - blk.i0);
+        const uint32_t *Sb = spin_buf(C, in, t - 2);
+        for (int e = tid; e < kRowsPerBlock * 8; e += 32 * kWarps) {
+            const int row = e >> 3, w = e & 7;
+            sbits[row][w] = row < rows ? Sb[(size_t)(blk.i0 + row) * RW + g * 8 + w] : 0u;
+        }
+        __syncthreads();
+        const int r = g * kGroup + tid;
+        if (C.flags[(size_t)((t - 2) & 1) * C.total_reps + in.rec_off + r]) {
+            const int W = (N + 31) / 32;
+            uint32_t w0 = 0, w1 = 0;
+            for (int row = 0; row < 32; ++row) w0 |= ((sbits[row][tid >> 5] >> (tid & 31)) & 1u) << row;
+            for (int row = 32; row < 64; ++row) w1 |= ((sbits[row][tid >> 5] >> (tid & 31)) & 1u) << (row - 32);
+            uint32_t *dst = C.best_bits + in.bits_off + (size_t)r * W;
+            const int word = blk.i0 / 32;
+            dst[word] = w0;
+            if (word + 1 < W) dst[word + 1] = w1;
+        }
+    }
+
+    // (c) field and update, 8 rows per warp, 8 replicas per lane.
+    const uint8_t *Scur = reinterpret_cast<const uint8_t *>(spin_buf(C, in, t));
+    uint32_t *Snext = const_cast<uint32_t *>(spin_buf(C, in, t + 1));
+    const float bgq = beta_at(t, inv_tm1_of(a.T_total), a.beta0, a.beta1) * (a.gamma * in.q);
+    const float eps = a.eps, gamma = a.gamma;
+    const bool more = t + 1 < C.t_first + a.nsteps;
+    const bool refresh_next = more && refresh_at(t + 1, a.refresh);
+    const int r0 = g * kGroup + lane * 8;          // first replica of this lane
+    int32_t epart[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int q = 0; q < kRowsPerWarp; ++q) {
+        const int i = blk.i0 + warp * kRowsPerWarp + q;
+        if (i >= N) break;
+        const int p_beg = C.row_ptr[in.rp_off + i], p_end = C.row_ptr[in.rp_off + i + 1];
+        int32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int32_t ksum = 0;
+        for (int p0 = p_beg; p0 < p_end; p0 += 32) {
+            const int p = p0 + lane;
+            const int cj = p < p_end ? C.col[in.nz_off + p] : 0;
+            const int kj = p < p_end ? (int)C.val[in.nz_off + p] : 0;
+            const int cnt = min(32, p_end - p0);
+            for (int e0 = 0; e0 < cnt; e0 += 8) {
+                uint32_t bytes[8];
+                int ks[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int c = __shfl_sync(0xffffffffu, cj, (e0 + u) & 31);
+                    ks[u] = __shfl_sync(0xffffffffu, kj, (e0 + u) & 31);
+                    if (e0 + u >= cnt) ks[u] = 0;
+                    bytes[u] = Scur[(size_t)c * (RW * 4) + g * 32 + lane];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    ksum += ks[u];
+#pragma unroll
+                    for (int rr = 0; rr < 8; ++rr) acc[rr] += ((bytes[u] >> rr) & 1u) ? ks[u] : 0;
+                }
+            }
+        }
+        const int32_t hk = C.hk[in.h_off + i];
+        const size_t xo = in.x_off + (size_t)i * R + r0;
+        float4 xa = *reinterpret_cast<const float4 *>(C.X + xo);
+        float4 xb = *reinterpret_cast<const float4 *>(C.X + xo + 4);
+        float4 va = *reinterpret_cast<const float4 *>(C.V + xo);
+        float4 vb = *reinterpret_cast<const float4 *>(C.V + xo + 4);
+        float xs[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+        float vs[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+        uint32_t nbyte = 0;
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+            const int32_t I = 2 * acc[rr] - ksum + hk;                    // Eq. 6, exact
+            epart[rr] += (xs[rr] >= 0.0f ? 1 : -1) * (I + hk);
+            float v = momentum_update(vs[rr], xs[rr], (float)I, eps, bgq, gamma);
+            float x = xs[rr];
+            if (more) {
+                if (refresh_next) v = draw_v(a.seed, in.inst_id, (uint32_t)(r0 + rr), (uint32_t)i, (uint32_t)(t + 1));
+                x = x + eps * v;
+            }
+            xs[rr] = x;
+            vs[rr] = v;
+            nbyte |= (uint32_t)(x >= 0.0f) << rr;
+        }
+        if (more) {
+            *reinterpret_cast<float4 *>(C.X + xo) = make_float4(xs[0], xs[1], xs[2], xs[3]);
+            *reinterpret_cast<float4 *>(C.X + xo + 4) = make_float4(xs[4], xs[5], xs[6], xs[7]);
+            reinterpret_cast<uint8_t *>(Snext)[(size_t)i * (RW * 4) + g * 32 + lane] = (uint8_t)nbyte;
+        }
+        *reinterpret_cast<float4 *>(C.V + xo) = make_float4(vs[0], vs[1], vs[2], vs[3]);
+        *reinterpret_cast<float4 *>(C.V + xo + 4) = make_float4(vs[4], vs[5], vs[6], vs[7]);
+    }
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) part[warp][lane * 8 + rr] = epart[rr];
+    __syncthreads();
+    {
+        long long s = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) s += part[w][tid];
+        atomicAdd(reinterpret_cast<unsigned long long *>(C.Esum) + (size_t)(t & 1) * C.total_reps + in.rec_off +
+                      g * kGroup + tid,
+                  (unsigned long long)s);
+    }
+}
+
+// Initial state (or given, [R][N] per instance), refresh at t0, first position update,
+// spins of iteration t0.  One thread per (instance-spin row, lane of 8 replicas).
+__global__ void csr_prologue(const CsrArgs C) {
+    const RunArgs &a = C.a;
+    const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over total_rows * R / 8
+    const int R = C.R, per_row = R / 8;
+    const int64_t row = gidx / per_row;
+    if (row >= C.total_rows) return;
+    const int l8 = (int)(gidx - row * per_row);
+    // find the instance of this global row (rows are stored instance after instance)
+    int lo = 0, hi = C.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (C.inst[mid].row_base <= row) lo = mid; else hi = mid - 1;
+    }
+    const CsrInst in = C.inst[lo];
+    const int i = (int)(row - in.row_base);
+    uint32_t byte = 0;
+    for (int rr = 0; rr < 8; ++rr) {
+        const int r = l8 * 8 + rr;
+        float x, v;
+        if (C.x_in && r < C.R_real) {
+            x = C.x_in[in.xin_off + (size_t)r * in.N + i];
+            v = C.v_in[in.xin_off + (size_t)r * in.N + i];
+        } else {
+            const U4 o = draw_raw(a.seed, in.inst_id, (uint32_t)r, (uint32_t)i, 0u);
+            x = box_muller(o.x, o.y);
+            v = box_muller(o.z, o.w);
+        }
+        if (refresh_at(a.t0, a.refresh)) v = draw_v(a.seed, in.inst_id, (uint32_t)r, (uint32_t)i, (uint32_t)a.t0);
+        x = x + a.eps * v;
+        C.X[in.x_off + (size_t)i * R + r] = x;
+        C.V[in.x_off + (size_t)i * R + r] = v;
+        byte |= (uint32_t)(x >= 0.0f) << rr;
+    }
+    uint8_t *S = reinterpret_cast<uint8_t *>(const_cast<uint32_t *>(spin_buf(C, in, a.t0)));
+    S[(size_t)i * (R / 8) + l8] = (uint8_t)byte;
+}
+
+// Final state back to [R][N] per instance (caller layout).
+__global__ void csr_export(const CsrArgs C) {
+    const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over total_rows * R
+    const int R = C.R;
+    const int64_t row = gidx / R;
+    if (row >= C.total_rows) return;
+    const int r = (int)(gidx - row * R);
+    int lo = 0, hi = C.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (C.inst[mid].row_base <= row) lo = mid; else hi = mid - 1;
+    }
+    const CsrInst in = C.inst[lo];
+    const int i = (int)(row - in.row_base);
+    if (r >= C.R_real) return;
+    C.x_out[in.xin_off + (size_t)r * in.N + i] = C.X[in.x_off + (size_t)i * R + r];
+    C.v_out[in.xin_off + (size_t)r * in.N + i] = C.V[in.x_off + (size_t)i * R + r];
+}
+
+__global__ void csr_settle_all(const CsrArgs C, int64_t tt) {
+    const int b = blockIdx.x;
+    const CsrInst in = C.inst[b];
+    for (int r = threadIdx.x; r < C.R; r += blockDim.x) settle_csr(C, in, b, r, tt);
+}
+
+// Copies for iterations not handled by a later launch; one thread per (replica, word).
+__global__ void csr_copy_all(const CsrArgs C, int64_t t_from, int64_t t_last) {
+    const int b = blockIdx.y;
+    const CsrInst in = C.inst[b];
+    const int W = (in.N + 31) / 32;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)C.R * W) return;
+    const int r = (int)(idx / W), w = (int)(idx - (int64_t)r * W);
+    for (int64_t tt = t_from; tt <= t_last; ++tt) {
+        if (!C.flags[(size_t)(tt & 1) * C.total_reps + in.rec_off + r]) continue;
+        const uint32_t *Sb = spin_buf(C, in, tt);
+        uint32_t bits = 0;
+        for (int q = 0; q < 32; ++q) {
+            const int i = w * 32 + q;
+            if (i < in.N && ((Sb[(size_t)i * (C.R / 32) + (r >> 5)] >> (r & 31)) & 1u)) bits |= 1u << q;
+        }
+        C.best_bits[in.bits_off + (size_t)r * W + w] = bits;
+    }
+}
+
+// Field only: spins given as int8 [R][N] per instance -> field int32 [R][N], energy [R].
+__global__ void csr_field_only(const CsrArgs C) {
+    const RunArgs &a = C.a;
+    const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over total_rows * R
+    const int R = C.R;
+    const int64_t row = gidx / R;
+    if (row >= C.total_rows) return;
+    const int r = (int)(gidx - row * R);
+    int lo = 0, hi = C.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (C.inst[mid].row_base <= row) lo = mid; else hi = mid - 1;
+    }
+    const CsrInst in = C.inst[lo];
+    const int i = (int)(row - in.row_base);
+    if (r >= C.R_real) return;
+    const int8_t *s = a.spins_in + in.xin_off + (size_t)r * in.N;
+    int32_t I = C.hk[in.h_off + i];
+    for (int p = C.row_ptr[in.rp_off + i]; p < C.row_ptr[in.rp_off + i + 1]; ++p)
+        I += (int32_t)C.val[in.nz_off + p] * s[C.col[in.nz_off + p]];
+    if (a.field_out) a.field_out[in.xin_off + (size_t)r * in.N + i] = I;
+    atomicAdd(reinterpret_cast<unsigned long long *>(C.Esum) + in.rec_off + r,
+              (unsigned long long)(long long)(s[i] * (I + C.hk[in.h_off + i])));
+}
+
+__global__ void csr_field_energy(const CsrArgs C) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= C.total_reps) return;
+    unsigned long long *slot = reinterpret_cast<unsigned long long *>(C.Esum) + idx;
+    const int b = (int)(idx / C.R), r = (int)(idx - (int64_t)b * C.R);
+    if (C.a.energy_out && r < C.R_real) C.a.energy_out[(size_t)b * C.R_real + r] = -((long long)*slot) / 2;
+    *slot = 0ull;
+}
+
+__global__ void csr_count(const CsrArgs C) {
+    if (threadIdx.x == 0 && blockIdx.x == 0)
+        atomicAdd(C.a.replica_iters, (unsigned long long)((long long)C.total_reps * C.a.nsteps));
+}
+
+}  // namespace
+
+cudaError_t launch_csr(const CsrArgs &Cin, cudaStream_t st, int *launches) {
+    CsrArgs C = Cin;
+    C.t_first = C.a.t0;
+    int n = 0;
+    cudaError_t e = cudaMemsetAsync(C.Esum, 0, 2 * (size_t)C.total_reps * sizeof(int64_t), st);
+    if (e != cudaSuccess) return e;
+    if (C.a.field_mode) {
+        const int64_t work = C.total_rows * C.R;
+        csr_field_only<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(C);
+        csr_field_energy<<<(unsigned)((C.total_reps + 255) / 256), 256, 0, st>>>(C);
+        if (launches) *launches += 2;
+        return cudaGetLastError();
+    }
+    const int64_t pw = C.total_rows * (C.R / 8);
+    csr_prologue<<<(unsigned)((pw + 255) / 256), 256, 0, st>>>(C);
+    ++n;
+    const dim3 grid(C.nblocks, C.R / kGroup);
+    for (int64_t t = C.a.t0; t < C.a.t0 + C.a.nsteps; ++t) {
+        C.t = t;
+        csr_step<<<grid, 32 * kWarps, 0, st>>>(C);
+        ++n;
+    }
+    const int64_t t_last = C.a.t0 + C.a.nsteps - 1;
+    csr_settle_all<<<C.count, 256, 0, st>>>(C, t_last);
+    const dim3 cg((unsigned)(((int64_t)C.R * C.max_words + 255) / 256), C.count);
+    csr_copy_all<<<cg, 256, 0, st>>>(C, t_last - 1 >= C.a.t0 ? t_last - 1 : t_last, t_last);
+    csr_count<<<1, 32, 0, st>>>(C);
+    n += 3;
+    if (C.x_out) {
+        const int64_t work = C.total_rows * C.R;
+        csr_export<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(C);
+        ++n;
+    }
+    if (launches) *launches += n;
+    return cudaGetLastError();
+}
+
+}  // namespace phia

@@ -66,6 +66,66 @@ cudaError_t launch_convert_operand(const int8_t *Jk, int N, void *Jop, int Mpad,
 inline int large_kbytes(int N, int op) { return ((N * (op == kOpE4M3 ? 1 : 2)) + 127) / 128 * 128; }
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// Sparse batched path: many CSR instances, one launch per iteration over all of them.
+struct CsrInst {
+    int32_t N;
+    uint32_t inst_id;       // fourth Philox counter word
+    float q;                // 2^-frac_bits
+    int32_t pad;
+    int64_t rp_off;         // into row_ptr (N + 1 entries, values relative to nz_off)
+    int64_t nz_off;         // into col / val
+    int64_t h_off;          // into hk
+    int64_t row_base;       // global index of row 0 (rows are stored instance after instance)
+    int64_t x_off;          // into X, V ([N][R] per instance)
+    int64_t xin_off;        // into caller arrays ([R][N] per instance)
+    int64_t s_off;          // into each spin buffer, in uint32 words ([N][R/32] per instance)
+    int64_t rec_off;        // into per-replica records (R per instance)
+    int64_t bits_off;       // into best_bits (R * ceil(N/32) per instance)
+};
+struct CsrBlock {
+    int32_t inst;
+    int32_t i0;             // first of up to 64 rows
+};
+struct CsrArgs {
+    RunArgs a;              // run parameters; record pointers indexed by rec_off + r
+    const CsrInst *inst;
+    int32_t count;
+    const CsrBlock *blocks;
+    int32_t nblocks;
+    const int32_t *row_ptr; const int32_t *col; const int8_t *val; const int32_t *hk;
+    float *X, *V;
+    const float *x_in, *v_in;
+    float *x_out, *v_out;
+    uint32_t *S;            // 4 rotating spin buffers of total_swords words each
+    int64_t total_swords;
+    int64_t *Esum;          // [2][total_reps]
+    int8_t *flags;          // [2][total_reps]
+    int64_t total_reps;
+    uint32_t *best_bits;
+    const long long *targets;   // per instance, or null (then a.target)
+    int32_t R;              // replicas per instance as run (multiple of 256)
+    int32_t R_real;         // replicas the caller asked for (<= R); the rest pad the groups
+    int32_t max_words;      // max ceil(N/32)
+    int64_t total_rows;
+    int64_t t, t_first;
+};
+cudaError_t launch_csr(const CsrArgs &C, cudaStream_t st, int *launches);
+
+}  // namespace phia
+struct phia_batch_s;
+struct phia_instance_desc;
+struct phia_opts;
+struct phia_schedule;
+struct phia_stats;
+namespace phia {
+int batch_create(phia_batch_s **out, int32_t count, const phia_instance_desc *d, const phia_opts *opts);
+int batch_run(phia_batch_s *b, const phia_schedule *sched, int32_t R_real, int64_t t0, int64_t steps, int64_t total,
+              uint64_t seed, const float *x_in, float *x_out, const float *v_in, float *v_out, int reset,
+              const int8_t *spins_in, int32_t *field_out, int64_t *energy_out);
+int batch_best(phia_batch_s *b, int inst, int64_t *energy_k, int8_t *spins);
+int batch_replica_results(phia_batch_s *b, int inst, int32_t R, int64_t *be, int64_t *bs, int64_t *hs, uint32_t *bits);
+int batch_stats(phia_batch_s *b, int inst, phia_stats *out);
+
 // Thread-local error message of the C ABI.
 int set_last_error(int code, const char *msg);
 

@@ -54,6 +54,13 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int32), ("tc_kernel", ctypes.c_int32)]
 
 
+class InstanceDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("frac_bits", ctypes.c_int32), ("J_k", ctypes.c_void_p),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val_k", ctypes.c_void_p),
+                ("h_k", ctypes.c_void_p), ("instance_id", ctypes.c_uint32), ("has_target", ctypes.c_int32),
+                ("target_k", ctypes.c_int64)]
+
+
 # name -> (restype, argtypes); every symbol include/phia.h declares
 _P = ctypes.c_void_p
 SIGNATURES = {
@@ -72,6 +79,13 @@ SIGNATURES = {
     "phia_run_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
                                         ctypes.c_uint32, _P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
+    "phia_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, _P, _P]),
+    "phia_batch_anneal": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64]),
+    "phia_batch_best": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "phia_batch_replica_results": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P]),
+    "phia_batch_stats_get": (ctypes.c_int, [_P, _P]),
+    "phia_batch_sync": (ctypes.c_int, [_P]),
+    "phia_batch_destroy": (None, [_P]),
     "phia_sync": (ctypes.c_int, [_P]),
     "phia_destroy": (None, [_P]),
     "phia_last_error": (ctypes.c_char_p, []),
@@ -276,3 +290,81 @@ class Annealer:
                 self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many instances annealed together on the sparse path (phia_batch_*).
+
+    ``instances``: objects with ``kh``, ``frac_bits`` and either ``k`` (dense) or
+    ``row_ptr``/``col``/``val`` (CSR), e.g. from ``instances.py``.  ``targets``: optional
+    per-instance target energies (units of q) or None entries."""
+
+    def __init__(self, instances, instance_ids=None, targets=None, device=0, stream=None):
+        self._keep = []
+        descs = (InstanceDesc * len(instances))()
+        self.n = []
+        for k, inst in enumerate(instances):
+            kh = np.ascontiguousarray(inst.kh, dtype=np.int32)
+            self._keep.append(kh)
+            d = descs[k]
+            d.N = kh.shape[0]
+            d.frac_bits = int(getattr(inst, "frac_bits", 0))
+            d.h_k = kh.ctypes.data
+            if getattr(inst, "k", None) is not None:
+                J = np.ascontiguousarray(inst.k, dtype=np.int8)
+                self._keep.append(J)
+                d.J_k = J.ctypes.data
+            else:
+                rp = np.ascontiguousarray(inst.row_ptr, dtype=np.int32)
+                col = np.ascontiguousarray(inst.col, dtype=np.int32)
+                val = np.ascontiguousarray(inst.val, dtype=np.int8)
+                self._keep += [rp, col, val]
+                d.row_ptr, d.col, d.val_k = rp.ctypes.data, col.ctypes.data, val.ctypes.data
+            d.instance_id = k if instance_ids is None else int(instance_ids[k])
+            tg = None if targets is None else targets[k]
+            d.has_target = 0 if tg is None else 1
+            d.target_k = 0 if tg is None else int(tg)
+            self.n.append(int(d.N))
+        o = opts(path=PATH_AUTO, device=device, stream=stream)
+        self.h = ctypes.c_void_p()
+        _check(load().phia_batch_create(ctypes.byref(self.h), len(instances), descs, ctypes.byref(o)))
+        self._keep = None
+
+    def anneal(self, sched: Schedule, replicas: int, steps: int, seed: int):
+        _check(load().phia_batch_anneal(self.h, ctypes.byref(sched), int(replicas), int(steps),
+                                        int(seed) & (2**64 - 1)))
+
+    def best(self, k: int):
+        e = ctypes.c_int64()
+        spins = np.empty(self.n[k], dtype=np.int8)
+        _check(load().phia_batch_best(self.h, int(k), ctypes.byref(e), _np_ptr(spins)))
+        return int(e.value), spins
+
+    def replica_results(self, k: int, replicas: int):
+        W = (self.n[k] + 31) // 32
+        be = np.empty(replicas, dtype=np.int64)
+        bs = np.empty(replicas, dtype=np.int64)
+        hs = np.empty(replicas, dtype=np.int64)
+        bits = np.empty((replicas, W), dtype=np.uint32)
+        _check(load().phia_batch_replica_results(self.h, int(k), int(replicas), _np_ptr(be), _np_ptr(bs),
+                                                 _np_ptr(hs), _np_ptr(bits)))
+        return be, bs, hs, bits
+
+    def stats(self) -> Stats:
+        st = Stats()
+        _check(load().phia_batch_stats_get(self.h, ctypes.byref(st)))
+        return st
+
+    def sync(self):
+        _check(load().phia_batch_sync(self.h))
+
+    def close(self):
+        if self.h:
+            load().phia_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
