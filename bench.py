@@ -46,6 +46,13 @@ WORKLOADS = {
                       beta0=0.005, beta1=0.134, eps=0.1, gamma=2.0, refresh=50, run_seed=777,
                       name="N=2000 complete graph, J uniform {-1,+1}, h=0; 4096 replicas x 5000 iterations",
                       cmp_iters=20, cpu_replicas=64, cpu_iters=20),
+    # configs[3]: 256 Erdos-Renyi instances of uneven N, fixed point (f = 4), one batch
+    "batched_er": dict(kind="batch", count=256, seed=4, replicas=256, iterations=2000,
+                       beta0=0.01, beta1=0.18, eps=0.1, gamma=2.0, refresh=50, run_seed=4242,
+                       name="256 Erdos-Renyi instances, N ~ U[100,3000], density ~ U[0.006,0.06], J = k/16 "
+                            "(k ~ U[-127,127]), h = k/16 (k ~ U[-31,31]); 256 replicas each x 2000 iterations, "
+                            "one batch",
+                       cmp_instances=8, cmp_iters=20, cpu_instances=4, cpu_iters=50),
 }
 WORKLOAD = WORKLOADS["dense200"]
 WORKLOAD_NAME = WORKLOAD["name"]
@@ -210,6 +217,108 @@ def _roofline(w, kernel_ms, stats, peaks, src, clocks):
             "peak_source": f"{src} HBM copy bandwidth", "tensor": tensor}
 
 
+def run_batch(args, w):
+    """Config 4: one phia_batch over all instances; the comparator is the plain FP32
+    per-instance dense path, timed on a sample of instances and scaled by N^2."""
+    import torch
+    import oracle
+    from paper_2407_10205_gb300 import instances as ins
+    from paper_2407_10205_gb300 import phia
+    phia.load()
+    insts = ins.batched_er(w["count"], w["seed"])
+    R, T = w["replicas"], w["iterations"]
+    sched = phia.schedule(w["beta0"], w["beta1"], w["eps"], w["gamma"], refresh=w["refresh"])
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    Ns = np.array([c.n for c in insts])
+    nnz = np.array([c.nnz for c in insts])
+    su_step = int(R * T * Ns.sum())
+    with phia.Batch(insts, stream=stream.cuda_stream) as B:
+        for _ in range(args.warmup):
+            B.anneal(sched, R, T, w["run_seed"])
+            B.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        with ClockSampler(0) as cs:
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                torch.cuda.current_stream().synchronize()
+                ev[k][0].record(stream)
+                B.anneal(sched, R, T, w["run_seed"])
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+        st = B.stats()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        best0 = B.best(0)[0]
+    ms_per_step = sum(ms) / len(ms)
+    value = su_step / (ms_per_step * 1e-3)
+    # e2e: batch creation from host arrays + anneal + every instance's best
+    t0 = time.perf_counter()
+    with phia.Batch(insts, stream=stream.cuda_stream) as B2:
+        B2.anneal(sched, R, T, w["run_seed"])
+        for k in range(len(insts)):
+            B2.best(k)
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    h2d = int(sum(4 * (c.n + 1) + 5 * c.nnz + 4 * c.n for c in insts))
+    d2h = int(sum(3 * 8 * R + 4 * ((c.n + 31) // 32) + c.n for c in insts))
+    # comparator on a sample
+    g = np.random.default_rng(0)
+    sample = sorted(g.choice(len(insts), size=w["cmp_instances"], replace=False).tolist())
+    per_n2 = []
+    for k in sample:
+        dd = insts[k].to_dense()
+        with phia.Annealer(dd.k, dd.kh, frac_bits=dd.frac_bits, path=phia.PATH_FP32, stream=stream.cuda_stream) as C:
+            phia.anneal(C.h, sched, R, w["cmp_iters"], w["run_seed"])
+            phia.sync(C.h)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            phia.anneal(C.h, sched, R, w["cmp_iters"], w["run_seed"])
+            e1.record(stream)
+            stream.synchronize()
+            per_n2.append(e0.elapsed_time(e1) / w["cmp_iters"] / dd.n ** 2)
+    cmp_ms = float(np.mean(per_n2)) * float((Ns.astype(np.float64) ** 2).sum()) * T
+    # CPU baseline on a sample
+    cores = os.cpu_count() or 1
+    tc0 = time.perf_counter()
+    su_cpu = 0
+    for k in range(w["cpu_instances"]):
+        c = insts[k]
+        P = oracle.Instance(c.kh, row_ptr=c.row_ptr, col=c.col, val=c.val, frac_bits=c.frac_bits)
+        oracle.anneal(P, R, w["cpu_iters"], w["run_seed"], k, w["beta0"], w["beta1"], w["eps"], w["gamma"],
+                      refresh=w["refresh"], threads=cores, want_spins=False)
+        su_cpu += R * c.n * w["cpu_iters"]
+    dt_cpu = time.perf_counter() - tc0
+    peaks, src = _peaks()
+    launch_ms = float(st.device_ms) / T
+    bytes_launch = float(R * Ns.sum() * (16 + 1.0 / 8) + 5 * nnz.sum() * max(1, R // 256))
+    achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "fp32", "data": "synthetic",
+        "config": {"workload": w["name"], "instances": len(insts), "total_spins": int(Ns.sum()),
+                   "nnz": int(nnz.sum()), "replicas": R, "iterations": T, "path": "csr batch",
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "e2e": {"value": su_step / (e2e_ms * 1e-3), "unit": METRIC, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                     "frac": achieved / float(peaks["hbm_gbs"]), "traffic": KERNEL_TRAFFIC_BYTES.get("csr_step"),
+                     "kernel": "csr_step", "launch_ms": launch_ms, "algorithmic_bytes_per_launch": bytes_launch,
+                     "peak_source": f"{src} HBM copy bandwidth"},
+        "gpu_launches": args.steps * st.kernel_launches,
+        "clocks": cs.summary(),
+        "comparator": {"path": "fp32 per-instance dense, one launch per step", "value": su_step / (cmp_ms * 1e-3),
+                       "unit": METRIC, "ms_per_run": cmp_ms,
+                       "scaled": f"{w['cmp_instances']} instances x {w['cmp_iters']} iterations, time per N^2"},
+        "best_energy_k_instance0": int(best0),
+        "cpu_baseline": {"value": su_cpu / dt_cpu, "unit": METRIC, "cores": cores, "kind": "oracle",
+                         "sample": f"{w['cpu_instances']} instances x {R} replicas x {w['cpu_iters']} iterations "
+                                   f"({dt_cpu:.1f} s)"},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -221,6 +330,8 @@ def run_ours(args):
     from paper_2407_10205_gb300 import phia
     phia.load()
     w = WORKLOADS[args.workload]
+    if w["kind"] == "batch":
+        return run_batch(args, w)
     d = _instance(w)
     N, R, T = w["N"], w["replicas"], w["iterations"]
     sched = phia.schedule(w["beta0"], w["beta1"], w["eps"], w["gamma"], refresh=w["refresh"])
@@ -352,6 +463,16 @@ def run_profile(args):
     from paper_2407_10205_gb300 import phia
     phia.load()
     w = WORKLOADS[args.workload]
+    if w["kind"] == "batch":
+        from paper_2407_10205_gb300 import instances as ins
+        sched = phia.schedule(w["beta0"], w["beta1"], w["eps"], w["gamma"], refresh=w["refresh"])
+        with phia.Batch(ins.batched_er(w["count"], w["seed"])) as B:
+            for _ in range(args.warmup + args.steps):
+                B.anneal(sched, w["replicas"], w["iterations"], w["run_seed"])
+                B.sync()
+            st = B.stats()
+        print(json.dumps({"profile_only": True, "device_ms_last": st.device_ms, "launches_per_run": st.kernel_launches}))
+        return 0
     d = _instance(w)
     sched = phia.schedule(w["beta0"], w["beta1"], w["eps"], w["gamma"], refresh=w["refresh"])
     with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, tile_replicas=args.tile_replicas) as A:

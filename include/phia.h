@@ -258,6 +258,72 @@ int phia_batch_stats_get(phia_batch_t *b, phia_stats *out);
 int phia_batch_sync(phia_batch_t *b);
 void phia_batch_destroy(phia_batch_t *b);
 
+/* ---------------------------------------------------------------- serving
+ * A request loop with continuous batching.  Requests (an instance, a schedule, a replica
+ * count, a step cap, a seed, a target energy) are queued on submission and admitted in
+ * arrival order as soon as one of max_inflight slots and enough of the device-memory
+ * budget are free; while some run, later arrivals are admitted into freed slots.  Each
+ * admitted request keeps its couplings and replica state on the device and runs in
+ * chunks of chunk_iters iterations on its slot's own stream, so requests overlap on the
+ * GPU; it ends when a chunk shows its target reached (stop at target) or the step cap
+ * spent.  A request's result depends only on the request, not on the slot or the mix.
+ * Dense instances run on the tensor-core path, CSR instances on the CSR path.  The
+ * server is thread-safe: submit and poll from any thread. */
+typedef struct phia_server_opts {
+    int32_t device;
+    int32_t max_inflight;      /* slots (1..256), one CUDA stream each */
+    int64_t hbm_budget_bytes;  /* device memory the admitted requests may hold together */
+    int32_t chunk_iters;       /* iterations per launch chunk (target checked in between) */
+    int32_t reserved;          /* must be 0 */
+} phia_server_opts;
+
+typedef struct phia_request_status {
+    int32_t state;             /* 0 queued, 1 running, 2 done, < 0 a PHIA_E* code */
+    int32_t hit;               /* 1: the target was reached */
+    int64_t energy_k;          /* best energy (the earliest hit when the target was reached) */
+    int64_t hit_step;          /* first iteration reaching the target, or -1 */
+    int64_t steps_run;         /* iterations run */
+    double t_submit_s;         /* times since server creation (steady clock), -1 if not yet */
+    double t_admit_s;
+    double t_done_s;
+    int32_t path;              /* path that ran it */
+    int32_t reserved;
+} phia_request_status;
+
+typedef struct phia_server_stats {
+    int64_t completed;         /* requests done */
+    int64_t hits;              /* requests that reached their target */
+    int64_t spin_updates;      /* replicas * N * iterations over completed requests */
+    double ttt_p50_s;          /* time to target from arrival (submit), over hits */
+    double ttt_p99_s;
+    double ttt_admit_p50_s;    /* time to target from admission, over hits */
+    double ttt_admit_p99_s;
+    double elapsed_s;          /* since server creation */
+    int64_t used_bytes;        /* device memory currently held by admitted requests */
+} phia_server_stats;
+
+typedef struct phia_server_s phia_server_t;
+
+int phia_server_create(phia_server_t **out, const phia_server_opts *opts);
+
+/* Queue a request (the instance is copied; the caller keeps its arrays).  The
+ * instance's has_target/target_k, when set, override the schedule's target; stop at
+ * target is always on.  Returns its id in *request_id.  PHIA_ENOMEM if the request
+ * alone needs more than the whole budget. */
+int phia_server_submit(phia_server_t *s, const phia_instance_desc *inst, const phia_schedule *sched,
+                       int32_t replicas, int64_t step_cap, uint64_t seed, int64_t *request_id);
+
+/* Status of a request; spins (host, N int8, may be NULL) receive the best state once done. */
+int phia_server_poll(phia_server_t *s, int64_t request_id, phia_request_status *status, int8_t *spins);
+
+/* Block until every submitted request is done (PHIA_ETIMEOUT after timeout_ms). */
+int phia_server_wait_all(phia_server_t *s, int64_t timeout_ms);
+
+int phia_server_stats_get(phia_server_t *s, phia_server_stats *out);
+
+/* Stop the loop, free every request's device memory and the streams. */
+void phia_server_destroy(phia_server_t *s);
+
 /* Wait for all work enqueued on the handle's stream. */
 int phia_sync(phia_t *p);
 

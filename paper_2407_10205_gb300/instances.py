@@ -81,12 +81,22 @@ def dense_int(n: int, kmax: int, hmax: int, seed: int, frac_bits: int = 0) -> De
 
 
 def erdos_renyi(n: int, density: float, kmax: int, hmax: int, frac_bits: int, seed: int) -> Csr:
-    """Erdos-Renyi graph G(n, p): each pair i<j is an edge with probability p; an edge
-    carries k uniform in [-kmax, kmax] (a drawn k = 0 is kept as a stored zero)."""
+    """Erdos-Renyi graph G(n, p): each pair i<j is an edge with probability p, drawn as a
+    Binomial number of distinct pair indices; an edge carries k uniform in [-kmax, kmax]
+    (a drawn k = 0 is kept as a stored zero)."""
     g = _rng(seed)
-    iu, ju = np.triu_indices(n, 1)
-    keep = g.random(iu.shape[0]) < density
-    iu, ju = iu[keep], ju[keep]
+    M = n * (n - 1) // 2
+    m = int(g.binomial(M, density)) if M > 0 else 0
+    lin = np.sort(g.choice(M, size=m, replace=False)) if m > 0 else np.zeros(0, dtype=np.int64)
+    # linear index l -> (i, j), pairs in row-major upper-triangle order; row i starts at
+    # off(i) = i (2n - i - 1) / 2
+    lin = lin.astype(np.int64)
+    i = np.floor(((2 * n - 1) - np.sqrt((2.0 * n - 1) ** 2 - 8.0 * lin)) / 2).astype(np.int64)
+    off = lambda r: r * (2 * n - r - 1) // 2
+    i = np.where(off(i + 1) <= lin, i + 1, i)
+    i = np.where(off(i) > lin, i - 1, i)
+    j = lin - off(i) + i + 1
+    iu, ju = i, j
     w = g.integers(-kmax, kmax + 1, size=iu.shape[0]).astype(np.int8)
     kh = g.integers(-hmax, hmax + 1, size=n).astype(np.int32)
     rows = np.concatenate([iu, ju])
@@ -94,7 +104,7 @@ def erdos_renyi(n: int, density: float, kmax: int, hmax: int, frac_bits: int, se
     vals = np.concatenate([w, w])
     order = np.lexsort((cols, rows))
     rows, cols, vals = rows[order], cols[order], vals[order]
-    row_ptr = np.zeros(n + 1, dtype=np.int32)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.add.at(row_ptr, rows + 1, 1)
     row_ptr = np.cumsum(row_ptr).astype(np.int32)
     return Csr(row_ptr, cols.astype(np.int32), vals, kh, frac_bits)

@@ -61,6 +61,24 @@ class InstanceDesc(ctypes.Structure):
                 ("target_k", ctypes.c_int64)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_inflight", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
+                ("chunk_iters", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class RequestStatus(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("hit", ctypes.c_int32), ("energy_k", ctypes.c_int64),
+                ("hit_step", ctypes.c_int64), ("steps_run", ctypes.c_int64), ("t_submit_s", ctypes.c_double),
+                ("t_admit_s", ctypes.c_double), ("t_done_s", ctypes.c_double), ("path", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("hits", ctypes.c_int64), ("spin_updates", ctypes.c_int64),
+                ("ttt_p50_s", ctypes.c_double), ("ttt_p99_s", ctypes.c_double), ("ttt_admit_p50_s", ctypes.c_double),
+                ("ttt_admit_p99_s", ctypes.c_double), ("elapsed_s", ctypes.c_double), ("used_bytes", ctypes.c_int64)]
+
+
 # name -> (restype, argtypes); every symbol include/phia.h declares
 _P = ctypes.c_void_p
 SIGNATURES = {
@@ -86,6 +104,12 @@ SIGNATURES = {
     "phia_batch_stats_get": (ctypes.c_int, [_P, _P]),
     "phia_batch_sync": (ctypes.c_int, [_P]),
     "phia_batch_destroy": (None, [_P]),
+    "phia_server_create": (ctypes.c_int, [ctypes.POINTER(_P), _P]),
+    "phia_server_submit": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, _P]),
+    "phia_server_poll": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P]),
+    "phia_server_wait_all": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "phia_server_stats_get": (ctypes.c_int, [_P, _P]),
+    "phia_server_destroy": (None, [_P]),
     "phia_sync": (ctypes.c_int, [_P]),
     "phia_destroy": (None, [_P]),
     "phia_last_error": (ctypes.c_char_p, []),
@@ -361,6 +385,74 @@ class Batch:
     def close(self):
         if self.h:
             load().phia_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _desc_of(inst, instance_id=0, target=None):
+    """InstanceDesc for a Dense/Csr instance; returns (desc, arrays kept alive)."""
+    keep = []
+    d = InstanceDesc()
+    kh = np.ascontiguousarray(inst.kh, dtype=np.int32)
+    keep.append(kh)
+    d.N = kh.shape[0]
+    d.frac_bits = int(getattr(inst, "frac_bits", 0))
+    d.h_k = kh.ctypes.data
+    if getattr(inst, "k", None) is not None:
+        J = np.ascontiguousarray(inst.k, dtype=np.int8)
+        keep.append(J)
+        d.J_k = J.ctypes.data
+    else:
+        rp = np.ascontiguousarray(inst.row_ptr, dtype=np.int32)
+        col = np.ascontiguousarray(inst.col, dtype=np.int32)
+        val = np.ascontiguousarray(inst.val, dtype=np.int8)
+        keep += [rp, col, val]
+        d.row_ptr, d.col, d.val_k = rp.ctypes.data, col.ctypes.data, val.ctypes.data
+    d.instance_id = int(instance_id) & 0xFFFFFFFF
+    d.has_target = 0 if target is None else 1
+    d.target_k = 0 if target is None else int(target)
+    return d, keep
+
+
+class Server:
+    """The continuous-batching request loop (phia_server_*)."""
+
+    def __init__(self, max_inflight=8, hbm_budget_bytes=8 << 30, chunk_iters=100, device=0):
+        o = ServerOpts(int(device), int(max_inflight), int(hbm_budget_bytes), int(chunk_iters), 0)
+        self.h = ctypes.c_void_p()
+        _check(load().phia_server_create(ctypes.byref(self.h), ctypes.byref(o)))
+        self.n = {}
+
+    def submit(self, inst, sched: Schedule, replicas, step_cap, seed, instance_id=0, target=None) -> int:
+        d, keep = _desc_of(inst, instance_id, target)
+        rid = ctypes.c_int64()
+        _check(load().phia_server_submit(self.h, ctypes.byref(d), ctypes.byref(sched), int(replicas), int(step_cap),
+                                         int(seed) & (2**64 - 1), ctypes.byref(rid)))
+        self.n[rid.value] = int(d.N)
+        return int(rid.value)
+
+    def poll(self, rid: int, want_spins=False):
+        st = RequestStatus()
+        spins = np.empty(self.n[rid], dtype=np.int8) if want_spins else None
+        _check(load().phia_server_poll(self.h, int(rid), ctypes.byref(st), _np_ptr(spins)))
+        return st, spins
+
+    def wait_all(self, timeout_ms=600_000):
+        _check(load().phia_server_wait_all(self.h, int(timeout_ms)))
+
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        _check(load().phia_server_stats_get(self.h, ctypes.byref(st)))
+        return st
+
+    def close(self):
+        if self.h:
+            load().phia_server_destroy(self.h)
             self.h = None
 
     def __enter__(self):
