@@ -53,6 +53,12 @@ WORKLOADS = {
                             "(k ~ U[-127,127]), h = k/16 (k ~ U[-31,31]); 256 replicas each x 2000 iterations, "
                             "one batch",
                        cmp_instances=8, cmp_iters=20, cpu_instances=4, cpu_iters=50),
+    # configs[4]: serving stream, Poisson arrivals at 200/s over a pool of seeded instances
+    "serving": dict(kind="serving", pool=32, pool_seed=5, requests=400, arrival_seed=11, rate_hz=200.0,
+                    replicas=256, step_cap=5000, max_inflight=16, budget_gb=64, chunk_iters=100,
+                    cmp_requests=60, cmp_wall_s=90.0,
+                    name="serving: Poisson 200/s, N log-uniform [64,8192], half dense {-1,+1}, half sparse "
+                         "f=8 density 0.01; 256 replicas, step cap 5000, target = oracle best (4 x 200)"),
 }
 WORKLOAD = WORKLOADS["dense200"]
 WORKLOAD_NAME = WORKLOAD["name"]
@@ -319,6 +325,85 @@ def run_batch(args, w):
     return 0
 
 
+def _serve_stream(phia, pool, targets, arrivals, w, path, wall_cap_s=None):
+    """Replay an arrival stream against a server; returns per-request statuses and stats."""
+    import threading
+    from paper_2407_10205_gb300 import schedules
+    scheds = []
+    for inst in pool:
+        b0, b1, eps, gamma, refresh = schedules.suggest_schedule(inst)
+        scheds.append(phia.schedule(b0, b1, eps, gamma, refresh=refresh))
+    S = phia.Server(max_inflight=w["max_inflight"], hbm_budget_bytes=int(w["budget_gb"] * (1 << 30)),
+                    chunk_iters=w["chunk_iters"], path=path)
+    ids = []
+    t0 = time.perf_counter()
+
+    def submitter():
+        for (ta, k, sd) in arrivals:
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(S.submit(pool[k], scheds[k], w["replicas"], w["step_cap"], sd, instance_id=k,
+                                target=targets[k]))
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    try:
+        S.wait_all(timeout_ms=int((wall_cap_s or 3600) * 1000))
+        complete = True
+    except phia.PhiaError:
+        complete = False
+    sts = [S.poll(r)[0] for r in ids]
+    st = S.stats()
+    S.close()
+    return sts, st, complete
+
+
+def run_serving(args, w):
+    """Config 5: a stream of requests through the continuous-batching server."""
+    import torch
+    from paper_2407_10205_gb300 import instances as ins
+    from paper_2407_10205_gb300 import phia
+    phia.load()
+    with open(os.path.join(ROOT, "tests", "golden", "serving_targets.json")) as f:
+        tdoc = json.load(f)
+    pool = ins.serving_pool(w["pool"], w["pool_seed"])
+    targets = [e["target_k"] for e in tdoc["entries"]]
+    arrivals = ins.serving_arrivals(w["requests"], w["arrival_seed"], len(pool), w["rate_hz"])
+    # warm-up: one request of each pool entry (builds kernels, loads modules)
+    _serve_stream(phia, pool, targets, [(0.0, k, 1) for k in range(len(pool))], w, phia.PATH_AUTO)
+    with ClockSampler(0) as cs:
+        sts, st, complete = _serve_stream(phia, pool, targets, arrivals, w, phia.PATH_AUTO)
+    done = [s for s in sts if s.state == 2]
+    span = max(s.t_done_s for s in done) - min(s.t_submit_s for s in sts)
+    value = st.spin_updates / span
+    cmp_arr = arrivals[: w["cmp_requests"]]
+    csts, cst, ccomplete = _serve_stream(phia, pool, targets, cmp_arr, w, phia.PATH_FP32, w["cmp_wall_s"])
+    cdone = [s for s in csts if s.state == 2]
+    ours_first = _serve_stream(phia, pool, targets, cmp_arr, w, phia.PATH_AUTO)[1]
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "fp32", "data": "synthetic",
+        "config": {"workload": w["name"], "requests": len(arrivals), "pool": len(pool),
+                   "max_inflight": w["max_inflight"], "budget_gb": w["budget_gb"], "chunk_iters": w["chunk_iters"]},
+        "serving": {"completed": st.completed, "hits": st.hits, "ttt_p50_s": st.ttt_p50_s, "ttt_p99_s": st.ttt_p99_s,
+                    "ttt_admit_p50_s": st.ttt_admit_p50_s, "ttt_admit_p99_s": st.ttt_admit_p99_s,
+                    "span_s": span, "spin_updates": st.spin_updates, "all_done": complete},
+        "comparator": {"path": "fp32 per-instance (same server, PHIA_PATH_FP32)", "requests": len(cmp_arr),
+                       "completed": cst.completed, "hits": cst.hits, "ttt_p50_s": cst.ttt_p50_s,
+                       "ttt_p99_s": cst.ttt_p99_s, "all_done_within_s": w["cmp_wall_s"] if ccomplete else None,
+                       "ours_on_same_requests": {"ttt_p50_s": ours_first.ttt_p50_s, "ttt_p99_s": ours_first.ttt_p99_s,
+                                                 "hits": ours_first.hits}},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "note": "serving is end to end by construction: host instances in, results out"},
+        "clocks": cs.summary(),
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -332,6 +417,8 @@ def run_ours(args):
     w = WORKLOADS[args.workload]
     if w["kind"] == "batch":
         return run_batch(args, w)
+    if w["kind"] == "serving":
+        return run_serving(args, w)
     d = _instance(w)
     N, R, T = w["N"], w["replicas"], w["iterations"]
     sched = phia.schedule(w["beta0"], w["beta1"], w["eps"], w["gamma"], refresh=w["refresh"])

@@ -274,7 +274,8 @@ typedef struct phia_server_opts {
     int32_t max_inflight;      /* slots (1..256), one CUDA stream each */
     int64_t hbm_budget_bytes;  /* device memory the admitted requests may hold together */
     int32_t chunk_iters;       /* iterations per launch chunk (target checked in between) */
-    int32_t reserved;          /* must be 0 */
+    int32_t path;              /* PHIA_PATH_AUTO (dense: tensor core, CSR: CSR path) or
+                                  PHIA_PATH_FP32 (every request on the plain FP32 path) */
 } phia_server_opts;
 
 typedef struct phia_request_status {

@@ -86,11 +86,13 @@ double secs(Clock::time_point a, Clock::time_point b) {
 }
 
 // Device bytes a request keeps resident (couplings, operands, replica state, records).
-int64_t estimate_bytes(const Request &r) {
+int64_t estimate_bytes(const Request &r, bool fp32) {
     const int64_t N = r.N, R = std::max(r.replicas, 1);
     const int64_t Rp = (R + 255) / 256 * 256;
     int64_t b = 2 * R * N * 4 + 3 * Rp * 8 + Rp * ((N + 31) / 32) * 4 + N * 4;   // caller x, v; records
-    if (!r.J.empty()) {
+    if (fp32) {
+        b += N * N * 5 + 2 * R * N + R * N * 8;                       // int8 + FP32 J, spins, state
+    } else if (!r.J.empty()) {
         b += N * N;                                                   // int8 J
         const int64_t Kb = (N * 2 + 127) / 128 * 128, Mp = (N + 127) / 128 * 128;
         b += Mp * Kb + 4 * ((R + 127) / 128 * 128) * Kb + R * N * 8;   // operand, spin buffers, state
@@ -157,7 +159,16 @@ int admit(phia_server_s *S, Request &r, int slot) {
     o.instance_id = r.instance_id;
     o.stream = S->streams[slot];
     int rc;
-    if (!r.J.empty()) {
+    if (S->opts.path == PHIA_PATH_FP32) {
+        // the comparator: every request as a dense FP32 instance
+        o.path = PHIA_PATH_FP32;
+        if (r.J.empty()) {
+            r.J.assign((size_t)r.N * r.N, 0);
+            for (int i = 0; i < r.N; ++i)
+                for (int32_t p = r.row_ptr[i]; p < r.row_ptr[i + 1]; ++p) r.J[(size_t)i * r.N + r.col[p]] = r.val[p];
+        }
+        rc = phia_create(&r.h_dev, r.J.data(), r.h.data(), r.N, r.frac_bits, &o);
+    } else if (!r.J.empty()) {
         o.path = PHIA_PATH_TC;
         rc = phia_create(&r.h_dev, r.J.data(), r.h.data(), r.N, r.frac_bits, &o);
     } else {
@@ -241,6 +252,8 @@ int phia_server_create(phia_server_t **out, const phia_server_opts *opts) {
     if (opts->max_inflight < 1 || opts->max_inflight > 256) return set_last_error(PHIA_EINVAL, "max_inflight in [1, 256]");
     if (opts->hbm_budget_bytes <= 0) return set_last_error(PHIA_EINVAL, "hbm_budget_bytes must be > 0");
     if (opts->chunk_iters < 1) return set_last_error(PHIA_EINVAL, "chunk_iters must be >= 1");
+    if (opts->path != PHIA_PATH_AUTO && opts->path != PHIA_PATH_FP32)
+        return set_last_error(PHIA_EINVAL, "server path must be PHIA_PATH_AUTO or PHIA_PATH_FP32");
     if (cudaSetDevice(opts->device) != cudaSuccess) return set_last_error(PHIA_ECUDA, "cudaSetDevice failed");
     phia_server_s *S = new phia_server_s();
     S->opts = *opts;
@@ -287,7 +300,7 @@ int phia_server_submit(phia_server_t *S, const phia_instance_desc *d, const phia
     r.replicas = replicas;
     r.step_cap = step_cap;
     r.seed = seed;
-    r.bytes = estimate_bytes(r);
+    r.bytes = estimate_bytes(r, S->opts.path == PHIA_PATH_FP32);
     r.t_submit = Clock::now();
     std::lock_guard<std::mutex> lock(S->mu);
     if (r.bytes > S->opts.hbm_budget_bytes)

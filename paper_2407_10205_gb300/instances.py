@@ -150,6 +150,30 @@ def serving_stream(count: int, seed: int, rate_hz: float = 200.0, n_lo: int = 64
     return out
 
 
+def serving_pool(count: int, seed: int, n_lo: int = 64, n_hi: int = 8192) -> list:
+    """Pool of serving instances: N log-uniform in [n_lo, n_hi]; even entries dense
+    {-1,+1} with h = 0, odd entries sparse fixed point (8 fractional bits, density 0.01,
+    k and kh uniform in [-127, 127])."""
+    g = _rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(math.exp(g.uniform(math.log(n_lo), math.log(n_hi)))))
+        if i % 2 == 0:
+            out.append(sk_pm1(n, seed * 7919 + i + 1))
+        else:
+            out.append(erdos_renyi(n, 0.01, 127, 127, 8, seed * 7919 + i + 1))
+    return out
+
+
+def serving_arrivals(count: int, seed: int, pool_size: int, rate_hz: float = 200.0):
+    """Poisson arrival times (s) at rate_hz, each with a pool index and a run seed."""
+    g = _rng(seed)
+    t = np.cumsum(g.exponential(1.0 / rate_hz, size=count))
+    idx = g.integers(0, pool_size, size=count)
+    seeds = g.integers(1, 2**62, size=count)
+    return [(float(t[i]), int(idx[i]), int(seeds[i])) for i in range(count)]
+
+
 def random_spins(R: int, n: int, seed: int) -> np.ndarray:
     """Uniform +-1 states, int8 [R][n]."""
     g = _rng(seed)

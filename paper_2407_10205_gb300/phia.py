@@ -63,7 +63,7 @@ class InstanceDesc(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("max_inflight", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
-                ("chunk_iters", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("chunk_iters", ctypes.c_int32), ("path", ctypes.c_int32)]
 
 
 class RequestStatus(ctypes.Structure):
@@ -422,8 +422,8 @@ def _desc_of(inst, instance_id=0, target=None):
 class Server:
     """The continuous-batching request loop (phia_server_*)."""
 
-    def __init__(self, max_inflight=8, hbm_budget_bytes=8 << 30, chunk_iters=100, device=0):
-        o = ServerOpts(int(device), int(max_inflight), int(hbm_budget_bytes), int(chunk_iters), 0)
+    def __init__(self, max_inflight=8, hbm_budget_bytes=8 << 30, chunk_iters=100, device=0, path=PATH_AUTO):
+        o = ServerOpts(int(device), int(max_inflight), int(hbm_budget_bytes), int(chunk_iters), int(path))
         self.h = ctypes.c_void_p()
         _check(load().phia_server_create(ctypes.byref(self.h), ctypes.byref(o)))
         self.n = {}
