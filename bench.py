@@ -432,6 +432,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, stream=stream.cuda_stream) as A:
+        tune = phia.autotune(A.h, sched, R, probe_iters=min(T, 200))   # kernel variant for (N, R)
         for _ in range(args.warmup):
             phia.anneal(A.h, sched, R, T, seed)
             phia.sync(A.h)
@@ -504,6 +505,10 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
         "config": {"workload": w["name"], "N": N, "replicas": R, "iterations": T, "path": "tc",
                    "tc_kernel": "resident" if st.tc_kernel == 1 else "per-iteration",
+                   "autotune": {"tc_kernel": tune.tc_kernel, "tile_replicas": tune.tile_replicas,
+                                "coupling_mem": tune.coupling_mem, "candidates": tune.candidates,
+                                "best_us_per_iter": tune.best_us_per_iter,
+                                "worst_us_per_iter": tune.worst_us_per_iter},
                    "field_operand": ("e4m3" if st.operand == 1 else "bf16")
                    + " (exact re-encoding of int8 k), fp32 accumulation of integer products",
                    "state": "fp32 x, v", "l2": "flushed between timed steps (256 MB write)",
@@ -563,6 +568,8 @@ def run_profile(args):
     d = _instance(w)
     sched = phia.schedule(w["beta0"], w["beta1"], w["eps"], w["gamma"], refresh=w["refresh"])
     with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, tile_replicas=args.tile_replicas) as A:
+        if args.tile_replicas == 0:
+            phia.autotune(A.h, sched, w["replicas"], probe_iters=min(w["iterations"], 200))   # as bench.py does
         for _ in range(args.warmup + args.steps):
             phia.anneal(A.h, sched, w["replicas"], w["iterations"], w["run_seed"])
             phia.sync(A.h)

@@ -136,6 +136,25 @@ int phia_create_csr(phia_t **out, const int32_t *row_ptr, const int32_t *col,
 int phia_anneal(phia_t *p, const phia_schedule *sched, int32_t replicas, int64_t steps,
                 uint64_t seed);
 
+/* Autotuner.  Times short probe runs (probe_iters iterations of `replicas` replicas) of
+ * every tensor-core kernel variant that applies to this handle -- the resident kernel
+ * with 4, 8 or 16 replicas per CTA and J in shared or tensor memory (N small enough),
+ * and the per-iteration kernel -- keeps the fastest for the handle and caches it,
+ * process-wide, for (N, replicas, operand): handles created with all variant options
+ * automatic use the cached choice for runs with that replica count.  The probes
+ * overwrite the handle's last-run records.  Tensor-core path only (else PHIA_ENOTSUP). */
+typedef struct phia_tune_result {
+    int32_t tc_kernel;         /* 1 resident, 2 per iteration */
+    int32_t tile_replicas;     /* resident kernel: replicas per CTA */
+    int32_t coupling_mem;      /* resident kernel: 1 shared, 2 tensor memory */
+    int32_t candidates;        /* variants timed */
+    float best_us_per_iter;    /* device time per iteration of the chosen variant */
+    float worst_us_per_iter;   /* of the slowest variant */
+} phia_tune_result;
+
+int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32_t probe_iters,
+                  phia_tune_result *out);
+
 /* Lowest energy found by the last run (ties: earliest step, then lowest replica)
  * and its spins.  energy_k: host int64 (units of q).  spins: host, N int8 in
  * {-1,+1}, may be NULL.  Synchronises the stream.  PHIA_ETIMEOUT if a bounded

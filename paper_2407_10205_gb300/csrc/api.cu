@@ -6,6 +6,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -81,6 +83,8 @@ struct phia_s {
     int8_t *d_val = nullptr;
     // per-replica state
     int R_cap = 0, R_last = 0;
+    bool cap_large = false;             // replica buffers allocated for the per-iteration kernel
+    bool auto_tile = true;              // kernel variant chosen automatically (autotune cache)
     float *d_x = nullptr, *d_v = nullptr;
     int8_t *d_s0 = nullptr, *d_s1 = nullptr;
     int64_t *d_eacc = nullptr;
@@ -109,7 +113,7 @@ void free_replicas(phia_t *p) {
 }
 
 int ensure_replicas(phia_t *p, int R) {
-    if (R <= p->R_cap) return PHIA_OK;
+    if (R <= p->R_cap && p->cap_large == p->large) return PHIA_OK;
     CU(cudaStreamSynchronize(p->stream));
     free_replicas(p);
     const size_t RN = (size_t)R * p->N;
@@ -138,6 +142,7 @@ int ensure_replicas(phia_t *p, int R) {
         free_replicas(p);
         return fail(PHIA_ENOMEM, "device allocation for %d replicas failed", R);
     }
+    p->cap_large = p->large;
     CU(cudaMemsetAsync(p->d_eacc, 0, (size_t)R * 8, p->stream));
     if (p->large) {
         const size_t Rp = (size_t)round_up(R, 128);
@@ -184,6 +189,51 @@ RunArgs base_args(phia_t *p, int R) {
     a.tile_rl = p->tile_rl;
     a.coupling_mem = p->coupling_mem;
     return a;
+}
+
+// Autotune cache: (N, replicas, operand) -> kernel variant, process-wide.
+struct TuneKey {
+    int N, R, op;
+    bool operator<(const TuneKey &o) const {
+        return N != o.N ? N < o.N : (R != o.R ? R < o.R : op < o.op);
+    }
+};
+struct TuneChoice {
+    bool large;
+    int tile_rl, coupling_mem;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune;
+
+int ensure_operand(phia_t *p) {
+    if (p->d_Jop) return PHIA_OK;
+    p->Mpad = round_up(p->N, 128);
+    p->Kbytes = large_kbytes(p->N, p->op);
+    if (cudaMalloc(&p->d_Jop, (size_t)p->Mpad * p->Kbytes) != cudaSuccess)
+        return fail(PHIA_ENOMEM, "J operand allocation failed");
+    CU(launch_convert_operand(p->d_Jk, p->N, p->d_Jop, p->Mpad, p->Kbytes, p->op, p->stream));
+    return PHIA_OK;
+}
+
+// A handle whose kernel variant is automatic takes the cached autotune choice for its
+// (N, replicas, operand), if any.
+int apply_tuned(phia_t *p, int R) {
+    if (!p->auto_tile || p->path != PHIA_PATH_TC) return PHIA_OK;
+    TuneChoice c;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(TuneKey{p->N, R, p->op});
+        if (it == g_tune.end()) return PHIA_OK;
+        c = it->second;
+    }
+    if (c.large) {
+        int rc = ensure_operand(p);
+        if (rc) return rc;
+    }
+    p->large = c.large;
+    p->tile_rl = c.tile_rl;
+    p->coupling_mem = c.coupling_mem;
+    return PHIA_OK;
 }
 
 cudaError_t launch_path(phia_t *p, const RunArgs &a, int *launches) {
@@ -279,6 +329,7 @@ int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, 
     p->inst = o.instance_id;
     p->tile_rl = o.tile_replicas;
     p->coupling_mem = o.coupling_mem;
+    p->auto_tile = o.tile_replicas == 0 && o.coupling_mem == 0 && o.tc_kernel == 0;
     p->N = N;
     p->frac_bits = frac_bits;
     p->W = (N + 31) / 32;
@@ -356,6 +407,10 @@ static int run_impl(phia_t *p, const phia_schedule *sched, int32_t R, int64_t t0
     CU(cudaSetDevice(p->device));
     if (!reset && (!p->ran || p->R_last != R))
         return fail(PHIA_ESTATE, "reset_best = 0 needs a previous run with the same replica count");
+    if (reset) {
+        rc = apply_tuned(p, R);
+        if (rc) return rc;
+    }
     rc = ensure_replicas(p, R);
     if (rc) return rc;
     if (reset) {
@@ -382,6 +437,59 @@ static int run_impl(phia_t *p, const phia_schedule *sched, int32_t R, int64_t t0
     p->last_steps = steps;
     p->last_launches = launches;
     p->last_stop = sched->stop_at_target;
+    return PHIA_OK;
+}
+
+int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32_t probe_iters,
+                  phia_tune_result *out) {
+    if (!p || !sched) return fail(PHIA_EINVAL, "NULL argument");
+    if (p->path != PHIA_PATH_TC) return fail(PHIA_ENOTSUP, "the autotuner chooses among tensor-core kernels");
+    if (replicas < 1 || probe_iters < 1) return fail(PHIA_EINVAL, "need replicas >= 1 and probe_iters >= 1");
+    std::vector<TuneChoice> cands;
+    if (p->N <= tc_small_max_n(p->op)) {
+        for (int tile : {4, 8, 16})
+            for (int mem : {1, 2}) cands.push_back(TuneChoice{false, tile, mem});
+    }
+    cands.push_back(TuneChoice{true, 0, 0});
+    const bool saved_auto = p->auto_tile;
+    p->auto_tile = false;
+    float best_ms = 1e30f, worst_ms = 0.f;
+    TuneChoice best = cands[0];
+    for (const TuneChoice &c : cands) {
+        if (c.large) {
+            int rc = ensure_operand(p);
+            if (rc) { p->auto_tile = saved_auto; return rc; }
+        }
+        p->large = c.large;
+        p->tile_rl = c.tile_rl;
+        p->coupling_mem = c.coupling_mem;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {   // the first run warms up
+            int rc = run_impl(p, sched, replicas, 0, probe_iters, probe_iters, 1, nullptr, nullptr, nullptr, nullptr, 1);
+            if (rc) { p->auto_tile = saved_auto; return rc; }
+            CU(cudaEventSynchronize(p->ev1));
+            CU(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+        }
+        if (ms < best_ms) { best_ms = ms; best = c; }
+        worst_ms = std::max(worst_ms, ms);
+    }
+    p->large = best.large;
+    p->tile_rl = best.tile_rl;
+    p->coupling_mem = best.coupling_mem;
+    p->auto_tile = saved_auto;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[TuneKey{p->N, replicas, p->op}] = best;
+    }
+    if (out) {
+        memset(out, 0, sizeof *out);
+        out->tc_kernel = best.large ? 2 : 1;
+        out->tile_replicas = best.large ? 0 : tc_small_tile_replicas(replicas, best.tile_rl);
+        out->coupling_mem = best.large ? 0 : best.coupling_mem;
+        out->candidates = (int32_t)cands.size();
+        out->best_us_per_iter = 1000.f * best_ms / probe_iters;
+        out->worst_us_per_iter = 1000.f * worst_ms / probe_iters;
+    }
     return PHIA_OK;
 }
 

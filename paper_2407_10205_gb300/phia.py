@@ -79,6 +79,12 @@ class ServerStats(ctypes.Structure):
                 ("ttt_admit_p99_s", ctypes.c_double), ("elapsed_s", ctypes.c_double), ("used_bytes", ctypes.c_int64)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("tc_kernel", ctypes.c_int32), ("tile_replicas", ctypes.c_int32), ("coupling_mem", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("best_us_per_iter", ctypes.c_float),
+                ("worst_us_per_iter", ctypes.c_float)]
+
+
 # name -> (restype, argtypes); every symbol include/phia.h declares
 _P = ctypes.c_void_p
 SIGNATURES = {
@@ -86,6 +92,7 @@ SIGNATURES = {
     "phia_create_csr": (ctypes.c_int, [ctypes.POINTER(_P), _P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "phia_anneal": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64]),
     "phia_best": (ctypes.c_int, [_P, _P, _P]),
+    "phia_autotune": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "phia_stats_get": (ctypes.c_int, [_P, _P]),
     "phia_replica_results": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P]),
     "phia_run": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
@@ -199,6 +206,12 @@ def create_csr(row_ptr, col, val_k, h_k, frac_bits=0, o: Opts | None = None):
 
 def anneal(h, sched: Schedule, replicas: int, steps: int, seed: int):
     _check(load().phia_anneal(h, ctypes.byref(sched), int(replicas), int(steps), int(seed) & (2**64 - 1)))
+
+
+def autotune(h, sched: Schedule, replicas: int, probe_iters: int = 200) -> TuneResult:
+    r = TuneResult()
+    _check(load().phia_autotune(h, ctypes.byref(sched), int(replicas), int(probe_iters), ctypes.byref(r)))
+    return r
 
 
 def best(h, n: int):
