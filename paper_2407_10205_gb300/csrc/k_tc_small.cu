@@ -85,14 +85,18 @@ __device__ __forceinline__ void tmem_ld_sync(uint32_t taddr, float (&v)[RPT]) {
 // CH * RPT (8 or 16); the MMA always runs 16 replica columns.
 // AT: the couplings (A operand) live in tensor memory instead of shared memory, so
 // each MMA reads only the 16-replica spin tile from shared memory.
+// Warps 0 .. 4*MT*CH-1 run the epilogue (warp w reads TMEM lane quadrant w % 4); the
+// last warp is the control warp: its lane 0 issues the field MMAs, its first RL lanes
+// keep the records, so the MMA issue and the records overlap the epilogue warps' work.
 template <int MT, int OP, int CH, int RPT, bool AT>
-__global__ void __launch_bounds__(128 * MT * CH, CH == 1 ? 2 : 1) tc_small_kernel(const RunArgs a, int Kpad) {
+__global__ void __launch_bounds__(128 * MT * CH + 32, CH == 1 ? 2 : 1) tc_small_kernel(const RunArgs a, int Kpad) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
     constexpr int RL = CH * RPT;
+    constexpr int NEPI = 4 * MT * CH;        // epilogue warps
     constexpr uint32_t IDESC = make_idesc(OP == kOpE4M3 ? 0u : 1u, 128, kNB);
     constexpr uint32_t ACC_COLS = 2 * MT * kNB;
     static_assert(RL <= kNB, "live replicas exceed the MMA width");
-    static_assert(4 * MT * CH <= kMaxWarps && RPT <= kMaxRPT, "shared energy slots too small");
+    static_assert(NEPI <= kMaxWarps && RPT <= kMaxRPT, "shared energy slots too small");
     const int Kbytes = Kpad * ESZ;
     const int KS = Kbytes / 32;            // MMA K-steps (32 bytes of K each)
     const uint32_t SBO = (uint32_t)Kbytes * 8u;
@@ -105,12 +109,13 @@ __global__ void __launch_bounds__(128 * MT * CH, CH == 1 ? 2 : 1) tc_small_kerne
     SmallShared *sm = reinterpret_cast<SmallShared *>(sB + kNB * Kbytes);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool ctl = warp == NEPI;         // control warp
     const int q4 = warp & 3;               // TMEM lane quadrant this warp may access
     const int mt = (warp >> 2) % MT;       // output-spin tile
     const int ch = warp / (4 * MT);        // which RPT of the RL replicas
     const int N = a.N;
     const int i = mt * 128 + q4 * 32 + lane;
-    const bool live_i = i < N;
+    const bool live_i = !ctl && i < N;
     const int rbase = blockIdx.x * RL;
 
     if (warp == 0) {
@@ -147,7 +152,7 @@ __global__ void __launch_bounds__(128 * MT * CH, CH == 1 ? 2 : 1) tc_small_kerne
     if constexpr (AT) {
         // Row i of A (output spin i) into TMEM lane i % 128 of tile i / 128: 32 bytes of K
         // (8 columns) per store.  One warp per (lane quadrant, tile) does it.
-        if (ch == 0) {
+        if (!ctl && ch == 0) {
             const uint32_t base = sm->tmem_base + ((uint32_t)(q4 * 32) << 16) + ACC_COLS + mt * A_COLS;
             for (int c8 = 0; c8 < Kbytes / 32; ++c8) {
                 uint32_t w[8];
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(128 * MT * CH, CH == 1 ? 2 : 1) tc_small_kerne
     }
 
     // This thread's spin slots in B: replica c = ch*RPT + k sits at row c, column i.
-    uint8_t *my_b = operand_ptr<OP>(sB, ch * RPT, live_i ? i : 0, SBO);
+    uint8_t *my_b = operand_ptr<OP>(sB, ctl ? 0 : ch * RPT, live_i ? i : 0, SBO);
     const int32_t hki = live_i ? a.hk[i] : 0;
     float x[RPT], v[RPT];
     uint32_t cur = 0;  // bit k: spin i of replica ch*RPT+k is +1 in the B of this iteration
@@ -218,7 +223,7 @@ __global__ void __launch_bounds__(128 * MT * CH, CH == 1 ? 2 : 1) tc_small_kerne
     uint32_t phase = 0, prv = 0;
     bool timed_out = false, stopped = false;
     int it = 0;
-    // Field MMAs of one iteration: D[m] = A[m] B^T over all K-steps (thread 0 only).
+    // Field MMAs of one iteration: D[m] = A[m] B^T over all K-steps (control lane 0).
     // Descriptors advance by adding (byte offset >> 4) to the start-address field.
     const uint64_t adesc0 = smem_desc_noswizzle(smem_u32(sA), 128, SBO);
     const uint64_t bdesc0 = smem_desc_noswizzle(smem_u32(sB), 128, SBO);
@@ -245,83 +250,100 @@ __global__ void __launch_bounds__(128 * MT * CH, CH == 1 ? 2 : 1) tc_small_kerne
         mma_commit(&sm->mbar);
     };
     const bool two_acc = KS > 1;
-    if (tid == 0) issue_field();
+    if (ctl && lane == 0) issue_field();
     for (; it < nit; ++it) {
         const int64_t t = a.t0 + it;
-        const bool ok = mbar_wait_bounded(&sm->mbar, phase, kWaitTimeoutNs);
-        phase ^= 1u;
-        tc_fence_after();
-        float acc[RPT];
-        tmem_ld_sync<RPT>(my_taddr, acc);
-        if (two_acc) {
-            float acc2[RPT];
-            tmem_ld_sync<RPT>(my_taddr + kNB, acc2);
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) acc[k] += acc2[k];
-        }
-
-        const float bgq = beta_at(t, inv_tm1, a.beta0, a.beta1) * gq;
-        const bool more = it + 1 < nit;
-        const bool refresh_next = more && a.refresh > 0 && rc == 0;
+        bool ok = true;
         uint32_t nxt = 0;
+        if (!ctl) {
+            ok = mbar_wait_bounded(&sm->mbar, phase, kWaitTimeoutNs);
+            tc_fence_after();
+            float acc[RPT];
+            tmem_ld_sync<RPT>(my_taddr, acc);
+            if (two_acc) {
+                float acc2[RPT];
+                tmem_ld_sync<RPT>(my_taddr + kNB, acc2);
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-            const int c = ch * RPT + k, r = rbase + c;
-            const int32_t Ik = __float2int_rn(acc[k]) + hki;       // Eq. 6, exact
-            const int32_t sk = ((cur >> k) & 1u) ? 1 : -1;
-            int32_t part = live_i ? sk * (Ik + hki) : 0;            // s_i (I_i + h_i)
-            part = __reduce_add_sync(0xffffffffu, part);
-            if (lane == 0) sm->e_part[it & 1][warp][k] = part;
+                for (int k = 0; k < RPT; ++k) acc[k] += acc2[k];
+            }
+            // Field (Eq. 6, exact) and energy terms s_i (I_i + h_i) of every replica first,
+            // then their warp sums, then the updates: straight-line code across replicas.
+            int32_t Ik[RPT], part[RPT];
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                Ik[k] = __float2int_rn(acc[k]) + hki;
+                part[k] = live_i ? (((cur >> k) & 1u) ? (Ik[k] + hki) : -(Ik[k] + hki)) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) part[k] = __reduce_add_sync(0xffffffffu, part[k]);
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) sm->e_part[it & 1][warp][k] = part[k];
+            }
             if (a.field_mode) {
-                if (live_i && r < a.R && a.field_out) a.field_out[(size_t)r * N + i] = Ik;
-                continue;
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) {
+                    const int r = rbase + ch * RPT + k;
+                    if (live_i && r < a.R && a.field_out) a.field_out[(size_t)r * N + i] = Ik[k];
+                }
+            } else if (live_i) {
+                const float bgq = beta_at(t, inv_tm1, a.beta0, a.beta1) * gq;
+                const bool more = it + 1 < nit;
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) v[k] = momentum_update(v[k], x[k], (float)Ik[k], eps, bgq, gamma);
+                if (more) {
+                    if (a.refresh > 0 && rc == 0) {
+#pragma unroll
+                        for (int k = 0; k < RPT; ++k)
+                            v[k] = draw_v(a.seed, a.inst, (uint32_t)(rbase + ch * RPT + k), (uint32_t)i, (uint32_t)(t + 1));
+                    }
+#pragma unroll
+                    for (int k = 0; k < RPT; ++k) {
+                        x[k] = x[k] + eps * v[k];
+                        const bool plus = x[k] >= 0.0f;
+                        put_spin<OP>(my_b + k * 16, plus);
+                        nxt |= (uint32_t)plus << k;
+                    }
+                }
             }
-            if (!live_i) continue;
-            v[k] = momentum_update(v[k], x[k], (float)Ik, eps, bgq, gamma);
-            if (more) {
-                if (refresh_next) v[k] = draw_v(a.seed, a.inst, (uint32_t)r, (uint32_t)i, (uint32_t)(t + 1));
-                x[k] = x[k] + eps * v[k];
-                const bool plus = x[k] >= 0.0f;
-                put_spin<OP>(my_b + k * 16, plus);
-                nxt |= (uint32_t)plus << k;
-            }
+            fence_proxy_async_smem();
+            tc_fence_before();
         }
-        fence_proxy_async_smem();
-        tc_fence_before();
+        phase ^= 1u;
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
-        // Next iteration's field first: B holds its spins and every TMEM read is done.
-        if (tid == 0 && it + 1 < nit) issue_field();
-
-        // Records of iteration t (Table 3, state 5), one thread per replica column.
-        if (tid < RL) {
-            const int c = tid, r = rbase + c;
-            long long twice = 0;   // sum_i s_i (I_i + h_i) over the 4*MT warps holding replica c
+        if (ctl) {
+            // Next iteration's field first: B holds its spins and every TMEM read is done.
+            if (lane == 0 && it + 1 < nit) issue_field();
+            // Records of iteration t (Table 3, state 5), one lane per replica column.
+            if (lane < RL) {
+                const int c = lane, r = rbase + c;
+                long long twice = 0;   // sum_i s_i (I_i + h_i) over the 4*MT warps holding replica c
 #pragma unroll
-            for (int j = 0; j < 4 * MT; ++j) twice += sm->e_part[it & 1][(c / RPT) * 4 * MT + j][c % RPT];
-            const long long E = -twice / 2;                                  // Eq. 2 via the field
-            int imp = 0;
-            if (a.field_mode) {
-                if (r < a.R && a.energy_out) a.energy_out[r] = E;
-            } else if (r < a.R) {
-                const bool frozen = a.stop_at_target && sm->hit[c] >= 0;
-                if (!frozen && E < sm->best_e[c]) {
-                    sm->best_e[c] = E;
-                    sm->best_step[c] = t;
-                    imp = 1;
+                for (int j = 0; j < 4 * MT; ++j) twice += sm->e_part[it & 1][(c / RPT) * 4 * MT + j][c % RPT];
+                const long long E = -twice / 2;                                  // Eq. 2 via the field
+                int imp = 0;
+                if (a.field_mode) {
+                    if (r < a.R && a.energy_out) a.energy_out[r] = E;
+                } else if (r < a.R) {
+                    const bool frozen = a.stop_at_target && sm->hit[c] >= 0;
+                    if (!frozen && E < sm->best_e[c]) {
+                        sm->best_e[c] = E;
+                        sm->best_step[c] = t;
+                        imp = 1;
+                    }
+                    if (a.has_target && sm->hit[c] < 0 && E <= a.target) {
+                        sm->hit[c] = t;
+                        if (a.stop_at_target) atomicMin(a.min_hit, (unsigned long long)t);
+                    }
                 }
-                if (a.has_target && sm->hit[c] < 0 && E <= a.target) {
-                    sm->hit[c] = t;
-                    if (a.stop_at_target) atomicMin(a.min_hit, (unsigned long long)t);
-                }
+                sm->improved[it & 1][c] = imp;
             }
-            sm->improved[it & 1][c] = imp;
-        }
-        if (tid == 0)
-            sm->stop[it & 1] = (a.stop_at_target && !a.field_mode)
-                                   ? (*(volatile unsigned long long *)a.min_hit <= (unsigned long long)t)
-                                   : 0;
-        // Best spins of iteration t-1 (its records were settled before this barrier).
-        if (it > 0) {
+            if (lane == 0)
+                sm->stop[it & 1] = (a.stop_at_target && !a.field_mode)
+                                       ? (*(volatile unsigned long long *)a.min_hit <= (unsigned long long)t)
+                                       : 0;
+        } else if (it > 0) {
+            // Best spins of iteration t-1 (its records were settled before this barrier).
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 const int c = ch * RPT + k;
@@ -337,17 +359,19 @@ __global__ void __launch_bounds__(128 * MT * CH, CH == 1 ? 2 : 1) tc_small_kerne
         if (it > 0 && sm->stop[(it - 1) & 1]) { stopped = true; ++it; break; }
     }
     // A field issued for an iteration that will not run (stop) must finish before TMEM is freed.
-    if (stopped && it < nit && tid == 0) mbar_wait_bounded(&sm->mbar, phase, kWaitTimeoutNs);
+    if (stopped && it < nit && ctl && lane == 0) mbar_wait_bounded(&sm->mbar, phase, kWaitTimeoutNs);
 
     if (!timed_out) {
         __syncthreads();  // records of the last iteration settled
         const int last = it - 1;
+        if (!ctl) {
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-            const int c = ch * RPT + k;
-            if (last >= 0 && sm->improved[last & 1][c]) {
-                const uint32_t bits = __ballot_sync(0xffffffffu, live_i && ((prv >> k) & 1u));
-                if (lane == 0 && word < a.W) a.best_bits[(size_t)(rbase + c) * a.W + word] = bits;
+            for (int k = 0; k < RPT; ++k) {
+                const int c = ch * RPT + k;
+                if (last >= 0 && sm->improved[last & 1][c]) {
+                    const uint32_t bits = __ballot_sync(0xffffffffu, live_i && ((prv >> k) & 1u));
+                    if (lane == 0 && word < a.W) a.best_bits[(size_t)(rbase + c) * a.W + word] = bits;
+                }
             }
         }
     }
@@ -361,18 +385,17 @@ __global__ void __launch_bounds__(128 * MT * CH, CH == 1 ? 2 : 1) tc_small_kerne
             }
         }
     }
-    if (tid < RL && !a.field_mode) {
-        const int r = rbase + tid;
+    if (ctl && lane < RL && !a.field_mode) {
+        const int r = rbase + lane;
         if (r < a.R) {
-            a.best_e[r] = sm->best_e[tid];
-            a.best_step[r] = sm->best_step[tid];
-            a.hit_step[r] = sm->hit[tid];
+            a.best_e[r] = sm->best_e[lane];
+            a.best_step[r] = sm->best_step[lane];
+            a.hit_step[r] = sm->hit[lane];
         }
     }
-    if (tid == 0) {
+    if (ctl && lane == 0) {
         const int valid = min(RL, a.R - rbase);
-        const int done = timed_out ? it : it;
-        if (!a.field_mode) atomicAdd(a.replica_iters, (unsigned long long)((long long)valid * done));
+        if (!a.field_mode) atomicAdd(a.replica_iters, (unsigned long long)((long long)valid * it));
         if (timed_out) {
             atomicExch(a.err, 1);
             mbar_wait_bounded(&sm->mbar, phase ^ 1u, kWaitTimeoutNs);  // let the MMA in flight drain
@@ -395,7 +418,7 @@ cudaError_t launch_cfg(const RunArgs &a, int Kpad, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (a.R + RL - 1) / RL;
-    kern<<<grid, 128 * MT * CH, smem, st>>>(a, Kpad);
+    kern<<<grid, 128 * MT * CH + 32, smem, st>>>(a, Kpad);
     return cudaGetLastError();
 }
 
