@@ -85,11 +85,12 @@ __device__ __forceinline__ void tmem_ld_sync(uint32_t taddr, float (&v)[RPT]) {
 // CH * RPT (8 or 16); the MMA always runs 16 replica columns.
 // AT: the couplings (A operand) live in tensor memory instead of shared memory, so
 // each MMA reads only the 16-replica spin tile from shared memory.
-// Warps 0 .. 4*MT*CH-1 run the epilogue (warp w reads TMEM lane quadrant w % 4); the
-// last warp is the control warp: its lane 0 issues the field MMAs, its first RL lanes
-// keep the records, so the MMA issue and the records overlap the epilogue warps' work.
+// Warps 0 .. 4*MT*CH-1 run the epilogue (warp w reads TMEM lane quadrant w % 4); MT
+// control warps follow: lane 0 of control warp m issues the field MMAs of output tile m
+// (in parallel with the other tiles' issue), the first RL lanes of control warp 0 keep
+// the records, so MMA issue and records overlap the epilogue warps' work.
 template <int MT, int OP, int CH, int RPT, bool AT>
-__global__ void __launch_bounds__(128 * MT * CH + 32, CH == 1 ? 2 : 1) tc_small_kernel(const RunArgs a, int Kpad) {
+__global__ void __launch_bounds__(128 * MT * CH + 32 * MT, CH == 1 ? 2 : 1) tc_small_kernel(const RunArgs a, int Kpad) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
     constexpr int RL = CH * RPT;
     constexpr int NEPI = 4 * MT * CH;        // epilogue warps
@@ -109,7 +110,8 @@ __global__ void __launch_bounds__(128 * MT * CH + 32, CH == 1 ? 2 : 1) tc_small_
     SmallShared *sm = reinterpret_cast<SmallShared *>(sB + kNB * Kbytes);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool ctl = warp == NEPI;         // control warp
+    const bool ctl = warp >= NEPI;         // control warps
+    const int cw = warp - NEPI;            // control warp index = output tile it issues
     const int q4 = warp & 3;               // TMEM lane quadrant this warp may access
     const int mt = (warp >> 2) % MT;       // output-spin tile
     const int ch = warp / (4 * MT);        // which RPT of the RL replicas
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 32, CH == 1 ? 2 : 1) tc_small_
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(&sm->mbar, 1);
+        mbar_init(&sm->mbar, MT);          // one commit per output tile
         fence_mbarrier_init();
     }
     // Couplings into A (zero-padded to MT*128 rows x Kpad columns), B cleared.
@@ -223,34 +225,32 @@ __global__ void __launch_bounds__(128 * MT * CH + 32, CH == 1 ? 2 : 1) tc_small_
     uint32_t phase = 0, prv = 0;
     bool timed_out = false, stopped = false;
     int it = 0;
-    // Field MMAs of one iteration: D[m] = A[m] B^T over all K-steps (control lane 0).
-    // Descriptors advance by adding (byte offset >> 4) to the start-address field.
+    // Field MMAs of output tile m for one iteration: D[m] = A[m] B^T over all K-steps,
+    // K-step ks into D[m][ks & 1] (lane 0 of control warp m).  Descriptors advance by
+    // adding (byte offset >> 4) to the start-address field.
     const uint64_t adesc0 = smem_desc_noswizzle(smem_u32(sA), 128, SBO);
     const uint64_t bdesc0 = smem_desc_noswizzle(smem_u32(sB), 128, SBO);
-    // K-step ks of tile m accumulates into D[m][ks & 1]; tiles interleaved per K-step.
-    auto issue_field = [&]() {
+    auto issue_field = [&](int m) {
         tc_fence_after();
+        const uint64_t am = adesc0 + (uint64_t)((m * 16 * SBO) >> 4);
 #pragma unroll 1
         for (int ks = 0; ks < KS; ++ks) {
             const uint64_t bd = bdesc0 + (uint64_t)(ks * 16);   // 256 bytes per K-step
-#pragma unroll
-            for (int m = 0; m < MT; ++m) {
-                const uint32_t d = tmem + (uint32_t)((2 * m + (ks & 1)) * kNB);
-                if constexpr (AT) {
-                    const uint32_t at = tmem + ACC_COLS + m * A_COLS + ks * 8;   // 32 bytes = 8 columns
-                    if constexpr (OP == kOpE4M3) mma_e4m3_ta(d, at, bd, IDESC, ks > 1);
-                    else mma_bf16_ta(d, at, bd, IDESC, ks > 1);
-                } else {
-                    const uint64_t ad = adesc0 + (uint64_t)((m * 16 * SBO) >> 4) + (uint64_t)(ks * 16);
-                    if constexpr (OP == kOpE4M3) mma_e4m3(d, ad, bd, IDESC, ks > 1);
-                    else mma_bf16(d, ad, bd, IDESC, ks > 1);
-                }
+            const uint32_t d = tmem + (uint32_t)((2 * m + (ks & 1)) * kNB);
+            if constexpr (AT) {
+                const uint32_t at = tmem + ACC_COLS + m * A_COLS + ks * 8;   // 32 bytes = 8 columns
+                if constexpr (OP == kOpE4M3) mma_e4m3_ta(d, at, bd, IDESC, ks > 1);
+                else mma_bf16_ta(d, at, bd, IDESC, ks > 1);
+            } else {
+                const uint64_t ad = am + (uint64_t)(ks * 16);
+                if constexpr (OP == kOpE4M3) mma_e4m3(d, ad, bd, IDESC, ks > 1);
+                else mma_bf16(d, ad, bd, IDESC, ks > 1);
             }
         }
         mma_commit(&sm->mbar);
     };
     const bool two_acc = KS > 1;
-    if (ctl && lane == 0) issue_field();
+    if (ctl && lane == 0) issue_field(cw);
     for (; it < nit; ++it) {
         const int64_t t = a.t0 + it;
         bool ok = true;
@@ -313,9 +313,9 @@ __global__ void __launch_bounds__(128 * MT * CH + 32, CH == 1 ? 2 : 1) tc_small_
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
         if (ctl) {
             // Next iteration's field first: B holds its spins and every TMEM read is done.
-            if (lane == 0 && it + 1 < nit) issue_field();
+            if (lane == 0 && it + 1 < nit) issue_field(cw);
             // Records of iteration t (Table 3, state 5), one lane per replica column.
-            if (lane < RL) {
+            if (cw == 0 && lane < RL) {
                 const int c = lane, r = rbase + c;
                 long long twice = 0;   // sum_i s_i (I_i + h_i) over the 4*MT warps holding replica c
 #pragma unroll
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 32, CH == 1 ? 2 : 1) tc_small_
                 }
                 sm->improved[it & 1][c] = imp;
             }
-            if (lane == 0)
+            if (cw == 0 && lane == 0)
                 sm->stop[it & 1] = (a.stop_at_target && !a.field_mode)
                                        ? (*(volatile unsigned long long *)a.min_hit <= (unsigned long long)t)
                                        : 0;
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 32, CH == 1 ? 2 : 1) tc_small_
         if (it > 0 && sm->stop[(it - 1) & 1]) { stopped = true; ++it; break; }
     }
     // A field issued for an iteration that will not run (stop) must finish before TMEM is freed.
-    if (stopped && it < nit && ctl && lane == 0) mbar_wait_bounded(&sm->mbar, phase, kWaitTimeoutNs);
+    if (stopped && it < nit && ctl && cw == 0 && lane == 0) mbar_wait_bounded(&sm->mbar, phase, kWaitTimeoutNs);
 
     if (!timed_out) {
         __syncthreads();  // records of the last iteration settled
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 32, CH == 1 ? 2 : 1) tc_small_
             }
         }
     }
-    if (ctl && lane < RL && !a.field_mode) {
+    if (ctl && cw == 0 && lane < RL && !a.field_mode) {
         const int r = rbase + lane;
         if (r < a.R) {
             a.best_e[r] = sm->best_e[lane];
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 32, CH == 1 ? 2 : 1) tc_small_
             a.hit_step[r] = sm->hit[lane];
         }
     }
-    if (ctl && lane == 0) {
+    if (ctl && cw == 0 && lane == 0) {
         const int valid = min(RL, a.R - rbase);
         if (!a.field_mode) atomicAdd(a.replica_iters, (unsigned long long)((long long)valid * it));
         if (timed_out) {
@@ -418,7 +418,7 @@ cudaError_t launch_cfg(const RunArgs &a, int Kpad, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (a.R + RL - 1) / RL;
-    kern<<<grid, 128 * MT * CH + 32, smem, st>>>(a, Kpad);
+    kern<<<grid, 128 * MT * CH + 32 * MT, smem, st>>>(a, Kpad);
     return cudaGetLastError();
 }
 
