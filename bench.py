@@ -541,6 +541,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile-replicas", type=int, default=0, help="tensor-core replicas per CTA (0 = auto)")
     ap.add_argument("--coupling-mem", type=int, default=0, help="tensor-core: 1 = J in shared, 2 = in tensor memory")
+    ap.add_argument("--tc-kernel", type=int, default=0, help="tensor-core kernel: 1 tcgen05 resident, 2 per-iteration, 3 int8 mma.sync")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warmup + steps anneals of the tensor-core path and nothing else (for ncu)")
     args = ap.parse_args()
@@ -569,8 +570,8 @@ def run_profile(args):
     d = _instance(w)
     sched = phia.schedule(w["beta0"], w["beta1"], w["eps"], w["gamma"], refresh=w["refresh"])
     with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, tile_replicas=args.tile_replicas,
-                       coupling_mem=args.coupling_mem) as A:
-        if args.tile_replicas == 0:
+                       coupling_mem=args.coupling_mem, tc_kernel=args.tc_kernel) as A:
+        if args.tile_replicas == 0 and args.tc_kernel == 0:
             phia.autotune(A.h, sched, w["replicas"], probe_iters=min(w["iterations"], 200))   # as bench.py does
         for _ in range(args.warmup + args.steps):
             phia.anneal(A.h, sched, w["replicas"], w["iterations"], w["run_seed"])

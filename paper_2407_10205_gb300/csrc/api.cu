@@ -65,6 +65,7 @@ struct phia_s {
     int tile_rl = 0, coupling_mem = 0;
     phia_batch_s *batch = nullptr;      // CSR instances: a batch of one
     bool large = false;                 // tensor-core path through the per-iteration kernel
+    bool imma = false;                  // tensor-core path through the int8 mma.sync resident kernel
     void *d_Jop = nullptr;              // couplings in the operand encoding (per-iteration kernel)
     int Mpad = 0, Kbytes = 0;
     uint8_t *d_S = nullptr;             // [4][Rpad][Kbytes]
@@ -201,6 +202,7 @@ struct TuneKey {
 struct TuneChoice {
     bool large;
     int tile_rl, coupling_mem;
+    bool imma;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune;
@@ -231,6 +233,7 @@ int apply_tuned(phia_t *p, int R) {
         if (rc) return rc;
     }
     p->large = c.large;
+    p->imma = c.imma;
     p->tile_rl = c.tile_rl;
     p->coupling_mem = c.coupling_mem;
     return PHIA_OK;
@@ -243,6 +246,7 @@ cudaError_t launch_path(phia_t *p, const RunArgs &a, int *launches) {
         B.X = p->d_X; B.V = p->d_V; B.Kbytes = p->Kbytes; B.Mpad = p->Mpad; B.Rpad = round_up(a.R, 128);
         return launch_tc_large(B, a, p->op, p->stream, launches);
     }
+    if (p->path == PHIA_PATH_TC && p->imma) return launch_imma_small(a, p->stream, launches);
     if (p->path == PHIA_PATH_TC) return launch_tc_small(a, p->op, p->stream, launches);
     if (p->path == PHIA_PATH_FP32)
         return launch_fp32_run(a, p->d_x, p->d_v, p->d_s0, p->d_s1, p->d_eacc, p->stream, launches);
@@ -314,7 +318,9 @@ int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, 
             return fail(PHIA_ENOTSUP, "the resident kernel handles N <= %d with this operand (N = %d)",
                         tc_small_max_n(opk), N);
     }
-    if (o.tc_kernel < 0 || o.tc_kernel > 2) return fail(PHIA_EINVAL, "tc_kernel must be 0, 1 or 2");
+    if (o.tc_kernel < 0 || o.tc_kernel > 3) return fail(PHIA_EINVAL, "tc_kernel must be 0, 1, 2 or 3");
+    if (o.tc_kernel == 3 && N > imma_small_max_n())
+        return fail(PHIA_ENOTSUP, "the int8 mma.sync kernel handles N <= %d (N = %d)", imma_small_max_n(), N);
     if (o.reserved != 0) return fail(PHIA_EINVAL, "opts.reserved must be 0");
     int dev_count = 0;
     if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
@@ -334,8 +340,10 @@ int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, 
     p->frac_bits = frac_bits;
     p->W = (N + 31) / 32;
     p->max_abs_k = max_abs;
-    if (path == PHIA_PATH_TC)
+    if (path == PHIA_PATH_TC) {
         p->large = o.tc_kernel == 2 || (o.tc_kernel == 0 && N > tc_small_max_n(p->op));
+        p->imma = o.tc_kernel == 3;
+    }
     const size_t NN = (size_t)N * N;
     auto cleanup = [&](int code) { phia_destroy(p); return code; };
     if (cudaMalloc((void **)&p->d_Jk, NN) != cudaSuccess) return cleanup(fail(PHIA_ENOMEM, "J allocation failed"));
@@ -448,9 +456,13 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
     std::vector<TuneChoice> cands;
     if (p->N <= tc_small_max_n(p->op)) {
         for (int tile : {4, 8, 16})
-            for (int mem : {1, 2}) cands.push_back(TuneChoice{false, tile, mem});
+            for (int mem : {1, 2}) cands.push_back(TuneChoice{false, tile, mem, false});
     }
-    cands.push_back(TuneChoice{true, 0, 0});
+    if (p->N <= imma_small_max_n()) {
+        cands.push_back(TuneChoice{false, 8, 0, true});
+        cands.push_back(TuneChoice{false, 16, 0, true});
+    }
+    cands.push_back(TuneChoice{true, 0, 0, false});
     const bool saved_auto = p->auto_tile;
     p->auto_tile = false;
     float best_ms = 1e30f, worst_ms = 0.f;
@@ -461,6 +473,7 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
             if (rc) { p->auto_tile = saved_auto; return rc; }
         }
         p->large = c.large;
+        p->imma = c.imma;
         p->tile_rl = c.tile_rl;
         p->coupling_mem = c.coupling_mem;
         float ms = 0.f;
@@ -474,6 +487,7 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
         worst_ms = std::max(worst_ms, ms);
     }
     p->large = best.large;
+    p->imma = best.imma;
     p->tile_rl = best.tile_rl;
     p->coupling_mem = best.coupling_mem;
     p->auto_tile = saved_auto;
@@ -483,9 +497,9 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
     }
     if (out) {
         memset(out, 0, sizeof *out);
-        out->tc_kernel = best.large ? 2 : 1;
-        out->tile_replicas = best.large ? 0 : tc_small_tile_replicas(replicas, best.tile_rl);
-        out->coupling_mem = best.large ? 0 : best.coupling_mem;
+        out->tc_kernel = best.large ? 2 : (best.imma ? 3 : 1);
+        out->tile_replicas = best.large ? 0 : (best.imma ? best.tile_rl : tc_small_tile_replicas(replicas, best.tile_rl));
+        out->coupling_mem = best.large || best.imma ? 0 : best.coupling_mem;
         out->candidates = (int32_t)cands.size();
         out->best_us_per_iter = 1000.f * best_ms / probe_iters;
         out->worst_us_per_iter = 1000.f * worst_ms / probe_iters;
@@ -635,7 +649,7 @@ int phia_stats_get(phia_t *p, phia_stats *out) {
     out->path = p->path;
     out->operand = p->op == kOpE4M3 ? PHIA_OP_E4M3 : (p->op == kOpBF16 ? PHIA_OP_BF16 : 0);
     out->kernel_launches = p->last_launches;
-    out->tc_kernel = p->path == PHIA_PATH_TC ? (p->large ? 2 : 1) : 0;
+    out->tc_kernel = p->path == PHIA_PATH_TC ? (p->large ? 2 : (p->imma ? 3 : 1)) : 0;
     return PHIA_OK;
 }
 

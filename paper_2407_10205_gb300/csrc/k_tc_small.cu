@@ -90,7 +90,7 @@ __device__ __forceinline__ void tmem_ld_sync(uint32_t taddr, float (&v)[RPT]) {
 // (in parallel with the other tiles' issue), the first RL lanes of control warp 0 keep
 // the records, so MMA issue and records overlap the epilogue warps' work.
 template <int MT, int OP, int CH, int RPT, bool AT>
-__global__ void __launch_bounds__(128 * MT * CH + 32 * MT, CH == 1 ? 2 : 1) tc_small_kernel(const RunArgs a, int Kpad) {
+__global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_small_kernel(const RunArgs a, int Kpad) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
     constexpr int RL = CH * RPT;
     constexpr int NEPI = 4 * MT * CH;        // epilogue warps
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 32 * MT, CH == 1 ? 2 : 1) tc_s
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool ctl = warp >= NEPI;         // control warps
-    const int cw = warp - NEPI;            // control warp index = output tile it issues
+    const int cw = warp - NEPI;            // control warp: output tile cw % MT, K-step parity cw / MT
     const int q4 = warp & 3;               // TMEM lane quadrant this warp may access
     const int mt = (warp >> 2) % MT;       // output-spin tile
     const int ch = warp / (4 * MT);        // which RPT of the RL replicas
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 32 * MT, CH == 1 ? 2 : 1) tc_s
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(&sm->mbar, MT);          // one commit per output tile
+        mbar_init(&sm->mbar, 2 * MT);      // one commit per (output tile, K-step parity)
         fence_mbarrier_init();
     }
     // Couplings into A (zero-padded to MT*128 rows x Kpad columns), B cleared.
@@ -230,11 +230,12 @@ __global__ void __launch_bounds__(128 * MT * CH + 32 * MT, CH == 1 ? 2 : 1) tc_s
     // adding (byte offset >> 4) to the start-address field.
     const uint64_t adesc0 = smem_desc_noswizzle(smem_u32(sA), 128, SBO);
     const uint64_t bdesc0 = smem_desc_noswizzle(smem_u32(sB), 128, SBO);
-    auto issue_field = [&](int m) {
+    auto issue_field = [&](int w) {
         tc_fence_after();
+        const int m = w % MT, par = w / MT;
         const uint64_t am = adesc0 + (uint64_t)((m * 16 * SBO) >> 4);
 #pragma unroll 1
-        for (int ks = 0; ks < KS; ++ks) {
+        for (int ks = par; ks < KS; ks += 2) {
             const uint64_t bd = bdesc0 + (uint64_t)(ks * 16);   // 256 bytes per K-step
             const uint32_t d = tmem + (uint32_t)((2 * m + (ks & 1)) * kNB);
             if constexpr (AT) {
@@ -418,7 +419,7 @@ cudaError_t launch_cfg(const RunArgs &a, int Kpad, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (a.R + RL - 1) / RL;
-    kern<<<grid, 128 * MT * CH + 32 * MT, smem, st>>>(a, Kpad);
+    kern<<<grid, 128 * MT * CH + 64 * MT, smem, st>>>(a, Kpad);
     return cudaGetLastError();
 }
 

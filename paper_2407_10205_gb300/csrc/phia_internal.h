@@ -129,6 +129,10 @@ int batch_stats(phia_batch_s *b, int inst, phia_stats *out);
 // Thread-local error message of the C ABI.
 int set_last_error(int code, const char *msg);
 
+// int8 tensor-core resident kernel (mma.sync s8 x s8 -> s32) for small dense instances.
+int imma_small_max_n();
+cudaError_t launch_imma_small(const RunArgs &a, cudaStream_t st, int *launches);
+
 // Plain FP32 per-step path (the comparator).
 cudaError_t launch_fp32_run(const RunArgs &a, float *x, float *v, int8_t *s0, int8_t *s1,
                             int64_t *e_acc, cudaStream_t st, int *launches);

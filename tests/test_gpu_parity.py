@@ -22,11 +22,16 @@ TC_BF16 = ("tc", 2)
 TC_E4M3_TM = ("tc", 1, 2)   # couplings kept in tensor memory
 TC_BF16_TM = ("tc", 2, 2)
 FP32 = ("fp32", 0)
+IMMA8 = ("imma", 8)          # int8 mma.sync kernel, 8 replicas per CTA
+IMMA16 = ("imma", 16)
 
 
 def _handle(phia, d, path, frac=0):
     kind, op = path[0], path[1]
     mem = path[2] if len(path) > 2 else 0
+    if kind == "imma":
+        return phia.Annealer(d.k, d.kh, frac_bits=frac, path=phia.PATH_TC, tc_kernel=phia.KERNEL_IMMA,
+                             tile_replicas=op)
     p = phia.PATH_TC if kind == "tc" else phia.PATH_FP32
     return phia.Annealer(d.k, d.kh, frac_bits=frac, path=p, operand=op, coupling_mem=mem)
 
@@ -66,6 +71,8 @@ FIELD_CASES = [
     (FP32, 7, 5, 7, 7), (FP32, 200, 64, 7, 7), (FP32, 333, 19, 127, 50),
     (TC_E4M3_TM, 3, 1, 1, 0), (TC_E4M3_TM, 200, 64, 7, 7), (TC_E4M3_TM, 384, 16, 16, 5),
     (TC_BF16_TM, 5, 3, 127, 9), (TC_BF16_TM, 256, 48, 127, 127),
+    (IMMA8, 3, 1, 1, 0), (IMMA8, 33, 40, 127, 1 << 20), (IMMA8, 200, 64, 7, 7), (IMMA16, 256, 37, 127, 127),
+    (IMMA16, 100, 16, 127, 9),
 ]
 
 
@@ -86,7 +93,7 @@ def test_field_and_energy_bit_exact(gpu_lib, path, N, R, kmax, hmax):
 
 @pytest.mark.parametrize("path,N,kval", [(TC_E4M3, 384, 16), (TC_E4M3, 384, -16), (TC_BF16, 256, 127),
                                          (TC_BF16, 256, -127), (FP32, 384, 127), (TC_E4M3_TM, 384, 16),
-                                         (TC_BF16_TM, 256, -127)])
+                                         (TC_BF16_TM, 256, -127), (IMMA8, 256, 127), (IMMA16, 256, -127)])
 def test_field_extreme_magnitudes(gpu_lib, path, N, kval):
     """Every product of one sign at the largest exact |k|: the accumulator's largest
     partial sums (|I| = |k| (N - 1)) must stay exact; alternating states as well."""
@@ -124,7 +131,8 @@ def _safe_state(R, N, eps, seed):
 
 
 STEP_CASES = [(TC_E4M3, 16, 16, 1, 0, 0), (TC_E4M3, 200, 40, 7, 7, 0), (TC_BF16, 150, 20, 127, 31, 4),
-              (TC_E4M3, 333, 17, 16, 16, 3), (FP32, 200, 40, 7, 7, 0), (FP32, 77, 9, 127, 31, 4)]
+              (TC_E4M3, 333, 17, 16, 16, 3), (FP32, 200, 40, 7, 7, 0), (FP32, 77, 9, 127, 31, 4),
+              (IMMA8, 200, 40, 7, 7, 0), (IMMA16, 150, 20, 127, 31, 4)]
 
 
 @pytest.mark.parametrize("path,N,R,kmax,hmax,frac", STEP_CASES)
@@ -286,8 +294,11 @@ def test_tile_variants_bit_identical(gpu_lib, N, op):
     d = ins.dense_int(N, kmax, 7, seed=N)
     sched = phia.schedule(0.01, 0.2, 0.1, 2.0, refresh=40)
     outs = []
-    for tile, mem in ((4, 1), (8, 1), (16, 1), (4, 2), (8, 2), (16, 2)):
-        with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, operand=op, tile_replicas=tile, coupling_mem=mem) as A:
+    variants = [dict(tile_replicas=t, coupling_mem=m) for t, m in ((4, 1), (8, 1), (16, 1), (4, 2), (8, 2), (16, 2))]
+    if N <= 256:
+        variants += [dict(tile_replicas=8, tc_kernel=3), dict(tile_replicas=16, tc_kernel=3)]
+    for kw in variants:
+        with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, operand=op, **kw) as A:
             x = torch.empty((R, N), device="cuda"); v = torch.empty((R, N), device="cuda")
             phia.init_state(A.h, R, 17, x, v)
             phia.run(A.h, sched, R, 0, T, T, 17, x, v)
