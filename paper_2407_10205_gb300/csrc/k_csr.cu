@@ -55,6 +55,7 @@ __device__ __forceinline__ const uint32_t *spin_buf(const CsrArgs &C, const CsrI
 __global__ void __launch_bounds__(32 * kWarps) csr_step(const CsrArgs C) {
     __shared__ int32_t part[kWarps][kGroup];
     __shared__ uint32_t sbits[kRowsPerBlock][kGroup / 32];
+
     const RunArgs &a = C.a;
     const CsrBlock blk = C.blocks[blockIdx.x];
     const CsrInst in = C.inst[blk.inst];
@@ -102,31 +103,52 @@ __global__ void __launch_bounds__(32 * kWarps) csr_step(const CsrArgs C) {
         const int i = blk.i0 + warp * kRowsPerWarp + q;
         if (i >= N) break;
         const int p_beg = C.row_ptr[in.rp_off + i], p_end = C.row_ptr[in.rp_off + i + 1];
+        // sum_j k_j [s_j^r = +1] per replica r.  Two replicas share a 32-bit accumulator
+        // (low and high 16-bit halves, signed): the byte's bits are spread so that bit 2p
+        // sits at bit 0 and bit 2p+1 at bit 16 of word p, and one multiply-add by k adds
+        // k to both halves at once.  The low half stays below 2^15 in magnitude for up to
+        // 256 couplings (127 * 256 < 32768), so the sums are decoded every 256 couplings.
         int32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int32_t ksum = 0;
+        int32_t acc2[4] = {0, 0, 0, 0};
+        int since_flush = 0;
+        auto flush = [&]() {
+#pragma unroll
+            for (int q2 = 0; q2 < 4; ++q2) {
+                const int32_t lo = (int32_t)(int16_t)(acc2[q2] & 0xFFFF);
+                acc[2 * q2] += lo;
+                acc[2 * q2 + 1] += (acc2[q2] - lo) >> 16;
+                acc2[q2] = 0;
+            }
+        };
         for (int p0 = p_beg; p0 < p_end; p0 += 32) {
             const int p = p0 + lane;
             const int cj = p < p_end ? C.col[in.nz_off + p] : 0;
             const int kj = p < p_end ? (int)C.val[in.nz_off + p] : 0;
-            const int cnt = min(32, p_end - p0);
-            for (int e0 = 0; e0 < cnt; e0 += 8) {
+            const int cnt_chunk = min(32, p_end - p0);
+            if (since_flush + 32 > 256) { flush(); since_flush = 0; }
+            since_flush += 32;
+            for (int e0 = 0; e0 < cnt_chunk; e0 += 8) {
                 uint32_t bytes[8];
                 int ks[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int c = __shfl_sync(0xffffffffu, cj, (e0 + u) & 31);
                     ks[u] = __shfl_sync(0xffffffffu, kj, (e0 + u) & 31);
-                    if (e0 + u >= cnt) ks[u] = 0;
+                    if (e0 + u >= cnt_chunk) ks[u] = 0;
                     bytes[u] = Scur[(size_t)c * (RW * 4) + g * 32 + lane];
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     ksum += ks[u];
+                    const uint32_t t2 = bytes[u] | (bytes[u] << 15);
 #pragma unroll
-                    for (int rr = 0; rr < 8; ++rr) acc[rr] += ((bytes[u] >> rr) & 1u) ? ks[u] : 0;
+                    for (int q2 = 0; q2 < 4; ++q2)
+                        acc2[q2] += ks[u] * (int32_t)((t2 >> (2 * q2)) & 0x00010001u);
                 }
             }
         }
+        flush();
         const int32_t hk = C.hk[in.h_off + i];
         const size_t xo = in.x_off + (size_t)i * R + r0;
         float4 xa = *reinterpret_cast<const float4 *>(C.X + xo);
