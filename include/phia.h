@@ -209,9 +209,9 @@ int phia_philox_draws(uint64_t seed, uint32_t instance_id, uint32_t d, int32_t r
  * break the pool's accounting; others run a latency-critical loop in which cudaMalloc
  * and cudaFree are forbidden because they can synchronise the device and take unbounded
  * time.  Such callers own every input and output buffer, and this call takes its
- * scratch (the operand copy of J, the spin buffers, the energy sums) from one array of
- * 16 MiB compiled into the library, which every GPU that loads the library holds until
- * the process exits.
+ * scratch (the operand copy of J, the spin buffers, the energy sums, a working copy of
+ * x and v) from one array of 64 MiB compiled into the library, which every GPU that
+ * loads the library holds until the process exits.
  *
  * It runs the tensor-core path with one launch per iteration, exactly as phia_run does
  * on a handle created with tc_kernel = 2, and gives the same results.  All pointers are
@@ -221,7 +221,7 @@ int phia_philox_draws(uint64_t seed, uint32_t instance_id, uint32_t d, int32_t r
  * best_bits (replicas * ceil(N/32)), which reset_best = 1 initialises.  operand:
  * PHIA_OP_E4M3 (every |k| <= 16) or PHIA_OP_BF16 (AUTO means BF16).  stream: cudaStream_t
  * or NULL.  Sizes that need more scratch than the array holds (for example N = 2000 with
- * e4m3 and more than 1024 replicas) return PHIA_ERANGE.  The call allocates nothing:
+ * e4m3 and more than 2048 replicas) return PHIA_ERANGE.  The call allocates nothing:
  * no cudaMalloc, cudaFree or allocating library routine.  The first call on a device
  * looks up the array's device address once (cudaGetSymbolAddress), so make that first
  * call before any stream capture.  It returns after the work has finished (it

@@ -131,7 +131,8 @@ int ensure_replicas(phia_t *p, int R) {
         al((void **)&p->d_S, 4 * Rp * p->Kbytes);
         al((void **)&p->d_Epart, 2 * Rp * 8);
         al((void **)&p->d_flags, 2 * Rp);
-        al((void **)&p->d_X, RN * 4); al((void **)&p->d_V, RN * 4);
+        const size_t Mp = (size_t)round_up(p->N, 128);   // x, v in the interleaved [Rp/4][Mp][4] layout
+        al((void **)&p->d_X, Rp * Mp * 4); al((void **)&p->d_V, Rp * Mp * 4);
     }
     al((void **)&p->d_eacc, (size_t)R * 8);
     al((void **)&p->d_best_e, (size_t)R * 8);

@@ -56,17 +56,29 @@ __device__ __forceinline__ float draw_v(uint64_t seed, uint32_t inst, uint32_t r
 // Eq. 8's derivative factor 1 - tanh^2(y) = sech^2(y), evaluated through the identity
 // sech^2(y) = 4 e^{-2|y|} / (1 + e^{-2|y|})^2 with one fast exponential (relative error
 // a few 1e-6; it goes to 0 without cancellation for large |y|).
-__device__ __forceinline__ float sech2(float y) {
-    const float e = __expf(-2.0f * fabsf(y));
-    const float d = 1.0f + e;
-    return __fdividef(4.0f * e, d * d);
+// 2^x and 1/x by the hardware approximations (relative error about 2^-22; subnormal
+// results flush to 0, which changes nothing here: the term they scale is then far
+// below the rounding of v).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // Eq. A7 second line with the gradient of Eq. A8 under Eq. 8:
-//   v' = v + eps * (beta gamma (1 - tanh^2(gamma x)) q I - x),   bgq = beta * gamma * q.
+//   v' = v + eps * (beta gamma (1 - tanh^2(gamma x)) q I - x),   bgq = beta * gamma * q,
+// with 1 - tanh^2(y) = sech^2(y) = 4 e / (1 + e)^2, e = exp(-2 |y|) = 2^(-2 log2(e) |y|)
+// (e <= 1, so nothing overflows for any y).
 __device__ __forceinline__ float momentum_update(float v, float x, float I, float eps, float bgq,
                                                  float gamma) {
-    return v + eps * (bgq * sech2(gamma * x) * I - x);
+    const float e = ex2_approx(-2.8853900817779268f * fabsf(gamma * x));
+    const float d = 1.0f + e;
+    return v + eps * ((4.0f * bgq) * (e * rcp_approx(d * d)) * I - x);
 }
 
 // beta_t linear from beta0 (t = 0) to beta1 (t = T-1); inv_tm1 = 1 / (T - 1), 0 if T <= 1.
@@ -254,6 +266,28 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, uint64_
             smem_u32(dst)),
         "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Per-thread asynchronous 4-byte copy global -> shared; with `valid` false nothing is
+// read and the destination is zero-filled.
+__device__ __forceinline__ void cp_async_4(void *dst, const void *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+// Per-thread asynchronous 16-byte copy global -> shared (both 16-byte aligned), L2 only.
+__device__ __forceinline__ void cp_async_16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Wait until at most `n` of this thread's committed copy groups are still pending.
+template <int n>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(n) : "memory");
 }
 
 __device__ __forceinline__ void named_barrier_sync(uint32_t id, uint32_t threads) {

@@ -1,27 +1,37 @@
 // k_tc_large.cu -- tensor-core PHIA path for dense instances of any size: one launch per
-// iteration (Eq. A7), each CTA computing a 128-spin x 128-replica block of the field
-// I = J s + h (Eq. 6) and running the fused update on it.
+// iteration (Eq. A7).  The field I = J s + h (Eq. 6) is computed in 128-spin x
+// 128-replica output tiles, each followed by the fused update on that tile.
 //
+// The step kernel is persistent: one CTA per SM walks a static list of output tiles.
 // Operands (K-major, 128-byte swizzle, staged by TMA through a 3-deep mbarrier ring):
 //   A = couplings k re-encoded exactly (e4m3 or bf16), [Mpad][Kpad]
 //   B = spins of this iteration in the same encoding, [Rpad][Kpad], one of 4 rotating
 //       buffers (iteration t reads buffer t % 4 and writes t+1 % 4; buffers t-1 and t-2
 //       stay intact for the lagged best-state copies).
 // D = J s accumulates in TMEM (FP32, integer-valued, exact below 2^24): lane = output
-// spin, column = replica.
-// Warp roles: warp 0 issues TMA, warp 1 issues the MMAs (one thread each), warps 2-9 run
+// spin, column = replica; two accumulators, so the MMAs of a CTA's next tile run while
+// the epilogue drains the current one.
+// Warp roles: warp 0 issues TMA, warp 1 issues the MMAs (one thread each), warps 2-17 run
 // the epilogue: field + h, s (I + h) energy partials, momentum update (Eqs. 5, 8),
-// refresh, position update and the sign written as next iteration's B operand; x and v
-// stream from/to global memory ([R][N] FP32).
+// refresh, position update and the sign written as next iteration's B operand.
+// x and v live in a replica-interleaved layout [Rpad/4][Mpad][4] (FP32): the 4 replicas
+// of one group sit together for each spin, so a thread (one spin, an 8-replica chunk)
+// moves its values as two 16-byte vectors, a warp's vector covers 512 contiguous bytes,
+// and no padded element lies outside the array.
+// They reach the epilogue through a per-thread shared-memory ring filled by cp.async two
+// chunks ahead (across tile boundaries); results are stored straight to global memory.
+// The prologue converts a caller's [R][N] state in, an export kernel converts it out.
 // Records (Table 3, state 5) are lagged so no CTA waits for another: the launch for
-// iteration t lets the CTAs of output tile 0 settle the energies of iteration t-1 (sum
-// of every tile's partials) and every CTA copy, for replicas that improved at t-2, its
+// iteration t lets the tiles of output row 0 settle the energies of iteration t-1 (sum
+// of every tile's partials) and every tile copy, for replicas that improved at t-2, its
 // 128 spins of buffer t-2 into the bit-packed best state.  A final pair of launches
 // settles the last two iterations.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
+
+#include <algorithm>
 
 #include "device_common.cuh"
 #include "phia_internal.h"
@@ -30,33 +40,44 @@ namespace phia {
 
 namespace {
 
-constexpr int kBM = 128;       // output spins per CTA (TMEM lanes)
-constexpr int kBN = 128;       // replicas per CTA (TMEM columns)
+constexpr int kBM = 128;       // output spins per tile (TMEM lanes)
+constexpr int kBN = 128;       // replicas per tile (TMEM columns)
 constexpr int kBKB = 128;      // bytes of K per pipeline stage (one 128-byte swizzle row)
 constexpr int kStages = 3;
-constexpr int kEpiWarps = 8;   // two per TMEM lane quadrant, each half of the columns
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kEpiWarps = 16;  // four per TMEM lane quadrant, each a quarter of the columns
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kThreads = 64 + kEpiThreads;
+constexpr int kColsPerWarp = kBN / (kEpiWarps / 4);
+constexpr int kChunk = 8;                      // replica columns per epilogue step (two x/v groups)
+constexpr int kChunksPerTile = kColsPerWarp / kChunk;
+constexpr int kRing = 3;                       // x/v chunks per thread: the current + kRing - 1 ahead
 constexpr uint32_t kStageA = kBM * kBKB;
 constexpr uint32_t kStageB = kBN * kBKB;
+constexpr uint32_t kRingBytes = kRing * kChunk * kEpiThreads * 4;   // per array (x or v)
+static_assert(kChunk == 8, "a chunk is two 4-replica groups of the x/v layout");
+static_assert(kRing - 1 <= kChunksPerTile, "prefetch reaches at most into the next tile");
 
 struct LargeShared {
     uint64_t full[kStages];
     uint64_t empty[kStages];
-    uint64_t accf;
+    uint64_t accf[2];       // accumulator b holds a finished tile
+    uint64_t acce[2];       // accumulator b drained by the epilogue warps
+    uint64_t drain;         // every MMA issued has completed
     uint32_t tmem_base;
     int32_t timed_out;
-    int32_t part[4][kBN];   // per lane-quadrant warp sums of s_i (I_i + h_i)
+    int32_t part[2][4][kBN];   // per lane-quadrant warp sums of s_i (I_i + h_i), by accumulator
 };
 
-constexpr size_t kSmemBytes = 1024 + kStages * (kStageA + kStageB) + sizeof(LargeShared);
+constexpr size_t kSmemBytes = 1024 + kStages * (kStageA + kStageB) + 2 * kRingBytes + sizeof(LargeShared);
+static_assert(kSmemBytes <= 232448, "shared memory over the per-CTA limit");
 
 struct LargeArgs {
     RunArgs a;
     uint8_t *S;         // [4][Rpad][Kbytes] spin operand buffers
     int64_t *Epart;     // [2][Rpad] sums of s (I + h) over output tiles, by iteration parity
     int8_t *flags;      // [2][Rpad] improved at an iteration, by parity
-    float *X, *V;       // [R][N] state
-    int32_t Kbytes, Rpad, mtiles;
+    float *X, *V;       // [Rpad/4][Mp][4] state: replica r, spin i at ((r/4) Mp + i) 4 + r%4
+    int32_t Kbytes, Rpad, mtiles, ntiles, Mp;
     int64_t t;          // iteration of this launch
     int64_t t_first;    // first iteration of this call
 };
@@ -75,6 +96,71 @@ __device__ __forceinline__ bool spin_is_plus(const uint8_t *row, int i) {
     // The sign bit sits in the top byte of the encoding (e4m3: the byte; bf16: byte 1).
     if constexpr (OP == kOpE4M3) return (row[i] & 0x80) == 0;
     else return (row[2 * i + 1] & 0x80) == 0;
+}
+
+// Bit k set when spin k of the 32 encoded spins at p (16-byte aligned) is +1.
+template <int OP>
+__device__ __forceinline__ uint32_t plus_bits32(const uint8_t *p) {
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+    uint32_t bits = 0;
+    if constexpr (OP == kOpE4M3) {
+        // One byte per spin, sign in bit 7: gather the four inverted sign bits of a word
+        // into bits 24..27 of one product (the other partial products land below bit 20).
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint4 w = q[h];
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t b = ((~ws[k] & 0x80808080u) >> 7) * 0x01020408u;
+                bits |= ((b >> 24) & 0xFu) << (16 * h + 4 * k);
+            }
+        }
+    } else {
+        // Two bytes per spin, sign in bit 15 of each half-word.
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const uint4 w = q[h];
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t nw = ~ws[k];
+                bits |= (((nw >> 15) & 1u) | ((nw >> 30) & 2u)) << (8 * h + 2 * k);
+            }
+        }
+    }
+    return bits;
+}
+
+// One epilogue chunk of the accumulator: 32 lanes x kChunk consecutive columns.
+template <int C>
+__device__ __forceinline__ void tmem_ld_chunk(uint32_t taddr, float (&v)[C]) {
+    static_assert(C == 4 || C == 8 || C == 16, "unsupported chunk");
+    if constexpr (C == 16) tmem_ld_x16_sync(taddr, v);
+    else if constexpr (C == 8) tmem_ld_x8_sync(taddr, v);
+    else tmem_ld_x4_sync(taddr, v);
+}
+
+// Sums p[0..7] over the 32 lanes of the warp by halving exchanges: the result for
+// column (lane >> 2) & 7 ends up in every lane of that column's group of four.
+__device__ __forceinline__ int32_t warp_sum8(const int32_t (&p)[8], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    int32_t q[4], r[2];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int32_t send = b4 ? p[k] : p[k + 4], keep = b4 ? p[k + 4] : p[k];
+        q[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int32_t send = b3 ? q[k] : q[k + 2], keep = b3 ? q[k + 2] : q[k];
+        r[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const int32_t send = b2 ? r[0] : r[1], keep = b2 ? r[1] : r[0];
+    int32_t s = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    return s;
 }
 
 // Record step for replica r at iteration tt (Table 3, state 5): E from the sum the
@@ -98,7 +184,7 @@ __device__ __forceinline__ void settle_replica(const LargeArgs &L, int r, int64_
 }
 
 template <int OP>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
     tc_large_step(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const LargeArgs L) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
@@ -107,17 +193,21 @@ __global__ void __launch_bounds__(kThreads, 2)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = smem;
     uint8_t *sB = smem + kStages * kStageA;
-    LargeShared *sh = reinterpret_cast<LargeShared *>(sB + kStages * kStageB);
+    float *ring_x = reinterpret_cast<float *>(sB + kStages * kStageB);
+    float *ring_v = ring_x + kRingBytes / 4;
+    LargeShared *sh = reinterpret_cast<LargeShared *>(ring_v + kRingBytes / 4);
+    volatile int32_t *tout = &sh->timed_out;
 
     const RunArgs &a = L.a;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m = blockIdx.x, n = blockIdx.y;
+    const int G = gridDim.x;
+    const int my_tiles = (int)blockIdx.x < L.ntiles ? (L.ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
     const int64_t t = L.t;
     const int KB = L.Kbytes / kBKB;
     const int N = a.N, R = a.R;
 
     if (warp == 0) {
-        tmem_alloc(&sh->tmem_base, kBN);
+        tmem_alloc(&sh->tmem_base, 2 * kBN);
         tmem_relinquish();
     }
     if (tid == 32) {
@@ -125,7 +215,11 @@ __global__ void __launch_bounds__(kThreads, 2)
             mbar_init(&sh->full[s], 1);
             mbar_init(&sh->empty[s], 1);
         }
-        mbar_init(&sh->accf, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sh->accf[b], 1);
+            mbar_init(&sh->acce[b], kEpiWarps);
+        }
+        mbar_init(&sh->drain, 1);
         sh->timed_out = 0;
         fence_mbarrier_init();
     }
@@ -135,194 +229,281 @@ __global__ void __launch_bounds__(kThreads, 2)
     const uint32_t tmem = sh->tmem_base;
 
     if (warp == 0) {
-        // TMA producer.
+        // TMA producer: the k-blocks of every tile of this CTA through one ring.
         if (lane == 0) {
-            const int ybuf = (int)(t & 3) * L.Rpad + n * kBN;
-            for (int kb = 0; kb < KB; ++kb) {
-                const int s = kb % kStages;
-                if (kb >= kStages && !mbar_wait_bounded(&sh->empty[s], ((kb / kStages) - 1) & 1, kWaitTimeoutNs)) {
-                    sh->timed_out = 1;
-                    break;
+            int64_t kg = 0;
+            bool ok = true;
+            for (int lt = 0; lt < my_tiles && ok; ++lt) {
+                const int tile = (int)blockIdx.x + lt * G;
+                const int m = tile % L.mtiles, n = tile / L.mtiles;
+                const int ybuf = (int)(t & 3) * L.Rpad + n * kBN;
+                for (int kb = 0; kb < KB; ++kb, ++kg) {
+                    const int s = (int)(kg % kStages);
+                    if (kg >= kStages &&
+                        (*tout || !mbar_wait_bounded(&sh->empty[s], (uint32_t)((kg / kStages) - 1) & 1u, kWaitTimeoutNs))) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&sh->full[s], kStageA + kStageB);
+                    tma_load_2d(sA + s * kStageA, &tmA, &sh->full[s], kb * (kBKB / ESZ), m * kBM);
+                    tma_load_2d(sB + s * kStageB, &tmB, &sh->full[s], kb * (kBKB / ESZ), ybuf);
                 }
-                mbar_arrive_expect_tx(&sh->full[s], kStageA + kStageB);
-                tma_load_2d(sA + s * kStageA, &tmA, &sh->full[s], kb * (kBKB / ESZ), m * kBM);
-                tma_load_2d(sB + s * kStageB, &tmB, &sh->full[s], kb * (kBKB / ESZ), ybuf);
             }
+            if (!ok) *tout = 1;
+            // Copies still in flight (only after a timeout) land before the CTA exits.
+            for (int64_t k = kg > kStages ? kg - kStages : 0; k < kg; ++k)
+                mbar_wait_bounded(&sh->full[k % kStages], (uint32_t)(k / kStages) & 1u, kWaitTimeoutNs);
         }
     } else if (warp == 1) {
-        // MMA issuer: 4 K-steps of 32 bytes per stage.
+        // MMA issuer: 4 K-steps of 32 bytes per stage, accumulators alternating per tile.
         if (lane == 0) {
+            int64_t kg = 0;
             bool ok = true;
-            for (int kb = 0; kb < KB; ++kb) {
-                const int s = kb % kStages;
-                if (!mbar_wait_bounded(&sh->full[s], (kb / kStages) & 1, kWaitTimeoutNs)) {
+            for (int lt = 0; lt < my_tiles && ok; ++lt) {
+                const int b = lt & 1;
+                if (lt >= 2 && (*tout || !mbar_wait_bounded(&sh->acce[b], (uint32_t)((lt >> 1) - 1) & 1u, kWaitTimeoutNs))) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint64_t ad = smem_desc_sw128(smem_u32(sA + s * kStageA));
-                const uint64_t bd = smem_desc_sw128(smem_u32(sB + s * kStageB));
+                const uint32_t dt = tmem + (uint32_t)(b * kBN);
+                for (int kb = 0; kb < KB; ++kb, ++kg) {
+                    const int s = (int)(kg % kStages);
+                    if (*tout || !mbar_wait_bounded(&sh->full[s], (uint32_t)(kg / kStages) & 1u, kWaitTimeoutNs)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t ad = smem_desc_sw128(smem_u32(sA + s * kStageA));
+                    const uint64_t bd = smem_desc_sw128(smem_u32(sB + s * kStageB));
 #pragma unroll
-                for (int k = 0; k < kBKB / 32; ++k) {
-                    if constexpr (OP == kOpE4M3) mma_e4m3(tmem, ad + 2 * k, bd + 2 * k, IDESC, (kb | k) != 0);
-                    else mma_bf16(tmem, ad + 2 * k, bd + 2 * k, IDESC, (kb | k) != 0);
+                    for (int k = 0; k < kBKB / 32; ++k) {
+                        if constexpr (OP == kOpE4M3) mma_e4m3(dt, ad + 2 * k, bd + 2 * k, IDESC, (kb | k) != 0);
+                        else mma_bf16(dt, ad + 2 * k, bd + 2 * k, IDESC, (kb | k) != 0);
+                    }
+                    mma_commit(&sh->empty[s]);
                 }
-                mma_commit(&sh->empty[s]);
+                if (ok) mma_commit(&sh->accf[b]);
             }
-            if (!ok) sh->timed_out = 1;
-            mma_commit(&sh->accf);
+            if (!ok) *tout = 1;
+            // Every MMA issued has completed before the accumulators are released.
+            mma_commit(&sh->drain);
+            mbar_wait_bounded(&sh->drain, 0, kWaitTimeoutNs);
         }
     } else {
-        // Epilogue warps.
+        // Epilogue warps: warp w reads TMEM lane quadrant w % 4 and column group (w - 2) / 4;
+        // thread et owns spin i of its quadrant and 32 replica columns (4 chunks) per tile.
         const int ew = warp - 2;
         const int q4 = warp & 3;
-        const int half = ew >> 2;
-        const int i = m * kBM + q4 * 32 + lane;
-        const bool live_i = i < N;
+        const int cg = ew >> 2;
         const int et = ew * 32 + lane;
-
-        // (a) records of iteration t-1 for this replica tile (output tile 0 only).
-        if (m == 0 && t - 1 >= L.t_first && et < kBN) {
-            const int r = n * kBN + et;
-            if (r < R) settle_replica(L, r, t - 1);
-        }
-        // (b) best spins of iteration t-2 for the replicas that improved then.
-        if (t - 2 >= L.t_first) {
-            const int rb = n * kBN + half * 64;
-            const int8_t *F = L.flags + (size_t)((t - 2) & 1) * L.Rpad;
-            const bool f0 = rb + lane < R && F[rb + lane];
-            const bool f1 = rb + 32 + lane < R && F[rb + 32 + lane];
-            uint64_t todo = (uint64_t)__ballot_sync(0xffffffffu, f0) | ((uint64_t)__ballot_sync(0xffffffffu, f1) << 32);
-            const uint8_t *Sb = L.S + (size_t)((t - 2) & 3) * L.Rpad * L.Kbytes;
-            const int word = (m * kBM + q4 * 32) >> 5;
-            while (todo) {
-                // Up to 8 replicas per round, their loads in flight together.
-                int js[8];
-                bool plus[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    js[u] = todo ? __ffsll((long long)todo) - 1 : -1;
-                    if (todo) todo &= todo - 1;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    plus[u] = js[u] >= 0 && live_i && spin_is_plus<OP>(Sb + (size_t)(rb + js[u]) * L.Kbytes, i);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (js[u] < 0) break;
-                    const uint32_t bits = __ballot_sync(0xffffffffu, plus[u]);
-                    if (lane == 0 && word < a.W) a.best_bits[(size_t)(rb + js[u]) * a.W + word] = bits;
-                }
+        const int Mp = L.Mp;
+        // Ring slot s holds a chunk's x (and v) as two 16-byte halves per thread at
+        // float4 index (2 s + h) * kEpiThreads + et.
+        float4 *rx4 = reinterpret_cast<float4 *>(ring_x) + et;
+        float4 *rv4 = reinterpret_cast<float4 *>(ring_v) + et;
+        // Float offset of this thread's first 4 values of chunk c of tile (m, n); the
+        // other 4 (the next replica group) follow at + 4 Mp.
+        const size_t grp_stride = (size_t)Mp * 4;
+        auto xv_offset = [&](int m_, int n_, int c_) -> size_t {
+            const int grp = (n_ * kBN + cg * kColsPerWarp + c_ * kChunk) >> 2;
+            return ((size_t)grp * Mp + (m_ * kBM + q4 * 32 + lane)) * 4;
+        };
+        auto issue = [&](size_t off, int slot) {
+            cp_async_16(rx4 + (2 * slot) * kEpiThreads, L.X + off);
+            cp_async_16(rx4 + (2 * slot + 1) * kEpiThreads, L.X + off + grp_stride);
+            cp_async_16(rv4 + (2 * slot) * kEpiThreads, L.V + off);
+            cp_async_16(rv4 + (2 * slot + 1) * kEpiThreads, L.V + off + grp_stride);
+        };
+        int m_cur = (int)blockIdx.x % L.mtiles, n_cur = (int)blockIdx.x / L.mtiles;
+        if (!a.field_mode)
+            for (int c0 = 0; c0 < kRing - 1; ++c0) {
+                issue(xv_offset(m_cur, n_cur, c0), c0);
+                cp_async_commit();
             }
-        }
-        // (c) the field of this iteration.  x and v of a 16-replica chunk are loaded
-        // together (predicated, all in flight at once); chunk 0 before the MMAs finish.
-        const int32_t hki = live_i ? a.hk[i] : 0;
         const float bgq = beta_at(t, inv_tm1_of(a.T_total), a.beta0, a.beta1) * (a.gamma * a.q);
         const float eps = a.eps, gamma = a.gamma;
         const bool more = t + 1 < L.t_first + a.nsteps;
         const bool refresh_next = more && refresh_at(t + 1, a.refresh);
         uint8_t *Sn = L.S + (size_t)((t + 1) & 3) * L.Rpad * L.Kbytes;
-        const uint32_t tbase = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(half * 64);
-        const int rc0 = n * kBN + half * 64;   // first replica of this warp's columns
-        float xs[16], vs[16];
-        auto load_chunk = [&](int c) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int r = rc0 + c * 16 + j;
-                const bool lv = live_i && r < R;
-                const size_t idx = (size_t)r * N + i;
-                xs[j] = lv ? L.X[idx] : 0.0f;
-                vs[j] = lv ? L.V[idx] : 0.0f;
+        int slot = 0;                                   // ring slot of the current chunk
+        for (int lt = 0; lt < my_tiles; ++lt) {
+            const int m = m_cur, n = n_cur;
+            const int b = lt & 1;
+            const int nxt_tile = (int)blockIdx.x + (lt + 1) * G;
+            const bool has_nxt = lt + 1 < my_tiles;
+            const int m_nxt = nxt_tile % L.mtiles, n_nxt = nxt_tile / L.mtiles;
+            const int i = m * kBM + q4 * 32 + lane;
+            const bool live_i = i < N;
+            // (a) records of iteration t-1 for this replica tile (output row 0 only).
+            if (m == 0 && t - 1 >= L.t_first && et < kBN) {
+                const int r = n * kBN + et;
+                if (r < R) settle_replica(L, r, t - 1);
             }
-        };
-        if (!a.field_mode) load_chunk(0);
-        const bool ok = mbar_wait_bounded(&sh->accf, 0, kWaitTimeoutNs);
-        if (!ok) sh->timed_out = 1;
-        tc_fence_after();
+            // (b) best spins of iteration t-2 for the replicas that improved then: lane l
+            // packs the 32 spins of this warp's quadrant for replica rb + l.
+            if (t - 2 >= L.t_first) {
+                const int rb = n * kBN + cg * kColsPerWarp;
+                const int8_t *F = L.flags + (size_t)((t - 2) & 1) * L.Rpad;
+                const uint8_t *Sb = L.S + (size_t)((t - 2) & 3) * L.Rpad * L.Kbytes;
+                const int i0 = m * kBM + q4 * 32;
+                if (i0 < N) {
+                    const uint32_t valid = N - i0 >= 32 ? 0xffffffffu : ((1u << (N - i0)) - 1u);
+#pragma unroll
+                    for (int u = 0; u < kColsPerWarp / 32; ++u) {
+                        const int r = rb + u * 32 + lane;
+                        if (r < R && F[r])
+                            a.best_bits[(size_t)r * a.W + (i0 >> 5)] =
+                                plus_bits32<OP>(Sb + (size_t)r * L.Kbytes + (size_t)i0 * ESZ) & valid;
+                    }
+                }
+            }
+            // (c) the field of this iteration and the update.
+            const int32_t hki = live_i ? a.hk[i] : 0;
+            const int rc0 = n * kBN + cg * kColsPerWarp;          // first replica of this warp's columns
+            const int ncol = max(0, min(kColsPerWarp, R - rc0));   // live replica columns of this warp
+            uint8_t *sb = Sn + (size_t)rc0 * L.Kbytes + (size_t)i * ESZ;
+            // Warp-uniform, as the TMEM loads below are warp-collective.
+            const bool ok = __all_sync(0xffffffffu, !*tout && mbar_wait_bounded(&sh->accf[b], (uint32_t)(lt >> 1) & 1u,
+                                                                               kWaitTimeoutNs));
+            if (!ok) *tout = 1;
+            tc_fence_after();
+            const uint32_t tbase = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * kBN + cg * kColsPerWarp);
 #pragma unroll 1
-        for (int c = 0; c < 4; ++c) {
-            float acc[16];
-            tmem_ld_x16_sync(tbase + c * 16, acc);
-            if (a.field_mode) {
+            for (int c = 0; c < kChunksPerTile; ++c) {
+                const int col0 = c * kChunk;               // first column of the chunk in this warp's group
+                if (a.field_mode) {
+                    float acc[kChunk];
+                    if (ok) tmem_ld_chunk(tbase + col0, acc);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int r = rc0 + c * 16 + j;
-                    int32_t part = 0;
-                    if (live_i && r < R && ok) {
-                        const size_t idx = (size_t)r * N + i;
-                        const int32_t Ik = __float2int_rn(acc[j]) + hki;
-                        part = (a.spins_in[idx] > 0 ? 1 : -1) * (Ik + hki);
-                        if (a.field_out) a.field_out[idx] = Ik;
+                    for (int j = 0; j < kChunk; ++j) {
+                        const int r = rc0 + col0 + j;
+                        int32_t part = 0;
+                        if (live_i && r < R && ok) {
+                            const size_t idx = (size_t)r * N + i;
+                            const int32_t Ik = __float2int_rn(acc[j]) + hki;
+                            part = (a.spins_in[idx] > 0 ? 1 : -1) * (Ik + hki);
+                            if (a.field_out) a.field_out[idx] = Ik;
+                        }
+                        part = __reduce_add_sync(0xffffffffu, part);
+                        if (lane == 0) sh->part[b][q4][cg * kColsPerWarp + col0 + j] = part;
                     }
-                    part = __reduce_add_sync(0xffffffffu, part);
-                    if (lane == 0) sh->part[q4][half * 64 + c * 16 + j] = part;
+                    continue;
                 }
-                continue;
-            }
-            if (c > 0) load_chunk(c);
+                // Keep kRing - 1 chunks in flight: this tile's later chunks, then the next tile's.
+                {
+                    const int ca = c + kRing - 1;
+                    const int sa = slot + kRing - 1 >= kRing ? slot - 1 : slot + kRing - 1;
+                    if (ca < kChunksPerTile) issue(xv_offset(m, n, ca), sa);
+                    else if (has_nxt) issue(xv_offset(m_nxt, n_nxt, ca - kChunksPerTile), sa);
+                    cp_async_commit();
+                }
+                cp_async_wait<kRing - 1>();
+                const int sc = slot;
+                slot = slot + 1 == kRing ? 0 : slot + 1;
+                if (!ok) continue;
+                float acc[kChunk];
+                tmem_ld_chunk(tbase + col0, acc);
+                const float4 x0 = rx4[(2 * sc) * kEpiThreads], x1 = rx4[(2 * sc + 1) * kEpiThreads];
+                const float4 v0 = rv4[(2 * sc) * kEpiThreads], v1 = rv4[(2 * sc + 1) * kEpiThreads];
+                const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                float vs[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                const int nlive = live_i ? ncol - col0 : 0;   // live columns of this chunk for this thread
+                int32_t p[8];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int r = rc0 + c * 16 + j;
-                const bool lv = live_i && r < R && ok;
-                const int32_t Ik = __float2int_rn(acc[j]) + hki;            // Eq. 6, exact
-                float x = xs[j], v = vs[j];
-                int32_t part = lv ? (x >= 0.0f ? 1 : -1) * (Ik + hki) : 0;
-                v = momentum_update(v, x, (float)Ik, eps, bgq, gamma);
+                for (int j = 0; j < kChunk; ++j) {
+                    const int32_t Ik = __float2int_rn(acc[j]) + hki;            // Eq. 6, exact
+                    const int32_t e = Ik + hki;
+                    p[j] = j < nlive ? (xs[j] >= 0.0f ? e : -e) : 0;
+                    vs[j] = momentum_update(vs[j], xs[j], (float)Ik, eps, bgq, gamma);
+                }
+                const int32_t psum = warp_sum8(p, lane);
+                if ((lane & 3) == 0) sh->part[b][q4][cg * kColsPerWarp + col0 + (lane >> 2)] = psum;
+                if (refresh_next) {
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j)
+                        vs[j] = draw_v(a.seed, a.inst, (uint32_t)(rc0 + col0 + j), (uint32_t)i, (uint32_t)(t + 1));
+                }
+                // Padding elements (i >= N or replica >= R) are stored too: they stay inside
+                // the array and no record reads them.
+                const size_t off = xv_offset(m, n, c);
                 if (more) {
-                    if (refresh_next && lv) v = draw_v(a.seed, a.inst, (uint32_t)r, (uint32_t)i, (uint32_t)(t + 1));
-                    x = x + eps * v;
+                    float xn[8];
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j) xn[j] = xs[j] + eps * vs[j];
+                    *reinterpret_cast<float4 *>(L.X + off) = make_float4(xn[0], xn[1], xn[2], xn[3]);
+                    *reinterpret_cast<float4 *>(L.X + off + grp_stride) = make_float4(xn[4], xn[5], xn[6], xn[7]);
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j)
+                        if (j < nlive) put_spin_byte<OP>(sb + (size_t)(col0 + j) * L.Kbytes, 0, xn[j] >= 0.0f);
                 }
-                if (lv) {
-                    const size_t idx = (size_t)r * N + i;
-                    if (more) {
-                        L.X[idx] = x;
-                        put_spin_byte<OP>(Sn + (size_t)r * L.Kbytes, i, x >= 0.0f);
-                    }
-                    L.V[idx] = v;
-                }
-                part = __reduce_add_sync(0xffffffffu, part);
-                if (lane == 0) sh->part[q4][half * 64 + c * 16 + j] = part;
+                *reinterpret_cast<float4 *>(L.V + off) = make_float4(vs[0], vs[1], vs[2], vs[3]);
+                *reinterpret_cast<float4 *>(L.V + off + grp_stride) = make_float4(vs[4], vs[5], vs[6], vs[7]);
             }
+            // Accumulator b is free for the tile after next.
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh->acce[b]);
+            named_barrier_sync(1, kEpiThreads);
+            if (et < kBN) {
+                const int r = n * kBN + et;
+                const long long s4 =
+                    (long long)sh->part[b][0][et] + sh->part[b][1][et] + sh->part[b][2][et] + sh->part[b][3][et];
+                if (ok) atomicAdd(reinterpret_cast<unsigned long long *>(L.Epart) + (size_t)(t & 1) * L.Rpad + r,
+                                  (unsigned long long)s4);
+            }
+            m_cur = m_nxt;
+            n_cur = n_nxt;
         }
-        named_barrier_sync(1, 32 * kEpiWarps);
-        if (et < kBN) {
-            const int r = n * kBN + et;
-            const long long s4 = (long long)sh->part[0][et] + sh->part[1][et] + sh->part[2][et] + sh->part[3][et];
-            atomicAdd(reinterpret_cast<unsigned long long *>(L.Epart) + (size_t)(t & 1) * L.Rpad + r,
-                      (unsigned long long)s4);
-        }
+        cp_async_wait<0>();
     }
     tc_fence_before();
     __syncthreads();
     if (tid == 0 && sh->timed_out) atomicExch(a.err, 1);
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, kBN);
+        tmem_dealloc(tmem, 2 * kBN);
     }
 }
 
-// Initial state (or given), refresh at t0, first position update, spins of iteration t0.
+// Initial state (or given), refresh at t0, first position update, spins of iteration t0;
+// one thread per element of the padded interleaved x/v arrays (padding set to 0).
 template <int OP>
 __global__ void tc_large_prologue(const LargeArgs L) {
     const RunArgs &a = L.a;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)a.R * a.N) return;
-    const int r = (int)(idx / a.N), i = (int)(idx - (int64_t)r * a.N);
-    float x, v;
-    if (a.x_in) {
-        x = a.x_in[idx];
-        v = a.v_in[idx];
-    } else {
-        const U4 o = draw_raw(a.seed, a.inst, (uint32_t)r, (uint32_t)i, 0u);
-        x = box_muller(o.x, o.y);
-        v = box_muller(o.z, o.w);
+    if (idx >= (int64_t)L.Rpad * L.Mp) return;
+    const int64_t gi = idx >> 2;                       // (group, spin)
+    const int grp = (int)(gi / L.Mp), i = (int)(gi - (int64_t)grp * L.Mp);
+    const int r = grp * 4 + (int)(idx & 3);
+    float x = 0.0f, v = 0.0f;
+    if (r < a.R && i < a.N) {
+        const size_t src = (size_t)r * a.N + i;
+        if (a.x_in) {
+            x = a.x_in[src];
+            v = a.v_in[src];
+        } else {
+            const U4 o = draw_raw(a.seed, a.inst, (uint32_t)r, (uint32_t)i, 0u);
+            x = box_muller(o.x, o.y);
+            v = box_muller(o.z, o.w);
+        }
+        if (refresh_at(a.t0, a.refresh)) v = draw_v(a.seed, a.inst, (uint32_t)r, (uint32_t)i, (uint32_t)a.t0);
+        x = x + a.eps * v;
+        put_spin_byte<OP>(L.S + ((size_t)(a.t0 & 3) * L.Rpad + r) * L.Kbytes, i, x >= 0.0f);
     }
-    if (refresh_at(a.t0, a.refresh)) v = draw_v(a.seed, a.inst, (uint32_t)r, (uint32_t)i, (uint32_t)a.t0);
-    x = x + a.eps * v;
     L.X[idx] = x;
     L.V[idx] = v;
-    put_spin_byte<OP>(L.S + ((size_t)(a.t0 & 3) * L.Rpad + r) * L.Kbytes, i, x >= 0.0f);
+}
+
+// Final state back to the caller's [R][N] arrays.
+__global__ void tc_large_export(const LargeArgs L) {
+    const RunArgs &a = L.a;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)a.R * a.N) return;
+    const int r = (int)(idx / a.N), i = (int)(idx - (int64_t)r * a.N);
+    const size_t src = ((size_t)(r >> 2) * L.Mp + i) * 4 + (r & 3);
+    if (a.x_out) a.x_out[idx] = L.X[src];
+    if (a.v_out) a.v_out[idx] = L.V[src];
 }
 
 // Field-only mode: spins given, field and energy out (no records).
@@ -410,9 +591,11 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
     L.Kbytes = B.Kbytes;
     L.Rpad = B.Rpad;
     L.mtiles = B.Mpad / kBM;
+    L.ntiles = L.mtiles * (B.Rpad / kBN);
     L.t_first = a.t0;
-    L.X = a.x_out ? a.x_out : B.X;
-    L.V = a.v_out ? a.v_out : B.V;
+    L.X = B.X;
+    L.V = B.V;
+    L.Mp = B.Mpad;
     CUtensorMap tmA, tmB;
     const int esz = OP == kOpE4M3 ? 1 : 2;
     if (!make_map(&tmA, B.Jop, OP, (uint64_t)B.Kbytes / esz, (uint64_t)B.Mpad, (uint64_t)B.Kbytes, kBM) ||
@@ -421,7 +604,11 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
     auto step = tc_large_step<OP>;
     cudaError_t e = cudaFuncSetAttribute(step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    const dim3 grid(B.Mpad / kBM, B.Rpad / kBN);
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)std::min(L.ntiles, std::max(sms, 1)));
     e = cudaMemsetAsync(B.Epart, 0, 2 * (size_t)B.Rpad * sizeof(int64_t), st);   // energy sums start at 0
     if (e != cudaSuccess) return e;
     const int64_t RN = (int64_t)a.R * a.N;
@@ -439,7 +626,8 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
         if (launches) *launches += n;
         return cudaGetLastError();
     }
-    tc_large_prologue<OP><<<eg, 256, 0, st>>>(L);
+    const int64_t RMp = (int64_t)B.Rpad * B.Mpad;
+    tc_large_prologue<OP><<<(unsigned)((RMp + 255) / 256), 256, 0, st>>>(L);
     ++n;
     for (int64_t t = a.t0; t < a.t0 + a.nsteps; ++t) {
         L.t = t;
@@ -453,6 +641,10 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
                                                                      t_last);
     tc_large_count<<<1, 32, 0, st>>>(L);
     n += 3;
+    if (a.x_out || a.v_out) {
+        tc_large_export<<<eg, 256, 0, st>>>(L);
+        ++n;
+    }
     if (launches) *launches += n;
     return cudaGetLastError();
 }

@@ -15,7 +15,7 @@ namespace {
 
 // Scratch of phia_run_noalloc.  Every GPU on which the library's module is loaded holds
 // this array until the process exits; all calls share it.
-constexpr size_t kScratchBytes = (size_t)16 << 20;
+constexpr size_t kScratchBytes = (size_t)64 << 20;
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 128;
@@ -77,19 +77,23 @@ extern "C" int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N
         return set_last_error(PHIA_EINVAL, "phia_run_noalloc: invalid schedule");
     const int op = operand == PHIA_OP_E4M3 ? kOpE4M3 : kOpBF16;   // AUTO: bf16, exact for every int8 k
 
-    // Scratch layout: operand J, 4 spin buffers, energy sums, flags, run counters.
+    // Scratch layout: operand J, 4 spin buffers, energy sums, flags, run counters, and the
+    // working x, v in the kernel's interleaved layout (the caller's x, v are read at the
+    // start and written at the end).
     const int Mpad = round_up(N, 128), Kbytes = large_kbytes(N, op), Rpad = round_up(replicas, 128);
     const size_t off_jop = 0;
     const size_t off_s = off_jop + align256((size_t)Mpad * Kbytes);
     const size_t off_e = off_s + align256((size_t)4 * Rpad * Kbytes);
     const size_t off_f = off_e + align256((size_t)2 * Rpad * sizeof(int64_t));
     const size_t off_c = off_f + align256((size_t)2 * Rpad);
-    const size_t need = off_c + 256;
+    const size_t off_x = off_c + 256;
+    const size_t off_v = off_x + align256((size_t)Rpad * Mpad * 4);
+    const size_t need = off_v + align256((size_t)Rpad * Mpad * 4);
     if (need > kScratchBytes) {
         char msg[256];
         snprintf(msg, sizeof msg,
                  "phia_run_noalloc: N = %d and %d replicas need %zu bytes of scratch; the fixed scratch holds %zu "
-                 "(e.g. N <= 2000 with e4m3 and up to 1024 replicas)",
+                 "(e.g. N <= 2000 with e4m3 and up to 2048 replicas)",
                  N, replicas, need, kScratchBytes);
         return set_last_error(PHIA_ERANGE, msg);
     }
@@ -107,7 +111,7 @@ extern "C" int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N
     };
     // The array keeps the previous call's contents: clear what must start at zero (the
     // spin buffers' padding, the energy sums, the flags and the counters).
-    cudaError_t e = cudaMemsetAsync(base + off_s, 0, need - off_s, st);
+    cudaError_t e = cudaMemsetAsync(base + off_s, 0, off_x - off_s, st);
     if (e != cudaSuccess) return cuda_fail(e);
     e = launch_convert_operand(J_k, N, base + off_jop, Mpad, Kbytes, op, st);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -146,7 +150,8 @@ extern "C" int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N
     B.S = base + off_s;
     B.Epart = reinterpret_cast<int64_t *>(base + off_e);
     B.flags = reinterpret_cast<int8_t *>(base + off_f);
-    B.X = x; B.V = v;
+    B.X = reinterpret_cast<float *>(base + off_x);
+    B.V = reinterpret_cast<float *>(base + off_v);
     B.Kbytes = Kbytes; B.Mpad = Mpad; B.Rpad = Rpad;
     int launches = 0;
     e = launch_tc_large(B, a, op, st, &launches);

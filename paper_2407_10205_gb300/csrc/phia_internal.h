@@ -58,7 +58,7 @@ struct LargeBuffers {
     uint8_t *S;           // [4][Rpad][Kbytes] spin operand buffers (zero padding)
     int64_t *Epart;       // [2][Rpad], zero between uses
     int8_t *flags;        // [2][Rpad]
-    float *X, *V;         // [R][N] state when the caller gives none
+    float *X, *V;         // [Rpad/4][Mpad][4] working state (replica groups of 4 interleaved per spin)
     int32_t Kbytes, Mpad, Rpad;
 };
 cudaError_t launch_tc_large(const LargeBuffers &B, const RunArgs &a, int op, cudaStream_t st, int *launches);

@@ -25,7 +25,8 @@ def _field(phia, A, S):
 
 @pytest.mark.parametrize("N,R,kmax,hmax,op", [
     (5, 1, 7, 7, 1), (130, 129, 16, 100, 1), (257, 260, 7, 7, 1), (700, 40, 16, 1 << 20, 1),
-    (2000, 130, 1, 0, 1), (150, 3, 127, 127, 2), (640, 129, 127, 31, 2)])
+    (2000, 130, 1, 0, 1), (150, 3, 127, 127, 2), (640, 129, 127, 31, 2),
+    (640, 10240, 16, 100, 1)])   # 400 output tiles: several per CTA of the persistent kernel
 def test_large_field_bit_exact(gpu_lib, N, R, kmax, hmax, op):
     phia = gpu_lib
     d = ins.dense_int(N, kmax, hmax, seed=N + R)
@@ -77,10 +78,12 @@ def test_large_single_step_matches_oracle(gpu_lib):
         assert np.all(np.abs(vg[r] - vo) <= 1e-5 * np.maximum(scale, 1e-3))
 
 
-@pytest.mark.parametrize("N,op,R", [(200, 1, 50), (130, 2, 140)])
+@pytest.mark.parametrize("N,op,R", [(200, 1, 50), (130, 2, 140), (256, 1, 40000), (130, 2, 40000)])
 def test_large_equals_resident_kernel(gpu_lib, N, op, R):
     """The per-iteration and the resident kernel do the same arithmetic per replica:
-    records and final states are bit-identical."""
+    records and final states are bit-identical (R = 40000: over 600 output tiles, so
+    each CTA of the persistent per-iteration kernel runs several and reuses both of its
+    accumulators)."""
     phia = gpu_lib
     T = 120
     d = ins.dense_int(N, 7 if op == 1 else 90, 7, seed=N)
