@@ -127,7 +127,7 @@ int ensure_replicas(phia_t *p, int R) {
         al((void **)&p->d_s0, RN); al((void **)&p->d_s1, RN);
     }
     if (p->large) {
-        const size_t Rp = (size_t)round_up(R, 128);
+        const size_t Rp = (size_t)large_rpad(R);
         al((void **)&p->d_S, 4 * Rp * p->Kbytes);
         al((void **)&p->d_Epart, 2 * Rp * 8);
         al((void **)&p->d_flags, 2 * Rp);
@@ -147,7 +147,7 @@ int ensure_replicas(phia_t *p, int R) {
     p->cap_large = p->large;
     CU(cudaMemsetAsync(p->d_eacc, 0, (size_t)R * 8, p->stream));
     if (p->large) {
-        const size_t Rp = (size_t)round_up(R, 128);
+        const size_t Rp = (size_t)large_rpad(R);
         CU(cudaMemsetAsync(p->d_S, 0, 4 * Rp * p->Kbytes, p->stream));   // K and replica padding stay 0
         CU(cudaMemsetAsync(p->d_flags, 0, 2 * Rp, p->stream));
         CU(cudaMemsetAsync(p->d_Epart, 0, 2 * Rp * 8, p->stream));
@@ -244,7 +244,7 @@ cudaError_t launch_path(phia_t *p, const RunArgs &a, int *launches) {
     if (p->path == PHIA_PATH_TC && p->large) {
         LargeBuffers B;
         B.Jop = p->d_Jop; B.S = p->d_S; B.Epart = p->d_Epart; B.flags = p->d_flags;
-        B.X = p->d_X; B.V = p->d_V; B.Kbytes = p->Kbytes; B.Mpad = p->Mpad; B.Rpad = round_up(a.R, 128);
+        B.X = p->d_X; B.V = p->d_V; B.Kbytes = p->Kbytes; B.Mpad = p->Mpad; B.Rpad = large_rpad(a.R);
         return launch_tc_large(B, a, p->op, p->stream, launches);
     }
     if (p->path == PHIA_PATH_TC && p->imma) return launch_imma_small(a, p->stream, launches);

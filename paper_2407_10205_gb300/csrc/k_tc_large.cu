@@ -41,35 +41,43 @@ namespace phia {
 namespace {
 
 constexpr int kBM = 128;       // output spins per tile (TMEM lanes)
-constexpr int kBN = 128;       // replicas per tile (TMEM columns)
 constexpr int kBKB = 128;      // bytes of K per pipeline stage (one 128-byte swizzle row)
-constexpr int kStages = 3;
+constexpr int kMaxStages = 3;
+constexpr int kMaxBN = 256;
 constexpr int kEpiWarps = 16;  // four per TMEM lane quadrant, each a quarter of the columns
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;
-constexpr int kColsPerWarp = kBN / (kEpiWarps / 4);
 constexpr int kChunk = 8;                      // replica columns per epilogue step (two x/v groups)
-constexpr int kChunksPerTile = kColsPerWarp / kChunk;
 constexpr int kRing = 3;                       // x/v chunks per thread: the current + kRing - 1 ahead
 constexpr uint32_t kStageA = kBM * kBKB;
-constexpr uint32_t kStageB = kBN * kBKB;
 constexpr uint32_t kRingBytes = kRing * kChunk * kEpiThreads * 4;   // per array (x or v)
 static_assert(kChunk == 8, "a chunk is two 4-replica groups of the x/v layout");
-static_assert(kRing - 1 <= kChunksPerTile, "prefetch reaches at most into the next tile");
 
 struct LargeShared {
-    uint64_t full[kStages];
-    uint64_t empty[kStages];
+    uint64_t full[kMaxStages];
+    uint64_t empty[kMaxStages];
     uint64_t accf[2];       // accumulator b holds a finished tile
     uint64_t acce[2];       // accumulator b drained by the epilogue warps
     uint64_t drain;         // every MMA issued has completed
     uint32_t tmem_base;
     int32_t timed_out;
-    int32_t part[2][4][kBN];   // per lane-quadrant warp sums of s_i (I_i + h_i), by accumulator
+    int32_t part[2][4][kMaxBN];   // per lane-quadrant warp sums of s_i (I_i + h_i), by accumulator
 };
 
-constexpr size_t kSmemBytes = 1024 + kStages * (kStageA + kStageB) + 2 * kRingBytes + sizeof(LargeShared);
-static_assert(kSmemBytes <= 232448, "shared memory over the per-CTA limit");
+// Tile shape: 128 output spins x BN replicas.  BN = 256 halves the coupling-operand
+// traffic per output against BN = 128 (the shared-memory ring then holds 2 stages);
+// BN = 128 keeps more tiles when replicas are few.
+template <int BN>
+struct Tile {
+    static constexpr int kStages = BN == 256 ? 2 : 3;
+    static constexpr uint32_t kStageB = BN * kBKB;
+    static constexpr int kColsPerWarp = BN / (kEpiWarps / 4);
+    static constexpr int kChunksPerTile = kColsPerWarp / kChunk;
+    static constexpr size_t kSmemBytes = 1024 + kStages * (kStageA + kStageB) + 2 * kRingBytes + sizeof(LargeShared);
+    static_assert(kStages <= kMaxStages && BN <= kMaxBN, "tile over the shared bookkeeping");
+    static_assert(kSmemBytes <= 232448, "shared memory over the per-CTA limit");
+    static_assert(kRing - 1 <= kChunksPerTile, "prefetch reaches at most into the next tile");
+};
 
 struct LargeArgs {
     RunArgs a;
@@ -183,12 +191,16 @@ __device__ __forceinline__ void settle_replica(const LargeArgs &L, int r, int64_
     L.flags[(size_t)(tt & 1) * L.Rpad + r] = (int8_t)imp;
 }
 
-template <int OP>
+template <int OP, int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_large_step(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const LargeArgs L) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
-    constexpr uint32_t IDESC = make_idesc(OP == kOpE4M3 ? 0u : 1u, kBM, kBN);
+    constexpr uint32_t IDESC = make_idesc(OP == kOpE4M3 ? 0u : 1u, kBM, BN);
+    constexpr int kStages = Tile<BN>::kStages;
+    constexpr uint32_t kStageB = Tile<BN>::kStageB;
+    constexpr int kColsPerWarp = Tile<BN>::kColsPerWarp;
+    constexpr int kChunksPerTile = Tile<BN>::kChunksPerTile;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = smem;
@@ -207,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int N = a.N, R = a.R;
 
     if (warp == 0) {
-        tmem_alloc(&sh->tmem_base, 2 * kBN);
+        tmem_alloc(&sh->tmem_base, 2 * BN);
         tmem_relinquish();
     }
     if (tid == 32) {
@@ -236,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int lt = 0; lt < my_tiles && ok; ++lt) {
                 const int tile = (int)blockIdx.x + lt * G;
                 const int m = tile % L.mtiles, n = tile / L.mtiles;
-                const int ybuf = (int)(t & 3) * L.Rpad + n * kBN;
+                const int ybuf = (int)(t & 3) * L.Rpad + n * BN;
                 for (int kb = 0; kb < KB; ++kb, ++kg) {
                     const int s = (int)(kg % kStages);
                     if (kg >= kStages &&
@@ -266,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dt = tmem + (uint32_t)(b * kBN);
+                const uint32_t dt = tmem + (uint32_t)(b * BN);
                 for (int kb = 0; kb < KB; ++kb, ++kg) {
                     const int s = (int)(kg % kStages);
                     if (*tout || !mbar_wait_bounded(&sh->full[s], (uint32_t)(kg / kStages) & 1u, kWaitTimeoutNs)) {
@@ -306,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // other 4 (the next replica group) follow at + 4 Mp.
         const size_t grp_stride = (size_t)Mp * 4;
         auto xv_offset = [&](int m_, int n_, int c_) -> size_t {
-            const int grp = (n_ * kBN + cg * kColsPerWarp + c_ * kChunk) >> 2;
+            const int grp = (n_ * BN + cg * kColsPerWarp + c_ * kChunk) >> 2;
             return ((size_t)grp * Mp + (m_ * kBM + q4 * 32 + lane)) * 4;
         };
         auto issue = [&](size_t off, int slot) {
@@ -336,14 +348,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int i = m * kBM + q4 * 32 + lane;
             const bool live_i = i < N;
             // (a) records of iteration t-1 for this replica tile (output row 0 only).
-            if (m == 0 && t - 1 >= L.t_first && et < kBN) {
-                const int r = n * kBN + et;
+            if (m == 0 && t - 1 >= L.t_first && et < BN) {
+                const int r = n * BN + et;
                 if (r < R) settle_replica(L, r, t - 1);
             }
             // (b) best spins of iteration t-2 for the replicas that improved then: lane l
             // packs the 32 spins of this warp's quadrant for replica rb + l.
             if (t - 2 >= L.t_first) {
-                const int rb = n * kBN + cg * kColsPerWarp;
+                const int rb = n * BN + cg * kColsPerWarp;
                 const int8_t *F = L.flags + (size_t)((t - 2) & 1) * L.Rpad;
                 const uint8_t *Sb = L.S + (size_t)((t - 2) & 3) * L.Rpad * L.Kbytes;
                 const int i0 = m * kBM + q4 * 32;
@@ -360,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // (c) the field of this iteration and the update.
             const int32_t hki = live_i ? a.hk[i] : 0;
-            const int rc0 = n * kBN + cg * kColsPerWarp;          // first replica of this warp's columns
+            const int rc0 = n * BN + cg * kColsPerWarp;          // first replica of this warp's columns
             const int ncol = max(0, min(kColsPerWarp, R - rc0));   // live replica columns of this warp
             uint8_t *sb = Sn + (size_t)rc0 * L.Kbytes + (size_t)i * ESZ;
             // Warp-uniform, as the TMEM loads below are warp-collective.
@@ -368,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                                                kWaitTimeoutNs));
             if (!ok) *tout = 1;
             tc_fence_after();
-            const uint32_t tbase = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * kBN + cg * kColsPerWarp);
+            const uint32_t tbase = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * BN + cg * kColsPerWarp);
 #pragma unroll 1
             for (int c = 0; c < kChunksPerTile; ++c) {
                 const int col0 = c * kChunk;               // first column of the chunk in this warp's group
@@ -445,8 +457,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh->acce[b]);
             named_barrier_sync(1, kEpiThreads);
-            if (et < kBN) {
-                const int r = n * kBN + et;
+            if (et < BN) {
+                const int r = n * BN + et;
                 const long long s4 =
                     (long long)sh->part[b][0][et] + sh->part[b][1][et] + sh->part[b][2][et] + sh->part[b][3][et];
                 if (ok) atomicAdd(reinterpret_cast<unsigned long long *>(L.Epart) + (size_t)(t & 1) * L.Rpad + r,
@@ -462,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0 && sh->timed_out) atomicExch(a.err, 1);
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * kBN);
+        tmem_dealloc(tmem, 2 * BN);
     }
 }
 
@@ -581,8 +593,9 @@ bool make_map(CUtensorMap *m, const void *base, int op, uint64_t inner_elems, ui
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int OP>
-cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, int *launches) {
+template <int OP, int BN>
+cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, int *launches, int sms) {
+    constexpr size_t kSmem = Tile<BN>::kSmemBytes;
     LargeArgs L;
     L.a = a;
     L.S = B.S;
@@ -591,7 +604,7 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
     L.Kbytes = B.Kbytes;
     L.Rpad = B.Rpad;
     L.mtiles = B.Mpad / kBM;
-    L.ntiles = L.mtiles * (B.Rpad / kBN);
+    L.ntiles = L.mtiles * ((a.R + BN - 1) / BN);
     L.t_first = a.t0;
     L.X = B.X;
     L.V = B.V;
@@ -599,14 +612,10 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
     CUtensorMap tmA, tmB;
     const int esz = OP == kOpE4M3 ? 1 : 2;
     if (!make_map(&tmA, B.Jop, OP, (uint64_t)B.Kbytes / esz, (uint64_t)B.Mpad, (uint64_t)B.Kbytes, kBM) ||
-        !make_map(&tmB, B.S, OP, (uint64_t)B.Kbytes / esz, (uint64_t)4 * B.Rpad, (uint64_t)B.Kbytes, kBN))
+        !make_map(&tmB, B.S, OP, (uint64_t)B.Kbytes / esz, (uint64_t)4 * B.Rpad, (uint64_t)B.Kbytes, BN))
         return cudaErrorInvalidValue;
-    auto step = tc_large_step<OP>;
-    cudaError_t e = cudaFuncSetAttribute(step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto step = tc_large_step<OP, BN>;
+    cudaError_t e = cudaFuncSetAttribute(step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)std::min(L.ntiles, std::max(sms, 1)));
     e = cudaMemsetAsync(B.Epart, 0, 2 * (size_t)B.Rpad * sizeof(int64_t), st);   // energy sums start at 0
@@ -620,7 +629,7 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
         L.a.nsteps = 1;
         L.a.T_total = 1;
         tc_large_field_prologue<OP><<<eg, 256, 0, st>>>(L);
-        step<<<grid, kThreads, kSmemBytes, st>>>(tmA, tmB, L);
+        step<<<grid, kThreads, kSmem, st>>>(tmA, tmB, L);
         tc_large_field_out<<<(a.R + 255) / 256, 256, 0, st>>>(L);
         n += 3;
         if (launches) *launches += n;
@@ -631,7 +640,7 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
     ++n;
     for (int64_t t = a.t0; t < a.t0 + a.nsteps; ++t) {
         L.t = t;
-        step<<<grid, kThreads, kSmemBytes, st>>>(tmA, tmB, L);
+        step<<<grid, kThreads, kSmem, st>>>(tmA, tmB, L);
         ++n;
     }
     const int64_t t_last = a.t0 + a.nsteps - 1;
@@ -652,10 +661,17 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
 }  // namespace
 
 cudaError_t launch_tc_large(const LargeBuffers &B, const RunArgs &a, int op, cudaStream_t st, int *launches) {
-    if (op == kOpE4M3) return run_large<kOpE4M3>(B, a, st, launches);
-    return run_large<kOpBF16>(B, a, st, launches);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // 256-replica tiles when they still give every SM one, else 128-replica tiles.
+    const bool wide = (int64_t)(B.Mpad / kBM) * ((a.R + 255) / 256) >= sms;
+    if (op == kOpE4M3)
+        return wide ? run_large<kOpE4M3, 256>(B, a, st, launches, sms) : run_large<kOpE4M3, 128>(B, a, st, launches, sms);
+    return wide ? run_large<kOpBF16, 256>(B, a, st, launches, sms) : run_large<kOpBF16, 128>(B, a, st, launches, sms);
 }
 
-size_t tc_large_smem_bytes() { return kSmemBytes; }
+size_t tc_large_smem_bytes() { return Tile<256>::kSmemBytes; }
 
 }  // namespace phia

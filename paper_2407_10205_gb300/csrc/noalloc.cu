@@ -80,7 +80,7 @@ extern "C" int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N
     // Scratch layout: operand J, 4 spin buffers, energy sums, flags, run counters, and the
     // working x, v in the kernel's interleaved layout (the caller's x, v are read at the
     // start and written at the end).
-    const int Mpad = round_up(N, 128), Kbytes = large_kbytes(N, op), Rpad = round_up(replicas, 128);
+    const int Mpad = round_up(N, 128), Kbytes = large_kbytes(N, op), Rpad = large_rpad(replicas);
     const size_t off_jop = 0;
     const size_t off_s = off_jop + align256((size_t)Mpad * Kbytes);
     const size_t off_e = off_s + align256((size_t)4 * Rpad * Kbytes);

@@ -65,6 +65,8 @@ cudaError_t launch_tc_large(const LargeBuffers &B, const RunArgs &a, int op, cud
 cudaError_t launch_convert_operand(const int8_t *Jk, int N, void *Jop, int Mpad, int Kbytes, int op, cudaStream_t st);
 inline int large_kbytes(int N, int op) { return ((N * (op == kOpE4M3 ? 1 : 2)) + 127) / 128 * 128; }
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+// Replica padding of the per-iteration dense path (its widest tile is 256 replicas).
+inline int large_rpad(int R) { return round_up(R, 256); }
 
 // Sparse batched path: many CSR instances, one launch per iteration over all of them.
 struct CsrInst {
