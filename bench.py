@@ -55,7 +55,7 @@ WORKLOADS = {
                        cmp_instances=8, cmp_iters=20, cpu_instances=4, cpu_iters=50),
     # configs[4]: serving stream, Poisson arrivals at 200/s over a pool of seeded instances
     "serving": dict(kind="serving", pool=32, pool_seed=5, requests=400, arrival_seed=11, rate_hz=200.0,
-                    replicas=256, step_cap=5000, max_inflight=16, budget_gb=64, chunk_iters=100,
+                    replicas=256, step_cap=5000, max_inflight=64, budget_gb=64, chunk_iters=100,
                     cmp_requests=60, cmp_wall_s=90.0,
                     name="serving: Poisson 200/s, N log-uniform [64,8192], half dense {-1,+1}, half sparse "
                          "f=8 density 0.01; 256 replicas, step cap 5000, target = oracle best (4 x 200)"),
@@ -379,9 +379,12 @@ def run_serving(args, w):
     span = max(s.t_done_s for s in done) - min(s.t_submit_s for s in sts)
     value = st.spin_updates / span
     cmp_arr = arrivals[: w["cmp_requests"]]
-    csts, cst, ccomplete = _serve_stream(phia, pool, targets, cmp_arr, w, phia.PATH_FP32, w["cmp_wall_s"])
-    cdone = [s for s in csts if s.state == 2]
-    ours_first = _serve_stream(phia, pool, targets, cmp_arr, w, phia.PATH_AUTO)[1]
+    if args.no_comparator:
+        cst = ours_first = None
+        ccomplete = False
+    else:
+        csts, cst, ccomplete = _serve_stream(phia, pool, targets, cmp_arr, w, phia.PATH_FP32, w["cmp_wall_s"])
+        ours_first = _serve_stream(phia, pool, targets, cmp_arr, w, phia.PATH_AUTO)[1]
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": 1, "warmup": 1,
         "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -391,11 +394,12 @@ def run_serving(args, w):
         "serving": {"completed": st.completed, "hits": st.hits, "ttt_p50_s": st.ttt_p50_s, "ttt_p99_s": st.ttt_p99_s,
                     "ttt_admit_p50_s": st.ttt_admit_p50_s, "ttt_admit_p99_s": st.ttt_admit_p99_s,
                     "span_s": span, "spin_updates": st.spin_updates, "all_done": complete},
-        "comparator": {"path": "fp32 per-instance (same server, PHIA_PATH_FP32)", "requests": len(cmp_arr),
-                       "completed": cst.completed, "hits": cst.hits, "ttt_p50_s": cst.ttt_p50_s,
-                       "ttt_p99_s": cst.ttt_p99_s, "all_done_within_s": w["cmp_wall_s"] if ccomplete else None,
-                       "ours_on_same_requests": {"ttt_p50_s": ours_first.ttt_p50_s, "ttt_p99_s": ours_first.ttt_p99_s,
-                                                 "hits": ours_first.hits}},
+        "comparator": None if cst is None else {
+            "path": "fp32 per-instance (same server, PHIA_PATH_FP32)", "requests": len(cmp_arr),
+            "completed": cst.completed, "hits": cst.hits, "ttt_p50_s": cst.ttt_p50_s,
+            "ttt_p99_s": cst.ttt_p99_s, "all_done_within_s": w["cmp_wall_s"] if ccomplete else None,
+            "ours_on_same_requests": {"ttt_p50_s": ours_first.ttt_p50_s, "ttt_p99_s": ours_first.ttt_p99_s,
+                                      "hits": ours_first.hits}},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
                 "note": "serving is end to end by construction: host instances in, results out"},
         "clocks": cs.summary(),
@@ -418,6 +422,11 @@ def run_ours(args):
     if w["kind"] == "batch":
         return run_batch(args, w)
     if w["kind"] == "serving":
+        w = dict(w)
+        if args.max_inflight:
+            w["max_inflight"] = args.max_inflight
+        if args.chunk_iters:
+            w["chunk_iters"] = args.chunk_iters
         return run_serving(args, w)
     d = _instance(w)
     N, R, T = w["N"], w["replicas"], w["iterations"]
@@ -542,6 +551,9 @@ def main():
     ap.add_argument("--tile-replicas", type=int, default=0, help="tensor-core replicas per CTA (0 = auto)")
     ap.add_argument("--coupling-mem", type=int, default=0, help="tensor-core: 1 = J in shared, 2 = in tensor memory")
     ap.add_argument("--tc-kernel", type=int, default=0, help="tensor-core kernel: 1 tcgen05 resident, 2 per-iteration, 3 int8 mma.sync")
+    ap.add_argument("--max-inflight", type=int, default=0, help="serving: request slots (0 = the workload's)")
+    ap.add_argument("--chunk-iters", type=int, default=0, help="serving: iterations per chunk (0 = the workload's)")
+    ap.add_argument("--no-comparator", action="store_true", help="serving: skip the FP32 comparator runs")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warmup + steps anneals of the tensor-core path and nothing else (for ncu)")
     args = ap.parse_args()
