@@ -94,6 +94,8 @@ struct phia_s {
     // run counters
     unsigned long long *d_min_hit = nullptr, *d_iters = nullptr;
     int32_t *d_err = nullptr;
+    IterCtl *d_ctl = nullptr;           // iteration control of the per-iteration kernel
+    StepGraphCache *graphs = nullptr;   // its step launches as replayable graphs
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool ran = false;
     int64_t last_steps = 0;
@@ -245,6 +247,7 @@ cudaError_t launch_path(phia_t *p, const RunArgs &a, int *launches) {
         LargeBuffers B;
         B.Jop = p->d_Jop; B.S = p->d_S; B.Epart = p->d_Epart; B.flags = p->d_flags;
         B.X = p->d_X; B.V = p->d_V; B.Kbytes = p->Kbytes; B.Mpad = p->Mpad; B.Rpad = large_rpad(a.R);
+        B.ctl = p->d_ctl; B.graphs = p->graphs;
         return launch_tc_large(B, a, p->op, p->stream, launches);
     }
     if (p->path == PHIA_PATH_TC && p->imma) return launch_imma_small(a, p->stream, launches);
@@ -273,6 +276,8 @@ int finish_create(phia_t *p, const int32_t *h_k, const phia_opts *opts) {
     CU(cudaMalloc((void **)&p->d_iters, 8));
     CU(cudaMalloc((void **)&p->d_err, 4));
     CU(cudaMemsetAsync(p->d_err, 0, 4, p->stream));
+    CU(cudaMalloc((void **)&p->d_ctl, sizeof(IterCtl)));
+    p->graphs = step_graphs_new();
     CU(cudaEventCreate(&p->ev0));
     CU(cudaEventCreate(&p->ev1));
     CU(cudaStreamSynchronize(p->stream));
@@ -662,7 +667,8 @@ void phia_destroy(phia_t *p) {
     free_replicas(p);
     cudaFree(p->d_Jk); cudaFree(p->d_Jf); cudaFree(p->d_hk); cudaFree(p->d_Jop);
     cudaFree(p->d_rowptr); cudaFree(p->d_col); cudaFree(p->d_val);
-    cudaFree(p->d_min_hit); cudaFree(p->d_iters); cudaFree(p->d_err);
+    cudaFree(p->d_min_hit); cudaFree(p->d_iters); cudaFree(p->d_err); cudaFree(p->d_ctl);
+    step_graphs_free(p->graphs);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
     delete p;

@@ -42,6 +42,8 @@ struct phia_batch_s {
     uint32_t *d_bits = nullptr;
     unsigned long long *d_min_hit = nullptr, *d_iters = nullptr;
     int32_t *d_err = nullptr;
+    IterCtl *d_ctl = nullptr;               // iteration control of the step kernel
+    StepGraphCache *graphs = nullptr;       // its step launches as replayable graphs
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool ran = false;
     int64_t last_steps = 0;
@@ -238,6 +240,8 @@ int batch_create(phia_batch_s **out, int32_t count, const phia_instance_desc *d,
     if (ok && cudaMalloc((void **)&b->d_min_hit, 8) != cudaSuccess) ok = false;
     if (ok && cudaMalloc((void **)&b->d_iters, 8) != cudaSuccess) ok = false;
     if (ok && cudaMalloc((void **)&b->d_err, 4) != cudaSuccess) ok = false;
+    if (ok && cudaMalloc((void **)&b->d_ctl, sizeof(IterCtl)) != cudaSuccess) ok = false;
+    if (ok) b->graphs = step_graphs_new();
     if (ok && (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess)) ok = false;
     if (!ok) {
         cudaGetLastError();
@@ -322,7 +326,8 @@ int batch_run(phia_batch_s *b, const phia_schedule *sched, int32_t R_real, int64
     C.max_words = b->max_words;
     C.total_rows = b->total_rows;
     BCU(cudaEventRecord(b->ev0, b->stream));
-    cudaError_t e = launch_csr(C, b->stream, &launches);
+    C.ctl = b->d_ctl;
+    cudaError_t e = launch_csr(C, b->graphs, b->stream, &launches);
     if (e != cudaSuccess) return bfail(PHIA_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     BCU(cudaEventRecord(b->ev1, b->stream));
     if (!field_mode) {
@@ -482,6 +487,8 @@ void phia_batch_destroy(phia_batch_t *b) {
     free_state(b);
     cudaFree(b->d_inst); cudaFree(b->d_blocks); cudaFree(b->d_rowptr); cudaFree(b->d_col); cudaFree(b->d_val);
     cudaFree(b->d_hk); cudaFree(b->d_targets); cudaFree(b->d_min_hit); cudaFree(b->d_iters); cudaFree(b->d_err);
+    cudaFree(b->d_ctl);
+    step_graphs_free(b->graphs);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     delete b;

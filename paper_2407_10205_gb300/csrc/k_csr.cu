@@ -63,13 +63,13 @@ __global__ void __launch_bounds__(32 * kWarps) csr_step(const CsrArgs C) {
     const int g = blockIdx.y;                     // replica group of 256
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = in.N, R = C.R, RW = R / 32;
-    const int64_t t = C.t;
+    const int64_t t = C.ctl->t, t_first = C.ctl->t_first, t_end = C.ctl->t_end;
 
     // (a) records of iteration t-1 (block 0 of each instance).
-    if (blk.i0 == 0 && t - 1 >= C.t_first) settle_csr(C, in, b, g * kGroup + tid, t - 1);
+    if (blk.i0 == 0 && t - 1 >= t_first) settle_csr(C, in, b, g * kGroup + tid, t - 1);
     // (b) best spins of iteration t-2 for the replicas that improved then: this block's
     //     64 rows of spin bits go through shared memory, one thread per replica.
-    if (t - 2 >= C.t_first) {
+    if (t - 2 >= t_first) {
         const int rows = min(kRowsPerBlock, N - blk.i0);
         const uint32_t *Sb = spin_buf(C, in, t - 2);
         for (int e = tid; e < kRowsPerBlock * 8; e += 32 * kWarps) {
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(32 * kWarps) csr_step(const CsrArgs C) {
     uint32_t *Snext = const_cast<uint32_t *>(spin_buf(C, in, t + 1));
     const float bgq = beta_at(t, inv_tm1_of(a.T_total), a.beta0, a.beta1) * (a.gamma * in.q);
     const float eps = a.eps, gamma = a.gamma;
-    const bool more = t + 1 < C.t_first + a.nsteps;
+    const bool more = t + 1 < t_end;
     const bool refresh_next = more && refresh_at(t + 1, a.refresh);
     const int r0 = g * kGroup + lane * 8;          // first replica of this lane
     int32_t epart[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -191,6 +191,8 @@ __global__ void __launch_bounds__(32 * kWarps) csr_step(const CsrArgs C) {
                       g * kGroup + tid,
                   (unsigned long long)s);
     }
+    __syncthreads();
+    if (tid == 0) iter_ctl_finish(C.ctl);
 }
 
 // Initial state (or given, [R][N] per instance), refresh at t0, first position update,
@@ -198,6 +200,7 @@ __global__ void __launch_bounds__(32 * kWarps) csr_step(const CsrArgs C) {
 __global__ void csr_prologue(const CsrArgs C) {
     const RunArgs &a = C.a;
     const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over total_rows * R / 8
+    if (gidx == 0) iter_ctl_start(C.ctl, a.t0, a.nsteps);
     const int R = C.R, per_row = R / 8;
     const int64_t row = gidx / per_row;
     if (row >= C.total_rows) return;
@@ -318,9 +321,8 @@ __global__ void csr_count(const CsrArgs C) {
 
 }  // namespace
 
-cudaError_t launch_csr(const CsrArgs &Cin, cudaStream_t st, int *launches) {
-    CsrArgs C = Cin;
-    C.t_first = C.a.t0;
+cudaError_t launch_csr(const CsrArgs &Cin, StepGraphCache *graphs, cudaStream_t st, int *launches) {
+    const CsrArgs &C = Cin;
     int n = 0;
     cudaError_t e = cudaMemsetAsync(C.Esum, 0, 2 * (size_t)C.total_reps * sizeof(int64_t), st);
     if (e != cudaSuccess) return e;
@@ -335,10 +337,19 @@ cudaError_t launch_csr(const CsrArgs &Cin, cudaStream_t st, int *launches) {
     csr_prologue<<<(unsigned)((pw + 255) / 256), 256, 0, st>>>(C);
     ++n;
     const dim3 grid(C.nblocks, C.R / kGroup);
-    for (int64_t t = C.a.t0; t < C.a.t0 + C.a.nsteps; ++t) {
-        C.t = t;
-        csr_step<<<grid, 32 * kWarps, 0, st>>>(C);
-        ++n;
+    {
+        // The step kernel reads its iteration from C.ctl: every launch is the same, and
+        // the arguments leave out what only the prologue and the export read.
+        CsrArgs Cs = C;
+        Cs.a.t0 = 0;
+        Cs.a.nsteps = 0;
+        Cs.x_in = Cs.v_in = nullptr;
+        Cs.x_out = Cs.v_out = nullptr;
+        void *args[1] = {&Cs};
+        e = launch_steps(graphs, reinterpret_cast<const void *>(csr_step), grid, dim3(32 * kWarps), 0, args, &Cs,
+                         sizeof Cs, C.a.nsteps, st);
+        if (e != cudaSuccess) return e;
+        n += (int)C.a.nsteps;
     }
     const int64_t t_last = C.a.t0 + C.a.nsteps - 1;
     csr_settle_all<<<C.count, 256, 0, st>>>(C, t_last);

@@ -32,6 +32,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "device_common.cuh"
 #include "phia_internal.h"
@@ -86,8 +87,7 @@ struct LargeArgs {
     int8_t *flags;      // [2][Rpad] improved at an iteration, by parity
     float *X, *V;       // [Rpad/4][Mp][4] state: replica r, spin i at ((r/4) Mp + i) 4 + r%4
     int32_t Kbytes, Rpad, mtiles, ntiles, Mp;
-    int64_t t;          // iteration of this launch
-    int64_t t_first;    // first iteration of this call
+    IterCtl *ctl;       // iteration of the launch and range of the run
 };
 
 template <int OP>
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int G = gridDim.x;
     const int my_tiles = (int)blockIdx.x < L.ntiles ? (L.ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
-    const int64_t t = L.t;
+    const int64_t t = L.ctl->t, t_first = L.ctl->t_first, t_end = L.ctl->t_end;
     const int KB = L.Kbytes / kBKB;
     const int N = a.N, R = a.R;
 
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         const float bgq = beta_at(t, inv_tm1_of(a.T_total), a.beta0, a.beta1) * (a.gamma * a.q);
         const float eps = a.eps, gamma = a.gamma;
-        const bool more = t + 1 < L.t_first + a.nsteps;
+        const bool more = t + 1 < t_end;
         const bool refresh_next = more && refresh_at(t + 1, a.refresh);
         uint8_t *Sn = L.S + (size_t)((t + 1) & 3) * L.Rpad * L.Kbytes;
         int slot = 0;                                   // ring slot of the current chunk
@@ -348,13 +348,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int i = m * kBM + q4 * 32 + lane;
             const bool live_i = i < N;
             // (a) records of iteration t-1 for this replica tile (output row 0 only).
-            if (m == 0 && t - 1 >= L.t_first && et < BN) {
+            if (m == 0 && t - 1 >= t_first && et < BN) {
                 const int r = n * BN + et;
                 if (r < R) settle_replica(L, r, t - 1);
             }
             // (b) best spins of iteration t-2 for the replicas that improved then: lane l
             // packs the 32 spins of this warp's quadrant for replica rb + l.
-            if (t - 2 >= L.t_first) {
+            if (t - 2 >= t_first) {
                 const int rb = n * BN + cg * kColsPerWarp;
                 const int8_t *F = L.flags + (size_t)((t - 2) & 1) * L.Rpad;
                 const uint8_t *Sb = L.S + (size_t)((t - 2) & 3) * L.Rpad * L.Kbytes;
@@ -471,7 +471,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (tid == 0 && sh->timed_out) atomicExch(a.err, 1);
+    if (tid == 0) {
+        if (sh->timed_out) atomicExch(a.err, 1);
+        iter_ctl_finish(L.ctl);
+    }
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, 2 * BN);
@@ -484,6 +487,7 @@ template <int OP>
 __global__ void tc_large_prologue(const LargeArgs L) {
     const RunArgs &a = L.a;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx == 0) iter_ctl_start(L.ctl, a.t0, a.nsteps);
     if (idx >= (int64_t)L.Rpad * L.Mp) return;
     const int64_t gi = idx >> 2;                       // (group, spin)
     const int grp = (int)(gi / L.Mp), i = (int)(gi - (int64_t)grp * L.Mp);
@@ -523,6 +527,7 @@ template <int OP>
 __global__ void tc_large_field_prologue(const LargeArgs L) {
     const RunArgs &a = L.a;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx == 0) iter_ctl_start(L.ctl, 0, 1);
     if (idx >= (int64_t)a.R * a.N) return;
     const int r = (int)(idx / a.N), i = (int)(idx - (int64_t)r * a.N);
     put_spin_byte<OP>(L.S + (size_t)r * L.Kbytes, i, a.spins_in[idx] > 0);
@@ -597,7 +602,9 @@ template <int OP, int BN>
 cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, int *launches, int sms) {
     constexpr size_t kSmem = Tile<BN>::kSmemBytes;
     LargeArgs L;
+    memset(&L, 0, sizeof L);   // the bytes key the graph cache
     L.a = a;
+    L.ctl = B.ctl;
     L.S = B.S;
     L.Epart = B.Epart;
     L.flags = B.flags;
@@ -605,7 +612,6 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
     L.Rpad = B.Rpad;
     L.mtiles = B.Mpad / kBM;
     L.ntiles = L.mtiles * ((a.R + BN - 1) / BN);
-    L.t_first = a.t0;
     L.X = B.X;
     L.V = B.V;
     L.Mp = B.Mpad;
@@ -624,8 +630,6 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
     const unsigned eg = (unsigned)((RN + 255) / 256);
     int n = 0;
     if (a.field_mode) {
-        L.t = 0;
-        L.t_first = 0;
         L.a.nsteps = 1;
         L.a.T_total = 1;
         tc_large_field_prologue<OP><<<eg, 256, 0, st>>>(L);
@@ -638,10 +642,23 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
     const int64_t RMp = (int64_t)B.Rpad * B.Mpad;
     tc_large_prologue<OP><<<(unsigned)((RMp + 255) / 256), 256, 0, st>>>(L);
     ++n;
-    for (int64_t t = a.t0; t < a.t0 + a.nsteps; ++t) {
-        L.t = t;
-        step<<<grid, kThreads, kSmem, st>>>(tmA, tmB, L);
-        ++n;
+    {
+        // The step kernel reads its iteration from L.ctl: every launch is the same, and
+        // the arguments leave out what only the prologue and the export read.
+        LargeArgs Ls = L;
+        Ls.a.t0 = 0;
+        Ls.a.nsteps = 0;
+        Ls.a.x_in = Ls.a.v_in = nullptr;
+        Ls.a.x_out = Ls.a.v_out = nullptr;
+        void *args[3] = {&tmA, &tmB, &Ls};
+        uint8_t key[2 * sizeof(CUtensorMap) + sizeof(LargeArgs)];
+        memcpy(key, &tmA, sizeof tmA);
+        memcpy(key + sizeof tmA, &tmB, sizeof tmB);
+        memcpy(key + 2 * sizeof tmA, &Ls, sizeof Ls);
+        e = launch_steps(B.graphs, reinterpret_cast<const void *>(step), grid, dim3(kThreads), kSmem, args, key,
+                         sizeof key, a.nsteps, st);
+        if (e != cudaSuccess) return e;
+        n += (int)a.nsteps;
     }
     const int64_t t_last = a.t0 + a.nsteps - 1;
     tc_large_settle<<<(a.R + 255) / 256, 256, 0, st>>>(L, t_last);

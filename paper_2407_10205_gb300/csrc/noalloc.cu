@@ -150,6 +150,8 @@ extern "C" int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N
     B.S = base + off_s;
     B.Epart = reinterpret_cast<int64_t *>(base + off_e);
     B.flags = reinterpret_cast<int8_t *>(base + off_f);
+    B.ctl = reinterpret_cast<IterCtl *>(base + off_c + 64);
+    B.graphs = nullptr;   // a graph would be an allocation
     B.X = reinterpret_cast<float *>(base + off_x);
     B.V = reinterpret_cast<float *>(base + off_v);
     B.Kbytes = Kbytes; B.Mpad = Mpad; B.Rpad = Rpad;

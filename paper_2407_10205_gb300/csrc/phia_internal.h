@@ -44,6 +44,50 @@ struct RunArgs {
 };
 
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;  // 2 s bound on every device-side wait
+
+// Iteration control of a per-iteration path, in device memory.  The run's prologue
+// kernel sets it; every step launch reads t (and the run's range) at its start and the
+// last CTA of the launch to finish advances t.  Step launches therefore have identical
+// arguments, so a chunk of them can be replayed as one instantiated CUDA graph.
+struct IterCtl {
+    int64_t t;          // iteration of the next step launch
+    int64_t t_first;    // first iteration of the run
+    int64_t t_end;      // one past the run's last iteration
+    uint32_t done;      // CTAs of the current launch that have finished
+    uint32_t pad;
+};
+
+#ifdef __CUDACC__
+// End of a step launch, called by one thread per CTA after the CTA's last read of the
+// control block: the last CTA to arrive advances the iteration for the next launch.
+__device__ __forceinline__ void iter_ctl_finish(IterCtl *c) {
+    __threadfence();
+    const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+    if (atomicAdd(&c->done, 1u) == total - 1) {
+        c->done = 0;
+        c->t = c->t + 1;
+        __threadfence();
+    }
+}
+// The prologue of a run (one thread).
+__device__ __forceinline__ void iter_ctl_start(IterCtl *c, int64_t t0, int64_t nsteps) {
+    c->t = t0;
+    c->t_first = t0;
+    c->t_end = t0 + nsteps;
+    c->done = 0;
+}
+#endif
+
+// Instantiated graphs of step launches, owned by a handle or a batch.
+struct StepGraphCache;
+StepGraphCache *step_graphs_new();
+void step_graphs_free(StepGraphCache *c);
+// `steps` launches of `func` with the argument list `args` (each launch identical): full
+// chunks replay one cached graph of up to 100 launches, the rest launch directly.  With
+// no cache every launch is direct.  The cache key is the kernel, its launch shape and
+// the argument bytes `key` (`key_bytes` of them).
+cudaError_t launch_steps(StepGraphCache *cache, const void *func, dim3 grid, dim3 block, size_t smem, void **args,
+                         const void *key, size_t key_bytes, int64_t steps, cudaStream_t st);
 constexpr int kOpE4M3 = 1;
 constexpr int kOpBF16 = 2;
 
@@ -59,6 +103,8 @@ struct LargeBuffers {
     int64_t *Epart;       // [2][Rpad], zero between uses
     int8_t *flags;        // [2][Rpad]
     float *X, *V;         // [Rpad/4][Mpad][4] working state (replica groups of 4 interleaved per spin)
+    IterCtl *ctl;         // iteration control
+    StepGraphCache *graphs;   // or null: step launches go out one by one
     int32_t Kbytes, Mpad, Rpad;
 };
 cudaError_t launch_tc_large(const LargeBuffers &B, const RunArgs &a, int op, cudaStream_t st, int *launches);
@@ -109,9 +155,9 @@ struct CsrArgs {
     int32_t R_real;         // replicas the caller asked for (<= R); the rest pad the groups
     int32_t max_words;      // max ceil(N/32)
     int64_t total_rows;
-    int64_t t, t_first;
+    IterCtl *ctl;           // iteration control
 };
-cudaError_t launch_csr(const CsrArgs &C, cudaStream_t st, int *launches);
+cudaError_t launch_csr(const CsrArgs &C, StepGraphCache *graphs, cudaStream_t st, int *launches);
 
 }  // namespace phia
 struct phia_batch_s;
