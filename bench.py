@@ -70,7 +70,10 @@ METRIC = "spin-updates/s"
 ALGO_OPS_PER_UPDATE = 16
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each kernel, from the
 # committed ncu summaries under profiles/; absent once a kernel changed after its capture.
-KERNEL_TRAFFIC_BYTES = {}
+KERNEL_TRAFFIC_BYTES = {
+    "tc_large_step": 86_798_080 + 17_000_448,      # N = 2000, 4096 replicas (one iteration)
+    "csr_step": 965_294_336 + 763_158_528,          # 256 ER instances, 256 replicas (one iteration)
+}
 
 
 def _dist():
