@@ -202,17 +202,21 @@ def _roofline(w, kernel_ms, stats, peaks, src, clocks):
     tensor_achieved = 2.0 * N * su / (kernel_ms * 1e-3) / 1e12
     tensor = {"achieved": tensor_achieved, "peak": tensor_peak, "unit": "TFLOP/s",
               "frac": tensor_achieved / tensor_peak, "peak_source": f"{src} bf16 x 2 (nominal e4m3 : bf16 ratio)"}
-    if stats.tc_kernel == 1:
-        # Resident kernel: one launch per run.  The 2N field flops per spin update take a
-        # few hundred tensor cycles per iteration; the time goes to the per-spin FP32
-        # update and the per-iteration dependency chain, so the bound quoted is the FP32
-        # lane-op rate.
+    if stats.tc_kernel in (1, 3, 4):
+        # Resident kernels: one launch per run.  In the tensor-core ones the 2N field flops
+        # per spin update take a few hundred tensor cycles per iteration; the incremental
+        # one gathers only the columns of the spins that changed sign.  The time goes to
+        # the per-spin FP32 update and the per-iteration dependency chain, so the bound
+        # quoted is the FP32 lane-op rate.
+        kname = {1: "tc_small_kernel", 3: "imma_small_kernel", 4: "inc_small_kernel"}[stats.tc_kernel]
+        if stats.tc_kernel == 4:
+            tensor = None
         sm_mhz = clocks.get("sm_max_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
         alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e9
         achieved = ALGO_OPS_PER_UPDATE * su / (kernel_ms * 1e-3) / 1e9
         return {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
-                "frac": achieved / alu_peak, "traffic": KERNEL_TRAFFIC_BYTES.get("tc_small_kernel"),
-                "kernel": "tc_small_kernel",
+                "frac": achieved / alu_peak, "traffic": KERNEL_TRAFFIC_BYTES.get(kname),
+                "kernel": kname,
                 "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (derived)", "tensor": tensor}
     # Per-iteration kernel: per launch it must move x and v in and out (16 B per spin
     # update), write the next spins (1 B per spin update) and read the spins and J once.
@@ -516,7 +520,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
         "config": {"workload": w["name"], "N": N, "replicas": R, "iterations": T, "path": "tc",
-                   "tc_kernel": "resident" if st.tc_kernel == 1 else "per-iteration",
+                   "tc_kernel": {1: "resident tcgen05", 2: "per-iteration tcgen05", 3: "resident int8 mma.sync",
+                                 4: "resident incremental field"}.get(st.tc_kernel, str(st.tc_kernel)),
                    "autotune": {"tc_kernel": tune.tc_kernel, "tile_replicas": tune.tile_replicas,
                                 "coupling_mem": tune.coupling_mem, "candidates": tune.candidates,
                                 "best_us_per_iter": tune.best_us_per_iter,

@@ -78,7 +78,10 @@ typedef struct phia_opts {
                               launch, J on chip; N <= 384 e4m3 / 256 bf16), 2 = one launch per
                               iteration (J streamed by TMA; any N), 3 = resident int8 kernel
                               (warp-level mma.sync s8 x s8 -> s32, J in registers; N <= 256;
-                              tile_replicas 8 or 16); 0 = automatic */
+                              tile_replicas 8 or 16), 4 = resident incremental-field kernel
+                              (CUDA cores: the exact integer field is updated by the columns of
+                              the spins that changed sign, Eq. 6 being linear in s; N <= 384
+                              e4m3 / 256 bf16; tile_replicas 4, 8 or 16); 0 = automatic */
     int32_t reserved;      /* must be 0 */
 } phia_opts;
 
@@ -110,8 +113,8 @@ typedef struct phia_stats {
     int32_t path;          /* path actually used (PHIA_PATH_TC / _FP32 / _CSR) */
     int32_t operand;       /* operand actually used (PHIA_OP_E4M3 / _BF16), 0 for other paths */
     int32_t kernel_launches; /* kernels launched by the last run */
-    int32_t tc_kernel;     /* tensor-core kernel used (1 resident tcgen05, 2 per iteration, 3 resident
-                              int8 mma.sync), 0 for other paths */
+    int32_t tc_kernel;     /* dense kernel used (1 resident tcgen05, 2 per iteration, 3 resident
+                              int8 mma.sync, 4 resident incremental field), 0 for other paths */
 } phia_stats;
 
 typedef struct phia_s phia_t;
@@ -142,13 +145,15 @@ int phia_anneal(phia_t *p, const phia_schedule *sched, int32_t replicas, int64_t
 /* Autotuner.  Times short probe runs (probe_iters iterations of `replicas` replicas) of
  * every tensor-core kernel variant that applies to this handle -- the resident tcgen05
  * kernel with 4, 8 or 16 replicas per CTA and J in shared or tensor memory, the
- * resident int8 mma.sync kernel with 8 or 16 replicas per CTA (N small enough), and the
- * per-iteration kernel -- keeps the fastest for the handle and caches it,
+ * resident int8 mma.sync kernel with 8 or 16 replicas per CTA (N small enough), the
+ * resident incremental-field kernel with 4, 8 or 16 replicas per CTA (N small enough),
+ * and the per-iteration kernel -- keeps the fastest for the handle and caches it,
  * process-wide, for (N, replicas, operand): handles created with all variant options
  * automatic use the cached choice for runs with that replica count.  The probes
  * overwrite the handle's last-run records.  Tensor-core path only (else PHIA_ENOTSUP). */
 typedef struct phia_tune_result {
-    int32_t tc_kernel;         /* 1 resident tcgen05, 2 per iteration, 3 resident int8 mma.sync */
+    int32_t tc_kernel;         /* 1 resident tcgen05, 2 per iteration, 3 resident int8 mma.sync,
+                                  4 resident incremental field */
     int32_t tile_replicas;     /* resident kernel: replicas per CTA */
     int32_t coupling_mem;      /* resident kernel: 1 shared, 2 tensor memory */
     int32_t candidates;        /* variants timed */

@@ -66,6 +66,7 @@ struct phia_s {
     phia_batch_s *batch = nullptr;      // CSR instances: a batch of one
     bool large = false;                 // tensor-core path through the per-iteration kernel
     bool imma = false;                  // tensor-core path through the int8 mma.sync resident kernel
+    bool inc = false;                   // dense path through the incremental-field resident kernel
     void *d_Jop = nullptr;              // couplings in the operand encoding (per-iteration kernel)
     int Mpad = 0, Kbytes = 0;
     uint8_t *d_S = nullptr;             // [4][Rpad][Kbytes]
@@ -206,6 +207,7 @@ struct TuneChoice {
     bool large;
     int tile_rl, coupling_mem;
     bool imma;
+    bool inc;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune;
@@ -237,6 +239,7 @@ int apply_tuned(phia_t *p, int R) {
     }
     p->large = c.large;
     p->imma = c.imma;
+    p->inc = c.inc;
     p->tile_rl = c.tile_rl;
     p->coupling_mem = c.coupling_mem;
     return PHIA_OK;
@@ -251,6 +254,9 @@ cudaError_t launch_path(phia_t *p, const RunArgs &a, int *launches) {
         return launch_tc_large(B, a, p->op, p->stream, launches);
     }
     if (p->path == PHIA_PATH_TC && p->imma) return launch_imma_small(a, p->stream, launches);
+    // The incremental kernel has no field-only mode: the resident tensor-core kernel
+    // covers the same sizes.
+    if (p->path == PHIA_PATH_TC && p->inc && !a.field_mode) return launch_inc_small(a, p->stream, launches);
     if (p->path == PHIA_PATH_TC) return launch_tc_small(a, p->op, p->stream, launches);
     if (p->path == PHIA_PATH_FP32)
         return launch_fp32_run(a, p->d_x, p->d_v, p->d_s0, p->d_s1, p->d_eacc, p->stream, launches);
@@ -324,7 +330,12 @@ int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, 
             return fail(PHIA_ENOTSUP, "the resident kernel handles N <= %d with this operand (N = %d)",
                         tc_small_max_n(opk), N);
     }
-    if (o.tc_kernel < 0 || o.tc_kernel > 3) return fail(PHIA_EINVAL, "tc_kernel must be 0, 1, 2 or 3");
+    if (o.tc_kernel < 0 || o.tc_kernel > 4) return fail(PHIA_EINVAL, "tc_kernel must be 0, 1, 2, 3 or 4");
+    if (o.tc_kernel == 4 && path == PHIA_PATH_TC) {
+        const int nmax = std::min(inc_small_max_n(), tc_small_max_n(op == PHIA_OP_E4M3 ? kOpE4M3 : kOpBF16));
+        if (N > nmax)
+            return fail(PHIA_ENOTSUP, "the incremental kernel handles N <= %d with this operand (N = %d)", nmax, N);
+    }
     if (o.tc_kernel == 3 && N > imma_small_max_n())
         return fail(PHIA_ENOTSUP, "the int8 mma.sync kernel handles N <= %d (N = %d)", imma_small_max_n(), N);
     if (o.reserved != 0) return fail(PHIA_EINVAL, "opts.reserved must be 0");
@@ -349,6 +360,7 @@ int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, 
     if (path == PHIA_PATH_TC) {
         p->large = o.tc_kernel == 2 || (o.tc_kernel == 0 && N > tc_small_max_n(p->op));
         p->imma = o.tc_kernel == 3;
+        p->inc = o.tc_kernel == 4;
     }
     const size_t NN = (size_t)N * N;
     auto cleanup = [&](int code) { phia_destroy(p); return code; };
@@ -462,13 +474,17 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
     std::vector<TuneChoice> cands;
     if (p->N <= tc_small_max_n(p->op)) {
         for (int tile : {4, 8, 16})
-            for (int mem : {1, 2}) cands.push_back(TuneChoice{false, tile, mem, false});
+            for (int mem : {1, 2}) cands.push_back(TuneChoice{false, tile, mem, false, false});
     }
     if (p->N <= imma_small_max_n()) {
-        cands.push_back(TuneChoice{false, 8, 0, true});
-        cands.push_back(TuneChoice{false, 16, 0, true});
+        cands.push_back(TuneChoice{false, 8, 0, true, false});
+        cands.push_back(TuneChoice{false, 16, 0, true, false});
     }
-    cands.push_back(TuneChoice{true, 0, 0, false});
+    if (p->N <= std::min(inc_small_max_n(), tc_small_max_n(p->op))) {
+        for (int tile : {4, 8, 16})
+            if (inc_small_tile_replicas(p->N, tile) == tile) cands.push_back(TuneChoice{false, tile, 0, false, true});
+    }
+    cands.push_back(TuneChoice{true, 0, 0, false, false});
     const bool saved_auto = p->auto_tile;
     p->auto_tile = false;
     float best_ms = 1e30f, worst_ms = 0.f;
@@ -480,6 +496,7 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
         }
         p->large = c.large;
         p->imma = c.imma;
+        p->inc = c.inc;
         p->tile_rl = c.tile_rl;
         p->coupling_mem = c.coupling_mem;
         float ms = 0.f;
@@ -494,6 +511,7 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
     }
     p->large = best.large;
     p->imma = best.imma;
+    p->inc = best.inc;
     p->tile_rl = best.tile_rl;
     p->coupling_mem = best.coupling_mem;
     p->auto_tile = saved_auto;
@@ -503,9 +521,10 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
     }
     if (out) {
         memset(out, 0, sizeof *out);
-        out->tc_kernel = best.large ? 2 : (best.imma ? 3 : 1);
-        out->tile_replicas = best.large ? 0 : (best.imma ? best.tile_rl : tc_small_tile_replicas(replicas, best.tile_rl));
-        out->coupling_mem = best.large || best.imma ? 0 : best.coupling_mem;
+        out->tc_kernel = best.large ? 2 : (best.imma ? 3 : (best.inc ? 4 : 1));
+        out->tile_replicas = best.large ? 0
+                             : (best.imma || best.inc ? best.tile_rl : tc_small_tile_replicas(replicas, best.tile_rl));
+        out->coupling_mem = best.large || best.imma || best.inc ? 0 : best.coupling_mem;
         out->candidates = (int32_t)cands.size();
         out->best_us_per_iter = 1000.f * best_ms / probe_iters;
         out->worst_us_per_iter = 1000.f * worst_ms / probe_iters;
@@ -655,7 +674,7 @@ int phia_stats_get(phia_t *p, phia_stats *out) {
     out->path = p->path;
     out->operand = p->op == kOpE4M3 ? PHIA_OP_E4M3 : (p->op == kOpBF16 ? PHIA_OP_BF16 : 0);
     out->kernel_launches = p->last_launches;
-    out->tc_kernel = p->path == PHIA_PATH_TC ? (p->large ? 2 : (p->imma ? 3 : 1)) : 0;
+    out->tc_kernel = p->path == PHIA_PATH_TC ? (p->large ? 2 : (p->imma ? 3 : (p->inc ? 4 : 1))) : 0;
     return PHIA_OK;
 }
 

@@ -181,6 +181,12 @@ int set_last_error(int code, const char *msg);
 int imma_small_max_n();
 cudaError_t launch_imma_small(const RunArgs &a, cudaStream_t st, int *launches);
 
+// Incremental-field resident kernel for small dense instances (CUDA cores, exact
+// integer field updated by the columns whose spin changed sign; no field mode).
+int inc_small_max_n();
+int inc_small_tile_replicas(int N, int requested);
+cudaError_t launch_inc_small(const RunArgs &a, cudaStream_t st, int *launches);
+
 // Plain FP32 per-step path (the comparator).
 cudaError_t launch_fp32_run(const RunArgs &a, float *x, float *v, int8_t *s0, int8_t *s1,
                             int64_t *e_acc, cudaStream_t st, int *launches);

@@ -170,7 +170,7 @@ def schedule(beta0, beta1, eps, gamma, refresh=0, target=None, stop_at_target=Fa
 
 
 MEM_AUTO, MEM_SHARED, MEM_TENSOR = 0, 1, 2
-KERNEL_AUTO, KERNEL_RESIDENT, KERNEL_PER_STEP, KERNEL_IMMA = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_RESIDENT, KERNEL_PER_STEP, KERNEL_IMMA, KERNEL_INCREMENTAL = 0, 1, 2, 3, 4
 
 
 def opts(path=PATH_AUTO, operand=OP_AUTO, device=0, instance_id=0, stream=None, tile_replicas=0,
