@@ -151,7 +151,16 @@ int batch_create(phia_batch_s **out, int32_t count, const phia_instance_desc *d,
     phia_batch_s *b = new phia_batch_s();
     auto cleanup = [&](int code) { phia_batch_destroy(b); return code; };
     b->count = count;
-    int64_t row_base = 0;
+    int64_t row_base = 0, nnz_real = 0;
+    // Every row is padded to a multiple of 8 entries with k = 0 (column 0): rows start
+    // 32-byte aligned in col and 8-byte aligned in val, so the step kernel reads a
+    // row's entries 8 at a time with aligned vector loads and no tail.
+    auto pad_row = [&]() {
+        while (col.size() % 8) {
+            col.push_back(0);
+            val.push_back(0);
+        }
+    };
     for (int k = 0; k < count; ++k) {
         const phia_instance_desc &x = d[k];
         const int n = x.N;
@@ -180,8 +189,10 @@ int batch_create(phia_batch_s **out, int32_t count, const phia_instance_desc *d,
                     if (x.J_k[(size_t)i * n + j] != 0) {
                         col.push_back(j);
                         val.push_back(x.J_k[(size_t)i * n + j]);
+                        ++nnz_real;
                     }
                 }
+                pad_row();
                 rp[i + 1] = (int32_t)(col.size() - in.nz_off);
             }
         } else {
@@ -200,8 +211,10 @@ int batch_create(phia_batch_s **out, int32_t count, const phia_instance_desc *d,
                         return cleanup(bfail(PHIA_EINVAL, "instance %d: CSR is not symmetric at (%d, %d)", k, i, j));
                     col.push_back(j);
                     val.push_back(x.val_k[p]);
+                    ++nnz_real;
                 }
-                rp[i + 1] = x.row_ptr[i + 1];
+                pad_row();
+                rp[i + 1] = (int32_t)(col.size() - in.nz_off);
             }
         }
         rowptr.insert(rowptr.end(), rp.begin(), rp.end());
@@ -216,7 +229,7 @@ int batch_create(phia_batch_s **out, int32_t count, const phia_instance_desc *d,
         b->max_words = std::max<int>(b->max_words, (int)words_of(n));
     }
     b->total_rows = row_base;
-    b->total_nnz = (int64_t)col.size();
+    b->total_nnz = nnz_real;
     int dev_count = 0;
     if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
         return cleanup(bfail(PHIA_ECUDA, "no CUDA device available"));

@@ -52,7 +52,7 @@ __device__ __forceinline__ const uint32_t *spin_buf(const CsrArgs &C, const CsrI
     return C.S + (size_t)(tt & 3) * C.total_swords + in.s_off;
 }
 
-__global__ void __launch_bounds__(32 * kWarps) csr_step(const CsrArgs C) {
+__global__ void __launch_bounds__(32 * kWarps, 3) csr_step(const CsrArgs C) {
     __shared__ int32_t part[kWarps][kGroup];
     __shared__ uint32_t sbits[kRowsPerBlock][kGroup / 32];
 
@@ -103,52 +103,47 @@ __global__ void __launch_bounds__(32 * kWarps) csr_step(const CsrArgs C) {
         const int i = blk.i0 + warp * kRowsPerWarp + q;
         if (i >= N) break;
         const int p_beg = C.row_ptr[in.rp_off + i], p_end = C.row_ptr[in.rp_off + i + 1];
-        // sum_j k_j [s_j^r = +1] per replica r.  Two replicas share a 32-bit accumulator
-        // (low and high 16-bit halves, signed): the byte's bits are spread so that bit 2p
-        // sits at bit 0 and bit 2p+1 at bit 16 of word p, and one multiply-add by k adds
-        // k to both halves at once.  The low half stays below 2^15 in magnitude for up to
-        // 256 couplings (127 * 256 < 32768), so the sums are decoded every 256 couplings.
+        // acc_r = sum_j k_j [s_j^r = +1] for this lane's 8 replicas r.  Rows are padded to
+        // multiples of 8 entries (k = 0), so the warp reads 8 columns and 8 couplings at
+        // a time with broadcast vector loads.  The spin bytes of 4 neighbours form one
+        // word B; (B >> r) & 0x01010101 holds replica r's four bits, one per byte, and a
+        // 4-way int8 dot product with the four couplings adds k [s = +1] for all four.
+        const int32_t *colp = C.col + in.nz_off;
+        const int8_t *valp = C.val + in.nz_off;
+        const uint8_t *Sl = Scur + g * 32 + lane;     // this lane's byte of spin row 0
+        const size_t rowb = (size_t)RW * 4;           // bytes per spin row
         int32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int32_t ksum = 0;
-        int32_t acc2[4] = {0, 0, 0, 0};
-        int since_flush = 0;
-        auto flush = [&]() {
-#pragma unroll
-            for (int q2 = 0; q2 < 4; ++q2) {
-                const int32_t lo = (int32_t)(int16_t)(acc2[q2] & 0xFFFF);
-                acc[2 * q2] += lo;
-                acc[2 * q2 + 1] += (acc2[q2] - lo) >> 16;
-                acc2[q2] = 0;
+        // The next round's columns and couplings load while this round's spins do.
+        int4 c0n = make_int4(0, 0, 0, 0), c1n = c0n;
+        int2 kkn = make_int2(0, 0);
+        if (p_beg < p_end) {
+            c0n = *reinterpret_cast<const int4 *>(colp + p_beg);
+            c1n = *reinterpret_cast<const int4 *>(colp + p_beg + 4);
+            kkn = *reinterpret_cast<const int2 *>(valp + p_beg);
+        }
+        for (int p = p_beg; p < p_end; p += 8) {
+            const int4 c0 = c0n, c1 = c1n;
+            const int2 kk = kkn;
+            if (p + 8 < p_end) {
+                c0n = *reinterpret_cast<const int4 *>(colp + p + 8);
+                c1n = *reinterpret_cast<const int4 *>(colp + p + 12);
+                kkn = *reinterpret_cast<const int2 *>(valp + p + 8);
             }
-        };
-        for (int p0 = p_beg; p0 < p_end; p0 += 32) {
-            const int p = p0 + lane;
-            const int cj = p < p_end ? C.col[in.nz_off + p] : 0;
-            const int kj = p < p_end ? (int)C.val[in.nz_off + p] : 0;
-            const int cnt_chunk = min(32, p_end - p0);
-            if (since_flush + 32 > 256) { flush(); since_flush = 0; }
-            since_flush += 32;
-            for (int e0 = 0; e0 < cnt_chunk; e0 += 8) {
-                uint32_t bytes[8];
-                int ks[8];
+            const uint32_t s0 = Sl[(size_t)c0.x * rowb], s1 = Sl[(size_t)c0.y * rowb];
+            const uint32_t s2 = Sl[(size_t)c0.z * rowb], s3 = Sl[(size_t)c0.w * rowb];
+            const uint32_t s4 = Sl[(size_t)c1.x * rowb], s5 = Sl[(size_t)c1.y * rowb];
+            const uint32_t s6 = Sl[(size_t)c1.z * rowb], s7 = Sl[(size_t)c1.w * rowb];
+            const uint32_t B0 = __byte_perm(__byte_perm(s0, s1, 0x0040), __byte_perm(s2, s3, 0x0040), 0x5410);
+            const uint32_t B1 = __byte_perm(__byte_perm(s4, s5, 0x0040), __byte_perm(s6, s7, 0x0040), 0x5410);
+            ksum = __dp4a(kk.x, 0x01010101, ksum);
+            ksum = __dp4a(kk.y, 0x01010101, ksum);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int c = __shfl_sync(0xffffffffu, cj, (e0 + u) & 31);
-                    ks[u] = __shfl_sync(0xffffffffu, kj, (e0 + u) & 31);
-                    if (e0 + u >= cnt_chunk) ks[u] = 0;
-                    bytes[u] = Scur[(size_t)c * (RW * 4) + g * 32 + lane];
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    ksum += ks[u];
-                    const uint32_t t2 = bytes[u] | (bytes[u] << 15);
-#pragma unroll
-                    for (int q2 = 0; q2 < 4; ++q2)
-                        acc2[q2] += ks[u] * (int32_t)((t2 >> (2 * q2)) & 0x00010001u);
-                }
+            for (int rr = 0; rr < 8; ++rr) {
+                acc[rr] = __dp4a((int)((B0 >> rr) & 0x01010101u), kk.x, acc[rr]);
+                acc[rr] = __dp4a((int)((B1 >> rr) & 0x01010101u), kk.y, acc[rr]);
             }
         }
-        flush();
         const int32_t hk = C.hk[in.h_off + i];
         const size_t xo = in.x_off + (size_t)i * R + r0;
         float4 xa = *reinterpret_cast<const float4 *>(C.X + xo);
