@@ -52,7 +52,7 @@ __device__ __forceinline__ const uint32_t *spin_buf(const CsrArgs &C, const CsrI
     return C.S + (size_t)(tt & 3) * C.total_swords + in.s_off;
 }
 
-__global__ void __launch_bounds__(32 * kWarps, 3) csr_step(const CsrArgs C) {
+__global__ void __launch_bounds__(32 * kWarps, 4) csr_step(const CsrArgs C) {
     __shared__ int32_t part[kWarps][kGroup];
     __shared__ uint32_t sbits[kRowsPerBlock][kGroup / 32];
 
