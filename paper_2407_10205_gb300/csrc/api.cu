@@ -302,13 +302,25 @@ int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, 
     int rc = common_create(out, N, frac_bits, opts, h_k);
     if (rc) return rc;
     if (!J_k) return fail(PHIA_EINVAL, "J_k is NULL");
+    // Symmetry, zero diagonal and max |k| over the upper triangle, in 64 x 64 tiles so that
+    // a tile and its mirror both stay in cache (a row-by-column walk misses on every
+    // element of the mirror for large N).
     int max_abs = 0;
-    for (int i = 0; i < N; ++i) {
+    constexpr int kTile = 64;
+    for (int i = 0; i < N; ++i)
         if (J_k[(size_t)i * N + i] != 0) return fail(PHIA_EINVAL, "nonzero diagonal J_k[%d][%d]", i, i);
-        for (int j = i + 1; j < N; ++j) {
-            const int a = J_k[(size_t)i * N + j], b = J_k[(size_t)j * N + i];
-            if (a != b) return fail(PHIA_EINVAL, "J_k is not symmetric at (%d, %d)", i, j);
-            max_abs = std::max(max_abs, std::abs(a));
+    for (int bi = 0; bi < N; bi += kTile) {
+        const int ie = std::min(N, bi + kTile);
+        for (int bj = bi; bj < N; bj += kTile) {
+            const int je = std::min(N, bj + kTile);
+            for (int i = bi; i < ie; ++i) {
+                const int8_t *row = J_k + (size_t)i * N;
+                for (int j = std::max(bj, i + 1); j < je; ++j) {
+                    const int a = row[j], b = J_k[(size_t)j * N + i];
+                    if (a != b) return fail(PHIA_EINVAL, "J_k is not symmetric at (%d, %d)", i, j);
+                    max_abs = std::max(max_abs, std::abs(a));
+                }
+            }
         }
     }
     phia_opts o{};

@@ -198,6 +198,11 @@ int batch_create(phia_batch_s **out, int32_t count, const phia_instance_desc *d,
         } else {
             if (!x.row_ptr || !x.col || !x.val_k) return cleanup(bfail(PHIA_EINVAL, "instance %d: CSR arrays missing", k));
             if (x.row_ptr[0] != 0) return cleanup(bfail(PHIA_EINVAL, "instance %d: row_ptr[0] != 0", k));
+            for (int i = 0; i < n; ++i)
+                if (x.row_ptr[i + 1] < x.row_ptr[i]) return cleanup(bfail(PHIA_EINVAL, "instance %d: row_ptr decreases", k));
+            // Rows with ascending columns are searched by bisection in the symmetry check.
+            std::vector<uint8_t> row_sorted(n);
+            for (int i = 0; i < n; ++i) row_sorted[i] = std::is_sorted(x.col + x.row_ptr[i], x.col + x.row_ptr[i + 1]);
             for (int i = 0; i < n; ++i) {
                 if (x.row_ptr[i + 1] < x.row_ptr[i]) return cleanup(bfail(PHIA_EINVAL, "instance %d: row_ptr decreases", k));
                 for (int32_t p = x.row_ptr[i]; p < x.row_ptr[i + 1]; ++p) {
@@ -206,7 +211,8 @@ int batch_create(phia_batch_s **out, int32_t count, const phia_instance_desc *d,
                     if (j == i) return cleanup(bfail(PHIA_EINVAL, "instance %d: self loop at %d", k, i));
                     // symmetry: (j, i) must exist with the same value
                     const int32_t *cb = x.col + x.row_ptr[j], *ce = x.col + x.row_ptr[j + 1];
-                    const int32_t *f = std::find(cb, ce, i);
+                    const int32_t *f = row_sorted[j] ? std::lower_bound(cb, ce, i) : std::find(cb, ce, i);
+                    if (f != ce && *f != i) f = ce;
                     if (f == ce || x.val_k[x.row_ptr[j] + (f - cb)] != x.val_k[p])
                         return cleanup(bfail(PHIA_EINVAL, "instance %d: CSR is not symmetric at (%d, %d)", k, i, j));
                     col.push_back(j);
