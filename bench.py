@@ -55,7 +55,7 @@ WORKLOADS = {
                        cmp_instances=8, cmp_iters=20, cpu_instances=4, cpu_iters=50),
     # configs[4]: serving stream, Poisson arrivals at 200/s over a pool of seeded instances
     "serving": dict(kind="serving", pool=32, pool_seed=5, requests=400, arrival_seed=11, rate_hz=200.0,
-                    replicas=256, step_cap=5000, max_inflight=64, budget_gb=64, chunk_iters=100,
+                    replicas=256, step_cap=5000, max_inflight=64, budget_gb=64, chunk_iters=200,
                     cmp_requests=60, cmp_wall_s=90.0,
                     name="serving: Poisson 200/s, N log-uniform [64,8192], half dense {-1,+1}, half sparse "
                          "f=8 density 0.01; 256 replicas, step cap 5000, target = oracle best (4 x 200)"),

@@ -43,6 +43,7 @@ struct Request {
     int64_t step_cap = 0;
     uint64_t seed = 0;
     int64_t bytes = 0;                     // device-memory estimate
+    bool resident = false;                 // dense and small enough for a resident kernel
     // progress
     int state = 0;                         // 0 queued, 1 running, 2 done, < 0 error
     int slot = -1;
@@ -141,7 +142,10 @@ void finish(phia_server_s *S, Request &r, int code) {
 
 // Launch the next chunk of a running request on its slot's stream.
 int launch_chunk(phia_server_s *S, Request &r) {
-    const int64_t chunk = std::min<int64_t>(S->opts.chunk_iters, r.step_cap - r.t_next);
+    // A resident kernel stops at the target by itself inside its one launch, so such a
+    // request runs to its step cap in one chunk; per-iteration paths check between chunks.
+    const int64_t per = r.resident && S->opts.path != PHIA_PATH_FP32 ? r.step_cap : S->opts.chunk_iters;
+    const int64_t chunk = std::min<int64_t>(per, r.step_cap - r.t_next);
     int rc = phia_run(r.h_dev, &r.sched, r.replicas, r.t_next, chunk, r.step_cap, r.seed, r.x, r.v,
                       r.t_next == 0 ? 1 : 0);
     if (rc) return rc;
@@ -284,6 +288,9 @@ int phia_server_submit(phia_server_t *S, const phia_instance_desc *d, const phia
     r.h.assign(d->h_k, d->h_k + d->N);
     if (d->J_k) {
         r.J.assign(d->J_k, d->J_k + (size_t)d->N * d->N);
+        int max_abs = 0;
+        for (int8_t k : r.J) max_abs = std::max(max_abs, k < 0 ? -(int)k : (int)k);
+        r.resident = d->N <= tc_small_max_n(max_abs <= 16 ? kOpE4M3 : kOpBF16);
     } else {
         r.row_ptr.assign(d->row_ptr, d->row_ptr + d->N + 1);
         const int32_t nnz = d->row_ptr[d->N];
