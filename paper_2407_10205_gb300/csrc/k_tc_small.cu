@@ -80,6 +80,46 @@ __device__ __forceinline__ void tmem_ld_sync(uint32_t taddr, float (&v)[RPT]) {
     else tmem_ld_x2_sync(taddr, v);
 }
 
+// Both accumulators (even and odd K-steps) of this thread's RPT columns: the two loads go
+// out together and one wait covers them; the registers pass through the wait so no use
+// is scheduled before it.
+template <int RPT>
+__device__ __forceinline__ void tmem_ld2_sync(uint32_t t0, uint32_t t1, float (&a)[RPT], float (&b)[RPT]) {
+    static_assert(RPT == 2 || RPT == 4 || RPT == 8, "unsupported replicas per thread");
+    uint32_t x[RPT], y[RPT];
+    if constexpr (RPT == 2) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(x[0]), "=r"(x[1]) : "r"(t0));
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(y[0]), "=r"(y[1]) : "r"(t1));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(x[0]), "+r"(x[1]), "+r"(y[0]), "+r"(y[1]) : : "memory");
+    } else if constexpr (RPT == 4) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]) : "r"(t0));
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(y[0]), "=r"(y[1]), "=r"(y[2]), "=r"(y[3]) : "r"(t1));
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(y[0]), "+r"(y[1]), "+r"(y[2]), "+r"(y[3])
+                     :
+                     : "memory");
+    } else {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]), "=r"(x[7])
+                     : "r"(t0));
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(y[0]), "=r"(y[1]), "=r"(y[2]), "=r"(y[3]), "=r"(y[4]), "=r"(y[5]), "=r"(y[6]), "=r"(y[7])
+                     : "r"(t1));
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(x[4]), "+r"(x[5]), "+r"(x[6]), "+r"(x[7]),
+                       "+r"(y[0]), "+r"(y[1]), "+r"(y[2]), "+r"(y[3]), "+r"(y[4]), "+r"(y[5]), "+r"(y[6]), "+r"(y[7])
+                     :
+                     : "memory");
+    }
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        a[k] = __uint_as_float(x[k]);
+        b[k] = __uint_as_float(y[k]);
+    }
+}
+
 // MT: 128-spin output tiles; OP: operand encoding; CH: warps sharing one TMEM lane
 // quadrant (split over replicas); RPT: replicas per thread.  Live replicas per CTA =
 // CH * RPT (8 or 16); the MMA always runs 16 replica columns.
@@ -260,12 +300,13 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
             ok = mbar_wait_bounded(&sm->mbar, phase, kWaitTimeoutNs);
             tc_fence_after();
             float acc[RPT];
-            tmem_ld_sync<RPT>(my_taddr, acc);
             if (two_acc) {
                 float acc2[RPT];
-                tmem_ld_sync<RPT>(my_taddr + kNB, acc2);
+                tmem_ld2_sync<RPT>(my_taddr, my_taddr + kNB, acc, acc2);
 #pragma unroll
                 for (int k = 0; k < RPT; ++k) acc[k] += acc2[k];
+            } else {
+                tmem_ld_sync<RPT>(my_taddr, acc);
             }
             // Field (Eq. 6, exact) and energy terms s_i (I_i + h_i) of every replica first,
             // then their warp sums, then the updates: straight-line code across replicas.
