@@ -96,7 +96,11 @@ typedef struct phia_schedule {
     int32_t has_target;    /* 1: record the first iteration with E <= target_k */
     int32_t stop_at_target;/* 1: freeze a replica's result at its first hit and end the run once
                               every replica has passed the earliest hit */
-    int32_t reserved;      /* must be 0 */
+    int32_t deriv;         /* derivative factor of Eq. 8 in the momentum update: 0 = exact,
+                              1 - tanh^2(gamma x); 1 = quadratic stand-in max(0, 1 - (gamma x /
+                              1.5)^2), after the FPGA's quadratic fit (Sec. 2.2), coefficients
+                              chosen here (value 1 at 0 and integral 2, as the exact factor);
+                              anything else is PHIA_EINVAL */
     int64_t target_k;      /* target energy in units of q */
 } phia_schedule;
 

@@ -63,7 +63,7 @@ class _Sched(ctypes.Structure):
                 ("eps", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("refresh", ctypes.c_int64),
                 ("has_target", ctypes.c_int32), ("stop_at_target", ctypes.c_int32),
-                ("target", ctypes.c_int64)]
+                ("target", ctypes.c_int64), ("deriv", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class _RepOut(ctypes.Structure):
@@ -97,6 +97,12 @@ def _load():
                                      ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_step.restype = ctypes.c_int64
+            lib.orc_step_mode.argtypes = [P(_Inst), ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]
+            lib.orc_step_mode.restype = ctypes.c_int64
+            lib.orc_dfactor.argtypes = [ctypes.c_double, ctypes.c_int32]
+            lib.orc_dfactor.restype = ctypes.c_double
             lib.orc_beta_at.argtypes = [P(_Sched), ctypes.c_int64, ctypes.c_int64]
             lib.orc_beta_at.restype = ctypes.c_double
             lib.orc_anneal_replica.argtypes = [P(_Inst), ctypes.c_int32, P(_Sched), ctypes.c_int64,
@@ -141,10 +147,10 @@ class Instance:
         return math.ldexp(1.0, -self.frac_bits)
 
 
-def _sched(beta0, beta1, eps, gamma, refresh=0, target=None, stop_at_target=False):
+def _sched(beta0, beta1, eps, gamma, refresh=0, target=None, stop_at_target=False, deriv=0):
     return _Sched(float(beta0), float(beta1), float(eps), float(gamma), int(refresh),
                   0 if target is None else 1, 1 if stop_at_target else 0,
-                  0 if target is None else int(target))
+                  0 if target is None else int(target), int(deriv), 0)
 
 
 # ----------------------------------------------------------------- wrappers
@@ -226,15 +232,23 @@ def brute_force(P: Instance):
     return int(e), int(cnt.value), arg
 
 
-def step(P: Instance, x, v, beta, eps, gamma):
-    """One Eq. A7 iteration in FP64.  Returns (x', v', s, I, E)."""
+def step(P: Instance, x, v, beta, eps, gamma, deriv=0):
+    """One Eq. A7 iteration in FP64 (deriv: 0 exact derivative factor of Eq. 8, 1 the
+    quadratic stand-in of `dfactor`).  Returns (x', v', s, I, E)."""
     x = np.array(x, dtype=np.float64, copy=True)
     v = np.array(v, dtype=np.float64, copy=True)
     s = np.empty(P.n, dtype=np.int8)
     I = np.empty(P.n, dtype=np.int64)
-    e = _load().orc_step(ctypes.byref(P._c), P.q, float(beta), float(eps), float(gamma),
-                         _ptr(x), _ptr(v), _ptr(s), _ptr(I))
+    e = _load().orc_step_mode(ctypes.byref(P._c), P.q, float(beta), float(eps), float(gamma), int(deriv),
+                              _ptr(x), _ptr(v), _ptr(s), _ptr(I))
     return x, v, s, I, int(e)
+
+
+def dfactor(y, deriv=0):
+    """The derivative factor of Eq. 8 at y = gamma x: 1 - tanh^2(y), or (deriv = 1) the
+    quadratic stand-in max(0, 1 - (y / 1.5)^2) (coefficients chosen here: the paper
+    prints none)."""
+    return float(_load().orc_dfactor(float(y), int(deriv)))
 
 
 def beta_at(t, T, beta0, beta1):
@@ -242,10 +256,10 @@ def beta_at(t, T, beta0, beta1):
 
 
 def anneal_replica(P: Instance, T, seed, inst_id, r, beta0, beta1, eps, gamma, refresh=0,
-                   target=None, stop_at_target=False, x0=None, v0=None, trace=False):
+                   target=None, stop_at_target=False, x0=None, v0=None, trace=False, deriv=0):
     """One replica of a PHIA run in FP64.  Returns a dict with best_e, best_step,
     hit_step, steps_run, best_s, x, v and (optionally) the per-iteration energies."""
-    S = _sched(beta0, beta1, eps, gamma, refresh, target, stop_at_target)
+    S = _sched(beta0, beta1, eps, gamma, refresh, target, stop_at_target, deriv)
     out = _RepOut()
     best_s = np.zeros(P.n, dtype=np.int8)
     xo = np.empty(P.n); vo = np.empty(P.n)
@@ -263,10 +277,10 @@ def anneal_replica(P: Instance, T, seed, inst_id, r, beta0, beta1, eps, gamma, r
 
 
 def anneal(P: Instance, R, T, seed, inst_id, beta0, beta1, eps, gamma, refresh=0,
-           target=None, stop_at_target=False, threads=None, r0=0, want_spins=True):
+           target=None, stop_at_target=False, threads=None, r0=0, want_spins=True, deriv=0):
     """R replicas (indices r0..r0+R-1) on `threads` host threads.
     Returns arrays best_e[R], best_step[R], hit_step[R], steps_run[R], best_s[R][n]."""
-    S = _sched(beta0, beta1, eps, gamma, refresh, target, stop_at_target)
+    S = _sched(beta0, beta1, eps, gamma, refresh, target, stop_at_target, deriv)
     outs = (_RepOut * R)()
     best_s = np.zeros((R, P.n), dtype=np.int8) if want_spins else None
     th = threads or os.cpu_count() or 1

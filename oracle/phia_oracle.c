@@ -169,6 +169,21 @@ int64_t orc_brute_force(const orc_inst *P, int64_t *n_min, int8_t *argmin)
 /* sgn with sgn(0) = +1 (the paper leaves sgn(0) open). */
 static int8_t orc_sgn(double x) { return x >= 0.0 ? 1 : -1; }
 
+/* The derivative factor of Eq. 8 at y = gamma x: 1 - tanh^2(y) (deriv = 0), or
+ * (deriv = 1) a quadratic stand-in for it.  Sec. 2.2 says the FPGA approximates the
+ * derivative by a quadratic polynomial but prints no coefficients; the ones here are
+ * this implementation's own choice: max(0, 1 - (y / 1.5)^2), equal to the exact factor
+ * at y = 0 and with the same integral over the real line (4 * 1.5 / 3 = 2). */
+double orc_dfactor(double y, int32_t deriv)
+{
+    if (deriv == 1) {
+        double u = y / 1.5;
+        return u * u >= 1.0 ? 0.0 : 1.0 - u * u;
+    }
+    double t = tanh(y);
+    return 1.0 - t * t;
+}
+
 /* One iteration of Eq. A7 with the gradient of Eq. A8 under the tanh surrogate
  * (Eqs. 7-8):
  *   x <- x + eps v
@@ -177,19 +192,25 @@ static int8_t orc_sgn(double x) { return x >= 0.0 ? 1 : -1; }
  *   dH/dx_i = -beta * gamma (1 - tanh^2(gamma x_i)) * q * I_i + x_i   (Eqs. 4, 5, 8)
  *   v <- v - eps dH/dx
  * Writes s and I (units of q); returns E(s) in units of q. */
-int64_t orc_step(const orc_inst *P, double q, double beta, double eps, double gamma,
-                 double *x, double *v, int8_t *s, int64_t *I)
+int64_t orc_step_mode(const orc_inst *P, double q, double beta, double eps, double gamma, int32_t deriv,
+                      double *x, double *v, int8_t *s, int64_t *I)
 {
     int n = P->n;
     for (int i = 0; i < n; ++i) x[i] = x[i] + eps * v[i];
     for (int i = 0; i < n; ++i) s[i] = orc_sgn(x[i]);
     orc_field(P, s, I);
     for (int i = 0; i < n; ++i) {
-        double t = tanh(gamma * x[i]);
-        double grad = -beta * gamma * (1.0 - t * t) * q * (double)I[i] + x[i];
+        double grad = -beta * gamma * orc_dfactor(gamma * x[i], deriv) * q * (double)I[i] + x[i];
         v[i] = v[i] - eps * grad;
     }
     return orc_energy_from_field(P, s, I);
+}
+
+/* The same with the exact derivative factor. */
+int64_t orc_step(const orc_inst *P, double q, double beta, double eps, double gamma,
+                 double *x, double *v, int8_t *s, int64_t *I)
+{
+    return orc_step_mode(P, q, beta, eps, gamma, 0, x, v, s, I);
 }
 
 /* Annealing schedule (Table 3, state 4: the temperature is adjusted as the run
@@ -203,6 +224,8 @@ typedef struct {
     int32_t has_target;
     int32_t stop_at_target;
     int64_t target;
+    int32_t deriv;      /* derivative factor: 0 exact, 1 quadratic stand-in (orc_dfactor) */
+    int32_t pad;
 } orc_sched;
 
 double orc_beta_at(const orc_sched *S, int64_t t, int64_t T)
@@ -251,7 +274,7 @@ void orc_anneal_replica(const orc_inst *P, int32_t frac_bits, const orc_sched *S
         if (S->refresh > 0 && t > 0 && t % S->refresh == 0)
             for (int j = 0; j < n; ++j) orc_draw(seed, inst_id, r, (uint32_t)j, (uint32_t)t, NULL, &v[j]);
         double beta = orc_beta_at(S, t, T);
-        int64_t e = orc_step(P, q, beta, S->eps, S->gamma, x, v, s, I);
+        int64_t e = orc_step_mode(P, q, beta, S->eps, S->gamma, S->deriv, x, v, s, I);
         if (energy_trace) energy_trace[t] = e;
         out->steps_run = t + 1;
         int frozen = S->stop_at_target && out->hit_step >= 0;

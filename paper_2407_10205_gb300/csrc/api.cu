@@ -172,7 +172,7 @@ int check_sched(const phia_schedule *s) {
     if (!(s->eps > 0.0f) || !(s->gamma > 0.0f)) return fail(PHIA_EINVAL, "eps and gamma must be > 0");
     if (!(s->beta0 >= 0.0f) || !(s->beta1 >= 0.0f)) return fail(PHIA_EINVAL, "beta0 and beta1 must be >= 0");
     if (s->refresh < 0) return fail(PHIA_EINVAL, "refresh must be >= 0");
-    if (s->reserved != 0) return fail(PHIA_EINVAL, "schedule.reserved must be 0");
+    if (s->deriv != 0 && s->deriv != 1) return fail(PHIA_EINVAL, "schedule.deriv must be 0 or 1");
     return PHIA_OK;
 }
 
@@ -462,6 +462,7 @@ static int run_impl(phia_t *p, const phia_schedule *sched, int32_t R, int64_t t0
     a.t0 = t0; a.nsteps = steps; a.T_total = total;
     a.beta0 = sched->beta0; a.beta1 = sched->beta1; a.eps = sched->eps; a.gamma = sched->gamma;
     a.refresh = sched->refresh;
+    a.deriv = sched->deriv;
     a.seed = seed;
     a.x_in = x_in; a.v_in = v_in; a.x_out = x_out; a.v_out = v_out;
     a.has_target = sched->has_target; a.stop_at_target = sched->stop_at_target; a.target = sched->target_k;

@@ -277,7 +277,7 @@ int batch_run(phia_batch_s *b, const phia_schedule *sched, int32_t R_real, int64
     const bool field_mode = spins_in != nullptr;
     if (!field_mode) {
         if (!sched) return bfail(PHIA_EINVAL, "schedule is NULL");
-        if (!(sched->eps > 0.0f) || !(sched->gamma > 0.0f) || sched->refresh < 0 || sched->reserved != 0)
+        if (!(sched->eps > 0.0f) || !(sched->gamma > 0.0f) || sched->refresh < 0 || (sched->deriv != 0 && sched->deriv != 1))
             return bfail(PHIA_EINVAL, "invalid schedule");
         if (steps < 1 || t0 < 0 || total < t0 + steps) return bfail(PHIA_EINVAL, "need steps >= 1, t0 + steps <= total");
         if (total > ((int64_t)1 << 31)) return bfail(PHIA_ERANGE, "total_steps must be < 2^31");
@@ -314,6 +314,7 @@ int batch_run(phia_batch_s *b, const phia_schedule *sched, int32_t R_real, int64
     if (!field_mode) {
         a.beta0 = sched->beta0; a.beta1 = sched->beta1; a.eps = sched->eps; a.gamma = sched->gamma;
         a.refresh = sched->refresh;
+        a.deriv = sched->deriv;
         a.has_target = (sched->has_target || b->any_target) ? 1 : 0;
         a.stop_at_target = sched->stop_at_target;
         a.target = sched->target_k;

@@ -74,11 +74,26 @@ __device__ __forceinline__ float rcp_approx(float x) {
 //   v' = v + eps * (beta gamma (1 - tanh^2(gamma x)) q I - x),   bgq = beta * gamma * q,
 // with 1 - tanh^2(y) = sech^2(y) = 4 e / (1 + e)^2, e = exp(-2 |y|) = 2^(-2 log2(e) |y|)
 // (e <= 1, so nothing overflows for any y).
-__device__ __forceinline__ float momentum_update(float v, float x, float I, float eps, float bgq,
-                                                 float gamma) {
+// Callers branch on the run's derivative mode once per loop, not per element, so each
+// kernel inlines one straight-line form and all kernels produce the same bits.
+__device__ __forceinline__ float momentum_exact(float v, float x, float I, float eps, float bgq, float gamma) {
     const float e = ex2_approx(-2.8853900817779268f * fabsf(gamma * x));
     const float d = 1.0f + e;
     return v + eps * ((4.0f * bgq) * (e * rcp_approx(d * d)) * I - x);
+}
+
+// The same with the factor replaced by the quadratic stand-in max(0, 1 - (gamma x / 1.5)^2)
+// (schedule deriv = 1; after the FPGA's quadratic fit, Sec. 2.2, coefficients chosen here:
+// value 1 at 0 and integral 2, as the exact factor).
+__device__ __forceinline__ float momentum_quad(float v, float x, float I, float eps, float bgq, float gamma) {
+    const float u = __fmul_rn(__fmul_rn(gamma, x), 0.6666667f);   // gamma x / 1.5
+    const float f = __fmul_rn(bgq, fmaxf(0.0f, __fmaf_rn(-u, u, 1.0f)));
+    return __fmaf_rn(eps, __fmaf_rn(f, I, -x), v);
+}
+
+__device__ __forceinline__ float momentum_update(float v, float x, float I, float eps, float bgq, float gamma,
+                                                 int deriv) {
+    return deriv == 1 ? momentum_quad(v, x, I, eps, bgq, gamma) : momentum_exact(v, x, I, eps, bgq, gamma);
 }
 
 // beta_t linear from beta0 (t = 0) to beta1 (t = T-1); inv_tm1 = 1 / (T - 1), 0 if T <= 1.

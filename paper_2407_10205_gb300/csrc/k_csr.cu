@@ -153,11 +153,24 @@ __global__ void __launch_bounds__(32 * kWarps, 4) csr_step(const CsrArgs C) {
         float xs[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
         float vs[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
         uint32_t nbyte = 0;
+        float If[8];
 #pragma unroll
         for (int rr = 0; rr < 8; ++rr) {
             const int32_t I = 2 * acc[rr] - ksum + hk;                    // Eq. 6, exact
             epart[rr] += (xs[rr] >= 0.0f ? 1 : -1) * (I + hk);
-            float v = momentum_update(vs[rr], xs[rr], (float)I, eps, bgq, gamma);
+            If[rr] = (float)I;
+        }
+        float vn[8];
+        if (a.deriv == 1) {
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr) vn[rr] = momentum_quad(vs[rr], xs[rr], If[rr], eps, bgq, gamma);
+        } else {
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr) vn[rr] = momentum_exact(vs[rr], xs[rr], If[rr], eps, bgq, gamma);
+        }
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+            float v = vn[rr];
             float x = xs[rr];
             if (more) {
                 if (refresh_next) v = draw_v(a.seed, in.inst_id, (uint32_t)(r0 + rr), (uint32_t)i, (uint32_t)(t + 1));

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256) fp32_step(const RunArgs a, int64_t t, flo
             if (a.field_mode) {
                 if (a.field_out) a.field_out[idx] = (int32_t)Ik;
             } else {
-                float vi = momentum_update(v[idx], x[idx], I, a.eps, bgq, a.gamma);
+                float vi = momentum_update(v[idx], x[idx], I, a.eps, bgq, a.gamma, a.deriv);
                 float xi = x[idx];
                 if (more) {
                     if (refresh_next) vi = draw_v(a.seed, a.inst, (uint32_t)r, (uint32_t)i, (uint32_t)(t + 1));

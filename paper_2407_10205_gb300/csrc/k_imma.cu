@@ -192,8 +192,13 @@ __global__ void __launch_bounds__(64 * KS, 1) imma_small_kernel(const RunArgs a,
         } else {
             const float bgq = beta_at(t, inv_tm1, a.beta0, a.beta1) * gq;
             const bool more = it + 1 < nit;
+            if (a.deriv == 1) {
 #pragma unroll
-            for (int q = 0; q < 4 * NT; ++q) v[q] = momentum_update(v[q], x[q], (float)Ik[q], eps, bgq, gamma);
+                for (int q = 0; q < 4 * NT; ++q) v[q] = momentum_quad(v[q], x[q], (float)Ik[q], eps, bgq, gamma);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4 * NT; ++q) v[q] = momentum_exact(v[q], x[q], (float)Ik[q], eps, bgq, gamma);
+            }
             if (more) {
                 if (a.refresh > 0 && rc == 0) {
 #pragma unroll

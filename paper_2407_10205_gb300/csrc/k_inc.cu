@@ -152,8 +152,13 @@ __global__ void __launch_bounds__(1024) inc_small_kernel(const RunArgs a) {
             const bool more = it + 1 < nit;
             if (live_i) {
                 const float bgq = beta_at(t, inv_tm1, a.beta0, a.beta1) * gq;
+                if (a.deriv == 1) {
 #pragma unroll
-                for (int k = 0; k < RPT; ++k) v[k] = momentum_update(v[k], x[k], (float)I[k], eps, bgq, gamma);
+                    for (int k = 0; k < RPT; ++k) v[k] = momentum_quad(v[k], x[k], (float)I[k], eps, bgq, gamma);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < RPT; ++k) v[k] = momentum_exact(v[k], x[k], (float)I[k], eps, bgq, gamma);
+                }
                 if (more) {
                     if (a.refresh > 0 && rc == 0) {
 #pragma unroll

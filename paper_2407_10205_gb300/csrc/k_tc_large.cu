@@ -422,12 +422,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float vs[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
                 const int nlive = live_i ? ncol - col0 : 0;   // live columns of this chunk for this thread
                 int32_t p[8];
+                float If[kChunk];
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j) {
                     const int32_t Ik = __float2int_rn(acc[j]) + hki;            // Eq. 6, exact
                     const int32_t e = Ik + hki;
                     p[j] = j < nlive ? (xs[j] >= 0.0f ? e : -e) : 0;
-                    vs[j] = momentum_update(vs[j], xs[j], (float)Ik, eps, bgq, gamma);
+                    If[j] = (float)Ik;
+                }
+                if (a.deriv == 1) {
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j) vs[j] = momentum_quad(vs[j], xs[j], If[j], eps, bgq, gamma);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j) vs[j] = momentum_exact(vs[j], xs[j], If[j], eps, bgq, gamma);
                 }
                 const int32_t psum = warp_sum8(p, lane);
                 if ((lane & 3) == 0) sh->part[b][q4][cg * kColsPerWarp + col0 + (lane >> 2)] = psum;

@@ -129,7 +129,7 @@ __device__ __forceinline__ void tmem_ld2_sync(uint32_t t0, uint32_t t1, float (&
 // control warps follow: lane 0 of control warp m issues the field MMAs of output tile m
 // (in parallel with the other tiles' issue), the first RL lanes of control warp 0 keep
 // the records, so MMA issue and records overlap the epilogue warps' work.
-template <int MT, int OP, int CH, int RPT, bool AT>
+template <int MT, int OP, int CH, int RPT, bool AT, int DERIV>
 __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_small_kernel(const RunArgs a, int Kpad) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
     constexpr int RL = CH * RPT;
@@ -331,8 +331,13 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
             } else if (live_i) {
                 const float bgq = beta_at(t, inv_tm1, a.beta0, a.beta1) * gq;
                 const bool more = it + 1 < nit;
+                if constexpr (DERIV == 1) {
 #pragma unroll
-                for (int k = 0; k < RPT; ++k) v[k] = momentum_update(v[k], x[k], (float)Ik[k], eps, bgq, gamma);
+                    for (int k = 0; k < RPT; ++k) v[k] = momentum_quad(v[k], x[k], (float)Ik[k], eps, bgq, gamma);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < RPT; ++k) v[k] = momentum_exact(v[k], x[k], (float)Ik[k], eps, bgq, gamma);
+                }
                 if (more) {
                     if (a.refresh > 0 && rc == 0) {
 #pragma unroll
@@ -456,7 +461,8 @@ cudaError_t launch_cfg(const RunArgs &a, int Kpad, cudaStream_t st) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
     constexpr int RL = CH * RPT;
     const size_t smem = (size_t)((AT ? 0 : MT * 128) + kNB) * Kpad * ESZ + sizeof(SmallShared) + 16;
-    auto kern = tc_small_kernel<MT, OP, CH, RPT, AT>;
+    // The derivative mode is a template parameter: the update loop stays straight-line.
+    auto kern = a.deriv == 1 ? tc_small_kernel<MT, OP, CH, RPT, AT, 1> : tc_small_kernel<MT, OP, CH, RPT, AT, 0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (a.R + RL - 1) / RL;

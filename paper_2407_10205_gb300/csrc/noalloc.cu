@@ -73,7 +73,7 @@ extern "C" int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N
     if (frac_bits < 0 || frac_bits > 30) return set_last_error(PHIA_EINVAL, "phia_run_noalloc: frac_bits not in [0, 30]");
     if (operand != PHIA_OP_E4M3 && operand != PHIA_OP_BF16 && operand != PHIA_OP_AUTO)
         return set_last_error(PHIA_EINVAL, "phia_run_noalloc: unknown operand");
-    if (!(sched->eps > 0.0f) || !(sched->gamma > 0.0f) || sched->refresh < 0 || sched->reserved != 0)
+    if (!(sched->eps > 0.0f) || !(sched->gamma > 0.0f) || sched->refresh < 0 || (sched->deriv != 0 && sched->deriv != 1))
         return set_last_error(PHIA_EINVAL, "phia_run_noalloc: invalid schedule");
     const int op = operand == PHIA_OP_E4M3 ? kOpE4M3 : kOpBF16;   // AUTO: bf16, exact for every int8 k
 
@@ -135,6 +135,7 @@ extern "C" int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N
     a.beta0 = sched->beta0; a.beta1 = sched->beta1; a.eps = sched->eps; a.gamma = sched->gamma;
     a.q = ldexpf(1.0f, -frac_bits);
     a.refresh = sched->refresh;
+    a.deriv = sched->deriv;
     a.seed = seed;
     a.inst = instance_id;
     a.x_in = x; a.v_in = v; a.x_out = x; a.v_out = v;

@@ -21,6 +21,7 @@ struct RunArgs {
     int64_t t0, nsteps, T_total;
     float beta0, beta1, eps, gamma, q;
     int32_t refresh;
+    int32_t deriv;              // derivative factor of Eq. 8: 0 exact, 1 quadratic stand-in
     uint64_t seed;
     uint32_t inst;
     const float *x_in, *v_in;   // initial state, or null -> Philox draw d = 0

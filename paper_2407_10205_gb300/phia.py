@@ -42,7 +42,7 @@ class Opts(ctypes.Structure):
 class Schedule(ctypes.Structure):
     _fields_ = [("beta0", ctypes.c_float), ("beta1", ctypes.c_float), ("eps", ctypes.c_float),
                 ("gamma", ctypes.c_float), ("refresh", ctypes.c_int32), ("has_target", ctypes.c_int32),
-                ("stop_at_target", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("stop_at_target", ctypes.c_int32), ("deriv", ctypes.c_int32),
                 ("target_k", ctypes.c_int64)]
 
 
@@ -163,9 +163,13 @@ def _dev_ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def schedule(beta0, beta1, eps, gamma, refresh=0, target=None, stop_at_target=False) -> Schedule:
+DERIV_EXACT, DERIV_QUADRATIC = 0, 1
+
+
+def schedule(beta0, beta1, eps, gamma, refresh=0, target=None, stop_at_target=False,
+             deriv=DERIV_EXACT) -> Schedule:
     return Schedule(float(beta0), float(beta1), float(eps), float(gamma), int(refresh),
-                    0 if target is None else 1, 1 if stop_at_target else 0, 0,
+                    0 if target is None else 1, 1 if stop_at_target else 0, int(deriv),
                     0 if target is None else int(target))
 
 

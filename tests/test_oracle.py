@@ -168,6 +168,53 @@ def test_three_spin_step_matches_hand_derivation():
     assert np.allclose(v, f("v_new"), rtol=1e-14, atol=0)
 
 
+def test_quadratic_derivative_factor():
+    """The quadratic stand-in for the derivative factor of Eq. 8 (deriv = 1; the paper's
+    FPGA uses a quadratic fit whose coefficients it does not print, these are chosen
+    here): 1 at y = 0, 0 from |y| = 1.5 on, even, never above 1, and its integral over
+    the real line is 2, the integral of the exact factor sech^2 (tanh(+inf) -
+    tanh(-inf)), both checked by the midpoint rule."""
+    assert o.dfactor(0.0, 1) == 1.0 and o.dfactor(0.0, 0) == 1.0
+    for y in (1.5, -1.5, 1.6, -7.0, 40.0):
+        assert o.dfactor(y, 1) == 0.0
+    ys = np.linspace(-2.0, 2.0, 401)
+    q = np.array([o.dfactor(y, 1) for y in ys])
+    qm = np.array([o.dfactor(-y, 1) for y in ys])
+    assert np.all(q <= 1.0) and np.array_equal(q, qm)
+    h = 1e-4
+    mid = np.arange(-1.5 + h / 2, 1.5, h)
+    assert abs(sum(o.dfactor(y, 1) for y in mid) * h - 2.0) < 1e-6
+    mid = np.arange(-12.0 + h / 2, 12.0, h)
+    assert abs(sum(o.dfactor(y, 0) for y in mid) * h - 2.0) < 1e-6
+
+
+def test_quadratic_derivative_step():
+    """deriv = 1 changes only the derivative factor: where every |gamma x'| >= 1.5 the
+    field term vanishes (v' = v - eps x' exactly); where every x' = 0 both factors are 1
+    and the update equals the exact one; elsewhere the two differ."""
+    g = read_golden("three_spin_step.txt")
+    k = np.array(g["J"].split(), dtype=np.int8).reshape(3, 3)
+    kh = np.array(g["h"].split(), dtype=np.int32)
+    P = _dense(k, kh)
+    eps, gamma, beta = 0.1, 2.0, 1.3
+    x, v = np.array([1.0, -1.0, 2.0]), np.array([0.5, -0.5, 0.1])
+    xn, vn, *_ = o.step(P, x, v, beta, eps, gamma, deriv=1)
+    assert np.all(np.abs(gamma * xn) >= 1.5)
+    assert np.array_equal(vn, v - eps * xn)
+    v0 = np.array([0.3, -0.7, 1.1])
+    x0 = -(eps * v0)
+    a = o.step(P, x0, v0, beta, eps, gamma, deriv=1)
+    b = o.step(P, x0, v0, beta, eps, gamma, deriv=0)
+    assert np.array_equal(a[0], np.zeros(3)) and np.array_equal(a[1], b[1])
+    c = o.step(P, f64(g["x"]), f64(g["v"]), beta, eps, gamma, deriv=1)
+    d = o.step(P, f64(g["x"]), f64(g["v"]), beta, eps, gamma, deriv=0)
+    assert not np.allclose(c[1], d[1])
+
+
+def f64(text):
+    return np.array(text.split(), dtype=np.float64)
+
+
 def test_beta_zero_discrete_invariant():
     """With beta = 0 the update is symplectic Euler on a unit oscillator per spin;
     x^2 + v^2 + eps x v is then exactly conserved (up to FP64 rounding)."""
