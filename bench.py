@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -53,6 +54,12 @@ WORKLOADS = {
                             "(k ~ U[-127,127]), h = k/16 (k ~ U[-31,31]); 256 replicas each x 2000 iterations, "
                             "one batch",
                        cmp_instances=8, cmp_iters=20, cpu_instances=4, cpu_iters=50),
+    # time-to-solution scaling of PHIA alone (Eq. 9) on SK instances of growing n
+    "tts": dict(kind="tts", sizes=(8, 16, 32, 64, 128, 256, 512, 1024), instances=20, replicas=256,
+                iterations=1000, ref_replicas=1024, ref_factor=20, seed=9,
+                name="TTS99 scaling: SK instances (J in {-1,+1}, h = 0), n = 8..1024, 20 instances per n; "
+                     "256 replicas x 1000 max(1, n/128) iterations against the best of 1024 replicas x 20 times "
+                     "as many"),
     # configs[4]: serving stream, Poisson arrivals at 200/s over a pool of seeded instances
     "serving": dict(kind="serving", pool=32, pool_seed=5, requests=400, arrival_seed=11, rate_hz=200.0,
                     replicas=256, step_cap=5000, max_inflight=64, budget_gb=64, chunk_iters=200,
@@ -416,6 +423,54 @@ def run_serving(args, w):
     return 0
 
 
+def run_tts(args, w):
+    """Time to solution (Eq. 9, 99% confidence) of PHIA alone against n on SK instances.
+    Per instance: the reference energy is the best found by a long run (ref_replicas x
+    ref_factor * iterations); P is the fraction of the short run's replicas whose best
+    energy reaches it; T1 is the short run's device time divided by its replicas (the
+    replicas run concurrently, so this is the time one run costs at full occupancy).
+    Reported per n: medians over the instances."""
+    import torch
+    from paper_2407_10205_gb300 import phia, instances as ins, schedules
+    rows = []
+    t_start = time.perf_counter()
+    for n in w["sizes"]:
+        ps, ttss, t1s = [], [], []
+        T = w["iterations"] * max(1, n // 128)
+        for k in range(w["instances"]):
+            d = ins.sk_pm1(n, w["seed"] * 100_003 + n * 1000 + k)
+            b0, b1, eps, gamma, refresh = schedules.suggest_schedule(d)
+            sched = phia.schedule(b0, b1, eps, gamma, refresh=refresh)
+            with phia.Annealer(d.k, d.kh, path=phia.PATH_TC) as A:
+                A.anneal(sched, w["ref_replicas"], T * w["ref_factor"], 1 + k)
+                ref, _ = phia.best(A.h, n)
+                phia.anneal(A.h, sched, w["replicas"], T, 7_777 + k)
+                st = phia.stats_get(A.h)
+                be, _, _, _ = phia.replica_results(A.h, w["replicas"], n)
+            p = float(np.mean(be <= ref))
+            t1 = st.device_ms * 1e-3 / w["replicas"]
+            if p <= 0.0:
+                tts = math.inf
+            elif p >= 0.99:
+                tts = t1
+            else:
+                tts = t1 * math.log(1.0 - 0.99) / math.log(1.0 - p)
+            ps.append(p); ttss.append(tts); t1s.append(t1)
+        med = float(np.median(ttss))
+        rows.append({"n": n, "iterations": T, "instances": w["instances"], "p_median": float(np.median(ps)),
+                     "p_min": float(np.min(ps)), "t1_s": float(np.median(t1s)),
+                     "tts99_s_median": med if math.isfinite(med) else None,
+                     "solved_instances": int(np.sum(np.array(ps) > 0))})
+    line = {"metric": "TTS99 (median over instances; null = not reached)", "value": rows[-1]["tts99_s_median"],
+            "unit": "s",
+            "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "dtype": "fp32",
+            "config": {"workload": w["name"], "replicas": w["replicas"],
+                       "reference": f"best of {w['ref_replicas']} replicas x {w['ref_factor']} times the iterations"},
+            "table": rows, "wall_s": time.perf_counter() - t_start}
+    print(json.dumps(line))
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -429,6 +484,8 @@ def run_ours(args):
     w = WORKLOADS[args.workload]
     if w["kind"] == "batch":
         return run_batch(args, w)
+    if w["kind"] == "tts":
+        return run_tts(args, w)
     if w["kind"] == "serving":
         w = dict(w)
         if args.max_inflight:
