@@ -18,8 +18,8 @@
 // of one group sit together for each spin, so a thread (one spin, an 8-replica chunk)
 // moves its values as two 16-byte vectors, a warp's vector covers 512 contiguous bytes,
 // and no padded element lies outside the array.
-// They reach the epilogue through a per-thread shared-memory ring filled by cp.async two
-// chunks ahead (across tile boundaries); results are stored straight to global memory.
+// They reach the epilogue through a per-thread shared-memory ring filled by cp.async one
+// chunk ahead (across tile boundaries); results are stored straight to global memory.
 // The prologue converts a caller's [R][N] state in, an export kernel converts it out.
 // Records (Table 3, state 5) are lagged so no CTA waits for another: the launch for
 // iteration t lets the tiles of output row 0 settle the energies of iteration t-1 (sum
@@ -49,7 +49,7 @@ constexpr int kEpiWarps = 16;  // four per TMEM lane quadrant, each a quarter of
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;
 constexpr int kChunk = 8;                      // replica columns per epilogue step (two x/v groups)
-constexpr int kRing = 3;                       // x/v chunks per thread: the current + kRing - 1 ahead
+constexpr int kRing = 2;                       // x/v chunks per thread: the current + kRing - 1 ahead
 constexpr uint32_t kStageA = kBM * kBKB;
 constexpr uint32_t kRingBytes = kRing * kChunk * kEpiThreads * 4;   // per array (x or v)
 static_assert(kChunk == 8, "a chunk is two 4-replica groups of the x/v layout");
@@ -66,11 +66,12 @@ struct LargeShared {
 };
 
 // Tile shape: 128 output spins x BN replicas.  BN = 256 halves the coupling-operand
-// traffic per output against BN = 128 (the shared-memory ring then holds 2 stages);
-// BN = 128 keeps more tiles when replicas are few.
+// traffic per output against BN = 128;
+// BN = 128 keeps more tiles when replicas are few.  Three operand stages and a two-chunk
+// x/v ring fit either shape (the third stage outweighs a deeper x/v prefetch).
 template <int BN>
 struct Tile {
-    static constexpr int kStages = BN == 256 ? 2 : 3;
+    static constexpr int kStages = 3;
     static constexpr uint32_t kStageB = BN * kBKB;
     static constexpr int kColsPerWarp = BN / (kEpiWarps / 4);
     static constexpr int kChunksPerTile = kColsPerWarp / kChunk;
