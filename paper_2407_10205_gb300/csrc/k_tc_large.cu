@@ -698,6 +698,4 @@ cudaError_t launch_tc_large(const LargeBuffers &B, const RunArgs &a, int op, cud
     return wide ? run_large<kOpBF16, 256>(B, a, st, launches, sms) : run_large<kOpBF16, 128>(B, a, st, launches, sms);
 }
 
-size_t tc_large_smem_bytes() { return Tile<256>::kSmemBytes; }
-
 }  // namespace phia
