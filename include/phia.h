@@ -94,8 +94,9 @@ typedef struct phia_schedule {
     int32_t refresh;       /* momentum redrawn before iteration t when t % refresh == 0, t > 0;
                               0 = drawn only at the start */
     int32_t has_target;    /* 1: record the first iteration with E <= target_k */
-    int32_t stop_at_target;/* 1: freeze a replica's result at its first hit and end the run once
-                              every replica has passed the earliest hit */
+    int32_t stop_at_target;/* 1: freeze a replica's result at its first hit; the resident
+                              kernels also end the run once every replica has passed the
+                              earliest hit, the per-iteration paths run all their iterations */
     int32_t deriv;         /* derivative factor of Eq. 8 in the momentum update: 0 = exact,
                               1 - tanh^2(gamma x); 1 = quadratic stand-in max(0, 1 - (gamma x /
                               1.5)^2), after the FPGA's quadratic fit (Sec. 2.2), coefficients
