@@ -43,7 +43,7 @@ namespace {
 
 constexpr int kBM = 128;       // output spins per tile (TMEM lanes)
 constexpr int kBKB = 128;      // bytes of K per pipeline stage (one 128-byte swizzle row)
-constexpr int kMaxStages = 3;
+constexpr int kMaxStages = 4;
 constexpr int kMaxBN = 256;
 constexpr int kEpiWarps = 16;  // four per TMEM lane quadrant, each a quarter of the columns
 constexpr int kEpiThreads = 32 * kEpiWarps;
@@ -67,11 +67,12 @@ struct LargeShared {
 
 // Tile shape: 128 output spins x BN replicas.  BN = 256 halves the coupling-operand
 // traffic per output against BN = 128;
-// BN = 128 keeps more tiles when replicas are few.  Three operand stages and a two-chunk
-// x/v ring fit either shape (the third stage outweighs a deeper x/v prefetch).
+// BN = 128 keeps more tiles when replicas are few.  With a two-chunk x/v ring the
+// 256-wide tile has room for three operand stages, the 128-wide one for four (more
+// stages in flight outweigh a deeper x/v prefetch).
 template <int BN>
 struct Tile {
-    static constexpr int kStages = 3;
+    static constexpr int kStages = BN == 256 ? 3 : 4;
     static constexpr uint32_t kStageB = BN * kBKB;
     static constexpr int kColsPerWarp = BN / (kEpiWarps / 4);
     static constexpr int kChunksPerTile = kColsPerWarp / kChunk;
