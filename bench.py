@@ -78,7 +78,7 @@ ALGO_OPS_PER_UPDATE = 16
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each kernel, from the
 # committed ncu summaries under profiles/; absent once a kernel changed after its capture.
 KERNEL_TRAFFIC_BYTES = {
-    "tc_large_step": 86_754_304 + 16_649_216,      # N = 2000, 4096 replicas (one iteration)
+    "tc_large_step": 86_751_744 + 16_593_152,      # N = 2000, 4096 replicas (one iteration)
     "csr_step": 975_856_896 + 773_062_144,          # 256 ER instances, 256 replicas (one iteration)
     "tc_small_kernel": 137_472,                     # N = 200, 1024 replicas (a launch is the whole run)
 }
