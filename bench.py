@@ -41,7 +41,7 @@ WORKLOADS = {
                      beta0=0.01, beta1=0.1, eps=0.1, gamma=2.0, refresh=50, run_seed=12345,
                      name="N=200 dense, k and kh uniform int [-7,7]; 1024 replicas x 2000 iterations, "
                           "linear beta 0.01->0.1",
-                     cmp_iters=2000, cpu_replicas=128, cpu_iters=2000),
+                     cmp_iters=2000, cpu_replicas=1024, cpu_iters=2000),
     # configs[2]: complete graph N=2000, J in {-1,+1}, h = 0
     "dense2000": dict(N=2000, kind="pm1", seed=3, replicas=4096, iterations=5000,
                       beta0=0.005, beta1=0.134, eps=0.1, gamma=2.0, refresh=50, run_seed=777,
@@ -99,8 +99,54 @@ def _instance(w=None):
     return ins.dense_int(w["N"], w["kmax"], w["hmax"], w["seed"])
 
 
+# sampler period: 1 ms polling slowed the timed process's host calls (not its device time)
+CLOCK_POLL_MS = 5.0
+# NVML clock-event reason bits (nvml.h) reported by the sampler
+_NVML_REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+                 "hw_thermal_slowdown": 0x40}
+
+
+def _nvml_poll(dev, period_ms):
+    """Body of the sampler's child process: print `monotonic_s,sm_mhz,max_sm_mhz,reason_bits`
+    for the device (PCI bus id or NVML index) every `period_ms`, reading NVML through ctypes.
+    Read-only queries; exits non-zero if NVML or the device is unavailable, zero once its
+    parent is gone."""
+    import ctypes
+    try:
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+    except OSError:
+        return 1
+    if nv.nvmlInit_v2() != 0:
+        return 1
+    h = ctypes.c_void_p()
+    if ":" in dev:
+        rc = nv.nvmlDeviceGetHandleByPciBusId_v2(dev.encode(), ctypes.byref(h))
+    else:
+        rc = nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(int(dev)), ctypes.byref(h))
+    if rc != 0:
+        return 1
+    reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+        nv.nvmlDeviceGetCurrentClocksThrottleReasons
+    NVML_CLOCK_SM = 1
+    mx, clk, bits = ctypes.c_uint(0), ctypes.c_uint(0), ctypes.c_ulonglong(0)
+    nv.nvmlDeviceGetMaxClockInfo(h, NVML_CLOCK_SM, ctypes.byref(mx))
+    parent = os.getppid()
+    try:
+        while os.getppid() == parent:             # ends with the timed process
+            if nv.nvmlDeviceGetClockInfo(h, NVML_CLOCK_SM, ctypes.byref(clk)) == 0 and \
+                    reasons(h, ctypes.byref(bits)) == 0:
+                print(f"{time.monotonic():.6f},{clk.value},{mx.value},{bits.value}", flush=True)
+            time.sleep(period_ms * 1e-3)
+    except (BrokenPipeError, KeyboardInterrupt):
+        pass
+    return 0
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """SM clock and clock-event (throttle) reasons sampled DURING the timed region: NVML
+    polled every CLOCK_POLL_MS by a child process (so short regions still get samples and the
+    timed process is not disturbed); only samples stamped inside the `with` block count.
+    Falls back to nvidia-smi every 200 ms where NVML cannot be loaded."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -108,46 +154,105 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.source = None
+        self.lines = []
 
-    def __enter__(self):
+    def _device_key(self):
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(self.gpu)
+            return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+        except Exception:
+            return str(self.gpu)
+
+    def start(self):
+        """Start the poller (before warm-up: a new NVML client stalls the process's first
+        host calls after it attaches, which must not land in the timed region).  Samples go
+        to a temporary file, so a long warm-up cannot fill a pipe and stall the poller."""
+        if self.proc is not None:
+            return self
+        import tempfile
+        self.out = tempfile.TemporaryFile(mode="w+b")
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                [sys.executable, os.path.abspath(__file__), "--clock-poll", self._device_key()],
+                stdout=self.out, stderr=subprocess.DEVNULL, text=True)
+            deadline = time.monotonic() + 30.0
+            while self.proc.poll() is None and os.fstat(self.out.fileno()).st_size == 0 \
+                    and time.monotonic() < deadline:
+                time.sleep(0.01)                       # the poller is live before timing starts
+            if self.proc.poll() is None and os.fstat(self.out.fileno()).st_size > 0:
+                self.source = f"nvml, {CLOCK_POLL_MS:g} ms"
+            else:
+                self._stop()
         except OSError:
             self.proc = None
+        if self.proc is None:
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                     "--format=csv,noheader,nounits", "-lms", "200"],
+                    stdout=self.out, stderr=subprocess.DEVNULL)
+                self.source = "nvidia-smi, 200 ms"
+            except OSError:
+                self.proc = None
+        return self
+
+    def _stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.proc.wait()
+            self.proc = None
+
+    def __enter__(self):
+        self.start()
+        self.off0 = os.fstat(self.out.fileno()).st_size     # output written before the region
+        self.t0 = time.monotonic()
         return self
 
     def __exit__(self, *a):
-        self.lines = []
-        if self.proc:
-            self.proc.terminate()
-            try:
-                out, _ = self.proc.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+        self.t1 = time.monotonic()
+        self._stop()
+        self.out.seek(0)
+        data = self.out.read()
+        self.out.close()
+        cut = data.rfind(b"\n", 0, self.off0) + 1             # whole lines from the region on
+        self.lines = [l for l in data[cut:].decode(errors="replace").splitlines() if l.strip()]
 
-    def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
+    def _samples(self):
+        """(sm_mhz, max_mhz, set of active reason names) per sample inside the region."""
+        out = []
+        for l in self.lines:
             f = [t.strip() for t in l.split(",")]
-            if len(f) < 9:
-                continue
             try:
-                sm.append(float(f[1])); mx = float(f[2])
+                if self.source and self.source.startswith("nvml"):
+                    if len(f) != 4 or not (self.t0 <= float(f[0]) <= self.t1):
+                        continue
+                    bits = int(f[3])
+                    out.append((float(f[1]), float(f[2]),
+                                {n for n, b in _NVML_REASONS.items() if bits & b}))
+                elif len(f) >= 9:
+                    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+                    out.append((float(f[1]), float(f[2]),
+                                {n for n, val in zip(names, f[5:9]) if val.lower().startswith("active")}))
             except ValueError:
                 continue
-            for n, val in zip(names, f[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
-        loaded = [s for s in sm if mx is None or s > 0.5 * mx] or sm
+        return out
+
+    def summary(self):
+        s = self._samples()
+        reasons = set().union(*(r for _, _, r in s)) if s else set()
+        mx = s[-1][1] if s else None
+        if not s:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0, "source": self.source}
+        sm = [c for c, _, _ in s]
+        loaded = [c for c in sm if mx is None or c > 0.5 * mx] or sm
         return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "sm_mhz_min": min(sm), "source": self.source}
 
 
 def cpu_baseline(w=None, sample_replicas=None):
@@ -169,6 +274,10 @@ def cpu_baseline(w=None, sample_replicas=None):
             "sample": f"{R} of the {w['replicas']} replicas x {T} of {w['iterations']} iterations ({dt:.1f} s)"}
 
 
+# oracle replicas per step of the reference arm (about 0.6 s on 16 cores)
+REF_REPLICAS_PER_STEP = 256
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
@@ -176,16 +285,16 @@ def run_reference(args):
     per_step = []
     cb = None
     for k in range(args.warmup + args.steps):
-        r = cpu_baseline(sample_replicas=32)
+        r = cpu_baseline(sample_replicas=REF_REPLICAS_PER_STEP)
         if k >= args.warmup:
             per_step.append(r["value"])
             cb = r
     val = statistics.median(per_step)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 32 * WORKLOAD["N"] * WORKLOAD["iterations"] / val * 1e3,
+            "ms_per_step": REF_REPLICAS_PER_STEP * WORKLOAD["N"] * WORKLOAD["iterations"] / val * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "sample_replicas_per_step": 32},
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "sample_replicas_per_step": REF_REPLICAS_PER_STEP},
             "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": val,
                              "unit": METRIC},
             "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -254,13 +363,15 @@ def run_batch(args, w):
     Ns = np.array([c.n for c in insts])
     nnz = np.array([c.nnz for c in insts])
     su_step = int(R * T * Ns.sum())
+    cs = ClockSampler(0).start()
     with phia.Batch(insts, stream=stream.cuda_stream) as B:
         for _ in range(args.warmup):
+            flush.fill_(0.0)                          # the flush kernel is loaded before timing
             B.anneal(sched, R, T, w["run_seed"])
             B.sync()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         torch.cuda.synchronize()
-        with ClockSampler(0) as cs:
+        with cs:
             for k in range(args.steps):
                 flush.fill_(float(k))
                 torch.cuda.current_stream().synchronize()
@@ -386,9 +497,10 @@ def run_serving(args, w):
     pool = ins.serving_pool(w["pool"], w["pool_seed"])
     targets = [e["target_k"] for e in tdoc["entries"]]
     arrivals = ins.serving_arrivals(w["requests"], w["arrival_seed"], len(pool), w["rate_hz"])
+    cs = ClockSampler(0).start()
     # warm-up: one request of each pool entry (builds kernels, loads modules)
     _serve_stream(phia, pool, targets, [(0.0, k, 1) for k in range(len(pool))], w, phia.PATH_AUTO)
-    with ClockSampler(0) as cs:
+    with cs:
         sts, st, complete = _serve_stream(phia, pool, targets, arrivals, w, phia.PATH_AUTO)
     done = [s for s in sts if s.state == 2]
     span = max(s.t_done_s for s in done) - min(s.t_submit_s for s in sts)
@@ -507,13 +619,15 @@ def run_ours(args):
 
     with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, stream=stream.cuda_stream) as A:
         tune = phia.autotune(A.h, sched, R, probe_iters=min(T, 200))   # kernel variant for (N, R)
+        cs = ClockSampler(local).start()
         for _ in range(args.warmup):
+            flush.fill_(0.0)                          # the flush kernel is loaded before timing
             phia.anneal(A.h, sched, R, T, seed)
             phia.sync(A.h)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         launches = 0
         barrier()
-        with ClockSampler(local) as cs:
+        with cs:
             t_wall = time.perf_counter()
             for k in range(args.steps):
                 flush.fill_(float(k))                     # L2 flush between timed steps
@@ -607,6 +721,8 @@ def run_ours(args):
 
 
 def main():
+    if len(sys.argv) == 3 and sys.argv[1] == "--clock-poll":
+        return _nvml_poll(sys.argv[2], CLOCK_POLL_MS)
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
