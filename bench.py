@@ -78,9 +78,9 @@ ALGO_OPS_PER_UPDATE = 16
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each kernel, from the
 # committed ncu summaries under profiles/; absent once a kernel changed after its capture.
 KERNEL_TRAFFIC_BYTES = {
-    "tc_large_step": 86_751_744 + 16_593_152,      # N = 2000, 4096 replicas (one iteration)
-    "csr_step": 975_856_896 + 773_062_144,          # 256 ER instances, 256 replicas (one iteration)
-    "tc_small_kernel": 137_472,                     # N = 200, 1024 replicas (a launch is the whole run)
+    "tc_large_step": 86_755_328 + 15_568_384,      # N = 2000, 4096 replicas (one iteration)
+    "csr_step": 975_639_296 + 772_641_536,          # 256 ER instances, 256 replicas (one iteration)
+    "tc_small_kernel": 146_432,                     # N = 200, 1024 replicas (a launch is the whole run)
 }
 
 

@@ -120,6 +120,12 @@ typedef struct phia_stats {
     int32_t kernel_launches; /* kernels launched by the last run */
     int32_t tc_kernel;     /* dense kernel used (1 resident tcgen05, 2 per iteration, 3 resident
                               int8 mma.sync, 4 resident incremental field), 0 for other paths */
+    int32_t reserved0;     /* 0 */
+    int64_t hit_ns;        /* device time to target: %globaltimer nanoseconds from the start of
+                              the run (its record reset, the first call of a resumed run) to
+                              the recording of hit_step for hit_replica, or -1.  The resident
+                              kernels record a hit in the iteration itself; the per-iteration
+                              paths settle records one launch later (Table 3, state 5). */
 } phia_stats;
 
 typedef struct phia_s phia_t;

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/phia.h"
+#include "device_common.cuh"
 #include "phia_internal.h"
 
 using namespace phia;
@@ -39,14 +40,16 @@ int fail(int code, const char *fmt, ...) {
     } while (0)
 
 __global__ void reset_records_kernel(int R, int W, int64_t *best_e, int64_t *best_step, int64_t *hit,
-                                     uint32_t *bits) {
+                                     uint32_t *bits, uint64_t *hit_ns, uint64_t *start_ns) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < R) {
         best_e[idx] = LLONG_MAX;
         best_step[idx] = -1;
         hit[idx] = -1;
+        hit_ns[idx] = 0;
     }
     if (idx < (int64_t)R * W) bits[idx] = 0u;
+    if (idx == 0) *start_ns = phia::globaltimer_ns();   // the run's start on the device clock
 }
 
 }  // namespace
@@ -92,6 +95,8 @@ struct phia_s {
     int64_t *d_eacc = nullptr;
     int64_t *d_best_e = nullptr, *d_best_step = nullptr, *d_hit = nullptr;
     uint32_t *d_bits = nullptr;
+    uint64_t *d_hit_ns = nullptr;       // %globaltimer of each replica's first hit
+    uint64_t *d_start_ns = nullptr;     // %globaltimer when the run's records were reset
     // run counters
     unsigned long long *d_min_hit = nullptr, *d_iters = nullptr;
     int32_t *d_err = nullptr;
@@ -111,8 +116,9 @@ void free_replicas(phia_t *p) {
     p->d_S = nullptr; p->d_Epart = nullptr; p->d_flags = nullptr; p->d_X = p->d_V = nullptr;
     cudaFree(p->d_x); cudaFree(p->d_v); cudaFree(p->d_s0); cudaFree(p->d_s1); cudaFree(p->d_eacc);
     cudaFree(p->d_best_e); cudaFree(p->d_best_step); cudaFree(p->d_hit); cudaFree(p->d_bits);
+    cudaFree(p->d_hit_ns);
     p->d_x = p->d_v = nullptr; p->d_s0 = p->d_s1 = nullptr; p->d_eacc = nullptr;
-    p->d_best_e = p->d_best_step = p->d_hit = nullptr; p->d_bits = nullptr;
+    p->d_best_e = p->d_best_step = p->d_hit = nullptr; p->d_bits = nullptr; p->d_hit_ns = nullptr;
     p->R_cap = 0;
 }
 
@@ -141,6 +147,7 @@ int ensure_replicas(phia_t *p, int R) {
     al((void **)&p->d_best_e, (size_t)R * 8);
     al((void **)&p->d_best_step, (size_t)R * 8);
     al((void **)&p->d_hit, (size_t)R * 8);
+    al((void **)&p->d_hit_ns, (size_t)R * 8);
     al((void **)&p->d_bits, (size_t)R * p->W * 4);
     if (!ok) {
         cudaGetLastError();
@@ -162,7 +169,8 @@ int ensure_replicas(phia_t *p, int R) {
 int reset_records(phia_t *p, int R) {
     const int64_t n = std::max<int64_t>(R, (int64_t)R * p->W);
     reset_records_kernel<<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(R, p->W, p->d_best_e, p->d_best_step,
-                                                                             p->d_hit, p->d_bits);
+                                                                             p->d_hit, p->d_bits, p->d_hit_ns,
+                                                                             p->d_start_ns);
     CU(cudaGetLastError());
     return PHIA_OK;
 }
@@ -189,6 +197,7 @@ RunArgs base_args(phia_t *p, int R) {
     a.q = ldexpf(1.0f, -p->frac_bits);
     a.inst = p->inst;
     a.best_e = p->d_best_e; a.best_step = p->d_best_step; a.hit_step = p->d_hit;
+    a.hit_ns = p->d_hit_ns;
     a.best_bits = p->d_bits; a.W = p->W;
     a.min_hit = p->d_min_hit; a.replica_iters = p->d_iters; a.err = p->d_err;
     a.tile_rl = p->tile_rl;
@@ -279,6 +288,8 @@ int finish_create(phia_t *p, const int32_t *h_k, const phia_opts *opts) {
     CU(cudaMalloc((void **)&p->d_hk, (size_t)p->N * 4));
     CU(cudaMemcpyAsync(p->d_hk, h_k, (size_t)p->N * 4, cudaMemcpyHostToDevice, p->stream));
     CU(cudaMalloc((void **)&p->d_min_hit, 8));
+    CU(cudaMalloc((void **)&p->d_start_ns, 8));
+    CU(cudaMemsetAsync(p->d_start_ns, 0, 8, p->stream));
     CU(cudaMalloc((void **)&p->d_iters, 8));
     CU(cudaMalloc((void **)&p->d_err, 4));
     CU(cudaMemsetAsync(p->d_err, 0, 4, p->stream));
@@ -683,6 +694,13 @@ int phia_stats_get(phia_t *p, phia_stats *out) {
     out->hit_replica = -1;
     for (int k = 0; k < (int)hs.size(); ++k)
         if (hs[k] >= 0 && (out->hit_step < 0 || hs[k] < out->hit_step)) { out->hit_step = hs[k]; out->hit_replica = k; }
+    out->hit_ns = -1;
+    if (out->hit_replica >= 0) {
+        uint64_t t_hit = 0, t_start = 0;
+        CU(cudaMemcpy(&t_hit, p->d_hit_ns + out->hit_replica, 8, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(&t_start, p->d_start_ns, 8, cudaMemcpyDeviceToHost));
+        if (t_hit >= t_start && t_start != 0) out->hit_ns = (int64_t)(t_hit - t_start);
+    }
     out->device_ms = ms;
     out->path = p->path;
     out->operand = p->op == kOpE4M3 ? PHIA_OP_E4M3 : (p->op == kOpBF16 ? PHIA_OP_BF16 : 0);
@@ -699,7 +717,7 @@ void phia_destroy(phia_t *p) {
     free_replicas(p);
     cudaFree(p->d_Jk); cudaFree(p->d_Jf); cudaFree(p->d_hk); cudaFree(p->d_Jop);
     cudaFree(p->d_rowptr); cudaFree(p->d_col); cudaFree(p->d_val);
-    cudaFree(p->d_min_hit); cudaFree(p->d_iters); cudaFree(p->d_err); cudaFree(p->d_ctl);
+    cudaFree(p->d_min_hit); cudaFree(p->d_iters); cudaFree(p->d_err); cudaFree(p->d_ctl); cudaFree(p->d_start_ns);
     step_graphs_free(p->graphs);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/phia.h"
+#include "device_common.cuh"
 #include "phia_internal.h"
 
 using namespace phia;
@@ -41,6 +42,8 @@ struct phia_batch_s {
     int64_t *d_best_e = nullptr, *d_best_step = nullptr, *d_hit = nullptr;
     uint32_t *d_bits = nullptr;
     unsigned long long *d_min_hit = nullptr, *d_iters = nullptr;
+    uint64_t *d_hit_ns = nullptr;       // %globaltimer of each replica's first hit
+    uint64_t *d_start_ns = nullptr;     // %globaltimer when the run's records were reset
     int32_t *d_err = nullptr;
     IterCtl *d_ctl = nullptr;               // iteration control of the step kernel
     StepGraphCache *graphs = nullptr;       // its step launches as replayable graphs
@@ -69,21 +72,24 @@ int bfail(int code, const char *fmt, ...) {
     } while (0)
 
 __global__ void batch_reset_records(int64_t n, int64_t nbits, int64_t *best_e, int64_t *best_step, int64_t *hit,
-                                    uint32_t *bits) {
+                                    uint32_t *bits, uint64_t *hit_ns, uint64_t *start_ns) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < n) {
         best_e[idx] = LLONG_MAX;
         best_step[idx] = -1;
         hit[idx] = -1;
+        hit_ns[idx] = 0;
     }
     if (idx < nbits) bits[idx] = 0u;
+    if (idx == 0) *start_ns = globaltimer_ns();   // the run's start on the device clock
 }
 
 void free_state(phia_batch_s *b) {
     cudaFree(b->d_X); cudaFree(b->d_V); cudaFree(b->d_S); cudaFree(b->d_Esum); cudaFree(b->d_flags);
     cudaFree(b->d_best_e); cudaFree(b->d_best_step); cudaFree(b->d_hit); cudaFree(b->d_bits);
+    cudaFree(b->d_hit_ns);
     b->d_X = b->d_V = nullptr; b->d_S = nullptr; b->d_Esum = nullptr; b->d_flags = nullptr;
-    b->d_best_e = b->d_best_step = b->d_hit = nullptr; b->d_bits = nullptr;
+    b->d_best_e = b->d_best_step = b->d_hit = nullptr; b->d_bits = nullptr; b->d_hit_ns = nullptr;
     b->Rcap = 0;
 }
 
@@ -123,6 +129,7 @@ int ensure_state(phia_batch_s *b, int R) {
     al((void **)&b->d_best_e, (size_t)reps * 8);
     al((void **)&b->d_best_step, (size_t)reps * 8);
     al((void **)&b->d_hit, (size_t)reps * 8);
+    al((void **)&b->d_hit_ns, (size_t)reps * 8);
     al((void **)&b->d_bits, (size_t)bits * 4);
     if (!ok) {
         cudaGetLastError();
@@ -257,6 +264,8 @@ int batch_create(phia_batch_s **out, int32_t count, const phia_instance_desc *d,
     up((void **)&b->d_targets, b->targets.data(), b->targets.size() * sizeof(long long));
     if (ok && cudaMalloc((void **)&b->d_inst, sizeof(CsrInst) * count) != cudaSuccess) ok = false;
     if (ok && cudaMalloc((void **)&b->d_min_hit, 8) != cudaSuccess) ok = false;
+    if (ok && cudaMalloc((void **)&b->d_start_ns, 8) != cudaSuccess) ok = false;
+    if (ok && cudaMemset(b->d_start_ns, 0, 8) != cudaSuccess) ok = false;
     if (ok && cudaMalloc((void **)&b->d_iters, 8) != cudaSuccess) ok = false;
     if (ok && cudaMalloc((void **)&b->d_err, 4) != cudaSuccess) ok = false;
     if (ok && cudaMalloc((void **)&b->d_ctl, sizeof(IterCtl)) != cudaSuccess) ok = false;
@@ -298,8 +307,8 @@ int batch_run(phia_batch_s *b, const phia_schedule *sched, int32_t R_real, int64
     int launches = 0;
     if (reset && !field_mode) {
         const int64_t n = std::max(reps, nbits);
-        batch_reset_records<<<(unsigned)((n + 255) / 256), 256, 0, b->stream>>>(reps, nbits, b->d_best_e,
-                                                                                b->d_best_step, b->d_hit, b->d_bits);
+        batch_reset_records<<<(unsigned)((n + 255) / 256), 256, 0, b->stream>>>(
+            reps, nbits, b->d_best_e, b->d_best_step, b->d_hit, b->d_bits, b->d_hit_ns, b->d_start_ns);
         BCU(cudaGetLastError());
         ++launches;
     }
@@ -323,6 +332,7 @@ int batch_run(phia_batch_s *b, const phia_schedule *sched, int32_t R_real, int64
     a.field_mode = field_mode ? 1 : 0;
     a.spins_in = spins_in; a.field_out = field_out; a.energy_out = energy_out;
     a.best_e = b->d_best_e; a.best_step = b->d_best_step; a.hit_step = b->d_hit;
+    a.hit_ns = b->d_hit_ns;
     a.min_hit = b->d_min_hit; a.replica_iters = b->d_iters; a.err = b->d_err;
     C.inst = b->d_inst; C.count = b->count;
     C.blocks = b->d_blocks; C.nblocks = (int32_t)b->blocks.size();
@@ -457,6 +467,14 @@ int batch_stats(phia_batch_s *b, int inst, phia_stats *out) {
     out->hit_replica = -1;
     for (int k = 0; k < (int)hs.size(); ++k)
         if (hs[k] >= 0 && (out->hit_step < 0 || hs[k] < out->hit_step)) { out->hit_step = hs[k]; out->hit_replica = k; }
+    out->hit_ns = -1;
+    if (out->hit_replica >= 0) {
+        uint64_t t_hit = 0, t_start = 0;
+        BCU(cudaMemcpy(&t_hit, b->d_hit_ns + (size_t)(inst < 0 ? 0 : inst) * b->R + out->hit_replica, 8,
+                       cudaMemcpyDeviceToHost));
+        BCU(cudaMemcpy(&t_start, b->d_start_ns, 8, cudaMemcpyDeviceToHost));
+        if (t_hit >= t_start && t_start != 0) out->hit_ns = (int64_t)(t_hit - t_start);
+    }
     out->device_ms = ms;
     out->path = PHIA_PATH_CSR;
     out->kernel_launches = b->last_launches;
@@ -506,7 +524,7 @@ void phia_batch_destroy(phia_batch_t *b) {
     cudaStreamSynchronize(b->stream);
     free_state(b);
     cudaFree(b->d_inst); cudaFree(b->d_blocks); cudaFree(b->d_rowptr); cudaFree(b->d_col); cudaFree(b->d_val);
-    cudaFree(b->d_hk); cudaFree(b->d_targets); cudaFree(b->d_min_hit); cudaFree(b->d_iters); cudaFree(b->d_err);
+    cudaFree(b->d_hk); cudaFree(b->d_targets); cudaFree(b->d_min_hit); cudaFree(b->d_start_ns); cudaFree(b->d_iters); cudaFree(b->d_err);
     cudaFree(b->d_ctl);
     step_graphs_free(b->graphs);
     if (b->ev0) cudaEventDestroy(b->ev0);

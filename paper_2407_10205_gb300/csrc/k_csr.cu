@@ -43,7 +43,10 @@ __device__ __forceinline__ void settle_csr(const CsrArgs &C, const CsrInst &in, 
         imp = 1;
     }
     const long long target = C.targets ? C.targets[b] : a.target;
-    if (a.has_target && a.hit_step[rec] < 0 && E <= target) a.hit_step[rec] = tt;
+    if (a.has_target && a.hit_step[rec] < 0 && E <= target) {
+        a.hit_step[rec] = tt;
+        if (a.hit_ns) a.hit_ns[rec] = globaltimer_ns();
+    }
     C.flags[(size_t)(tt & 1) * C.total_reps + rec] = (int8_t)imp;
     (void)b;
 }

@@ -119,7 +119,10 @@ __global__ void fp32_record(const RunArgs a, int64_t t, const int8_t *s_cur, int
             a.best_step[r] = t;
             imp = 1;
         }
-        if (a.has_target && a.hit_step[r] < 0 && E <= a.target) a.hit_step[r] = t;
+        if (a.has_target && a.hit_step[r] < 0 && E <= a.target) {
+            a.hit_step[r] = t;
+            if (a.hit_ns) a.hit_ns[r] = globaltimer_ns();
+        }
     }
     imp = __shfl_sync(0xffffffffu, imp, 0);
     if (!imp) return;

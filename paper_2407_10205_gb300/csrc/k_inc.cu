@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(1024) inc_small_kernel(const RunArgs a) {
                     }
                     if (a.has_target && sm->hit[c] < 0 && E <= a.target) {
                         sm->hit[c] = t;
+                        if (a.hit_ns) a.hit_ns[r] = globaltimer_ns();
                         if (a.stop_at_target) atomicMin(a.min_hit, (unsigned long long)t);
                     }
                 }

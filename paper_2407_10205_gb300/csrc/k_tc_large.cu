@@ -189,7 +189,10 @@ __device__ __forceinline__ void settle_replica(const LargeArgs &L, int r, int64_
         a.best_step[r] = tt;
         imp = 1;
     }
-    if (a.has_target && a.hit_step[r] < 0 && E <= a.target) a.hit_step[r] = tt;
+    if (a.has_target && a.hit_step[r] < 0 && E <= a.target) {
+        a.hit_step[r] = tt;
+        if (a.hit_ns) a.hit_ns[r] = globaltimer_ns();
+    }
     L.flags[(size_t)(tt & 1) * L.Rpad + r] = (int8_t)imp;
 }
 

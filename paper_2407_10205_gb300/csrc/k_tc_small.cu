@@ -37,6 +37,7 @@ struct SmallShared {
     long long best_e[kNB];
     long long best_step[kNB];
     long long hit[kNB];
+    unsigned long long hit_ns[kNB];        // %globaltimer of the first hit (written out at the end)
     int32_t improved[2][kNB];              // by iteration parity
 };
 
@@ -186,6 +187,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
         sm->best_e[tid] = rec ? a.best_e[r] : LLONG_MAX;
         sm->best_step[tid] = rec ? a.best_step[r] : -1;
         sm->hit[tid] = rec ? a.hit_step[r] : -1;
+        sm->hit_ns[tid] = (rec && a.hit_ns) ? a.hit_ns[r] : 0ull;
     }
     if (tid == 0) sm->stop[0] = sm->stop[1] = 0;
     tc_fence_before();
@@ -380,6 +382,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
                     }
                     if (a.has_target && sm->hit[c] < 0 && E <= a.target) {
                         sm->hit[c] = t;
+                        sm->hit_ns[c] = globaltimer_ns();
                         if (a.stop_at_target) atomicMin(a.min_hit, (unsigned long long)t);
                     }
                 }
@@ -438,6 +441,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
             a.best_e[r] = sm->best_e[lane];
             a.best_step[r] = sm->best_step[lane];
             a.hit_step[r] = sm->hit[lane];
+            if (a.hit_ns) a.hit_ns[r] = sm->hit_ns[lane];
         }
     }
     if (ctl && cw == 0 && lane == 0) {

@@ -33,6 +33,7 @@ struct RunArgs {
     int64_t *energy_out;        // [R]
     // per-replica records
     int64_t *best_e, *best_step, *hit_step;
+    uint64_t *hit_ns;           // %globaltimer when hit_step was recorded (null: not kept)
     uint32_t *best_bits;        // [R][W]
     int32_t W;
     int32_t has_target, stop_at_target;

@@ -51,7 +51,8 @@ class Stats(ctypes.Structure):
                 ("best_energy_k", ctypes.c_int64), ("best_replica", ctypes.c_int64),
                 ("best_step", ctypes.c_int64), ("hit_step", ctypes.c_int64), ("hit_replica", ctypes.c_int64),
                 ("device_ms", ctypes.c_float), ("path", ctypes.c_int32), ("operand", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int32), ("tc_kernel", ctypes.c_int32)]
+                ("kernel_launches", ctypes.c_int32), ("tc_kernel", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("hit_ns", ctypes.c_int64)]
 
 
 class InstanceDesc(ctypes.Structure):
