@@ -138,6 +138,16 @@ typedef struct phia_s phia_t;
 int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N,
                 int32_t frac_bits, const phia_opts *opts);
 
+/* Create a dense instance from device memory (for example PyTorch tensors): J_k, N*N
+ * int8 row-major, and h_k, N int32, both on opts->device (device or managed memory).
+ * Same requirements, errors, options and ownership as phia_create: the checks
+ * (symmetry, zero diagonal, |h_k| < 2^24, max |k| for the operand) run on the device,
+ * ordered after the caller's work on opts->stream; J and h are copied device to device
+ * into the handle's buffers; the caller keeps its buffers.  Host pointers, or buffers on
+ * another device -> PHIA_EINVAL. */
+int phia_create_from_device(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N,
+                            int32_t frac_bits, const phia_opts *opts);
+
 /* Create a sparse instance in CSR form (host arrays): row_ptr[N+1], col[nnz]
  * (0 <= col < N, no self loops), val_k[nnz] int8; the pattern and values must be
  * symmetric.  Stored zeros are allowed.  Runs on the CSR path (a batch of one); its

@@ -52,6 +52,36 @@ __global__ void reset_records_kernel(int R, int W, int64_t *best_e, int64_t *bes
     if (idx == 0) *start_ns = phia::globaltimer_ns();   // the run's start on the device clock
 }
 
+// Instance checks of phia_create_from_device, on the device: res[0] = lowest linear index
+// i*N + j (i < j) with k_ij != k_ji, res[1] = lowest i with k_ii != 0, res[2] = lowest i
+// with |kh_i| >= 2^24 (ULLONG_MAX where none), res[3] = max |k_ij| over i < j.
+__global__ void check_dense_kernel(const int8_t *J, const int32_t *h, int N, unsigned long long *res) {
+    const int64_t total = (int64_t)N * N;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned int mx = 0;
+    for (int64_t e = first; e < total; e += stride) {
+        const int i = (int)(e / N), j = (int)(e - (int64_t)i * N);
+        const int k = J[e];
+        if (j > i) {
+            if (k != J[(int64_t)j * N + i]) atomicMin(&res[0], (unsigned long long)e);
+            mx = max(mx, (unsigned int)abs(k));
+        } else if (j == i && k != 0) {
+            atomicMin(&res[1], (unsigned long long)i);
+        }
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(&res[3], (unsigned long long)mx);
+    for (int64_t i = first; i < N; i += stride)
+        if (h[i] >= (1 << 24) || h[i] <= -(1 << 24)) atomicMin(&res[2], (unsigned long long)i);
+}
+
+// J = k q in FP32 for the FP32 path, from the device copy of k.
+__global__ void k_to_f32_kernel(const int8_t *k, float *jf, int64_t n, float q) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        jf[e] = (float)k[e] * q;
+}
+
 }  // namespace
 
 namespace phia {
@@ -272,21 +302,23 @@ cudaError_t launch_path(phia_t *p, const RunArgs &a, int *launches) {
     return cudaErrorNotSupported;
 }
 
-int common_create(phia_t **out, int32_t N, int32_t frac_bits, const phia_opts *opts, const int32_t *h_k) {
+int common_create(phia_t **out, int32_t N, int32_t frac_bits, const phia_opts *opts, const int32_t *h_k,
+                  bool host_h = true) {
     if (!out) return fail(PHIA_EINVAL, "out is NULL");
     *out = nullptr;
     if (N < 1) return fail(PHIA_EINVAL, "N must be >= 1 (got %d)", N);
     if (N > (1 << 20)) return fail(PHIA_ERANGE, "N = %d exceeds 2^20", N);
     if (frac_bits < 0 || frac_bits > 30) return fail(PHIA_EINVAL, "frac_bits must be in [0, 30]");
     if (!h_k) return fail(PHIA_EINVAL, "h_k is NULL");
-    for (int i = 0; i < N; ++i)
+    for (int i = 0; host_h && i < N; ++i)
         if (h_k[i] >= (1 << 24) || h_k[i] <= -(1 << 24)) return fail(PHIA_ERANGE, "|h_k[%d]| >= 2^24", i);
     return PHIA_OK;
 }
 
-int finish_create(phia_t *p, const int32_t *h_k, const phia_opts *opts) {
+int finish_create(phia_t *p, const int32_t *h_k, const phia_opts *opts,
+                  cudaMemcpyKind h_kind = cudaMemcpyHostToDevice) {
     CU(cudaMalloc((void **)&p->d_hk, (size_t)p->N * 4));
-    CU(cudaMemcpyAsync(p->d_hk, h_k, (size_t)p->N * 4, cudaMemcpyHostToDevice, p->stream));
+    CU(cudaMemcpyAsync(p->d_hk, h_k, (size_t)p->N * 4, h_kind, p->stream));
     CU(cudaMalloc((void **)&p->d_min_hit, 8));
     CU(cudaMalloc((void **)&p->d_start_ns, 8));
     CU(cudaMemsetAsync(p->d_start_ns, 0, 8, p->stream));
@@ -308,34 +340,91 @@ extern "C" {
 
 const char *phia_last_error(void) { return g_err.c_str(); }
 
-int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, int32_t frac_bits,
-                const phia_opts *opts) {
-    int rc = common_create(out, N, frac_bits, opts, h_k);
+}  // extern "C"
+
+namespace {
+
+// The checks of phia_create on device-resident J and h, on opts.device and opts.stream.
+int check_dense_on_device(const int8_t *J_k, const int32_t *h_k, int N, const phia_opts &o, int *max_abs) {
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
+        return fail(PHIA_ECUDA, "no CUDA device available");
+    if (o.device < 0 || o.device >= dev_count) return fail(PHIA_EINVAL, "device %d out of range", o.device);
+    CU(cudaSetDevice(o.device));
+    const void *ptrs[2] = {J_k, h_k};
+    for (const void *ptr : ptrs) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return fail(PHIA_EINVAL, "J_k and h_k must be device memory (phia_create takes host arrays)");
+        }
+        if (at.type == cudaMemoryTypeDevice && at.device != o.device)
+            return fail(PHIA_EINVAL, "J_k / h_k are on device %d, opts.device is %d", at.device, o.device);
+    }
+    int sms = 0;
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device));
+    cudaStream_t st = (cudaStream_t)o.stream;
+    unsigned long long *res = nullptr;
+    CU(cudaMalloc((void **)&res, 4 * sizeof(unsigned long long)));
+    const unsigned long long init[4] = {ULLONG_MAX, ULLONG_MAX, ULLONG_MAX, 0ull};
+    unsigned long long got[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(res, init, sizeof init, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        const int64_t total = (int64_t)N * N;
+        const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)sms * 8));
+        check_dense_kernel<<<blocks, 256, 0, st>>>(J_k, h_k, N, res);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(got, res, sizeof got, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(res);
+    if (e != cudaSuccess) return fail(PHIA_ECUDA, "device instance check failed: %s", cudaGetErrorString(e));
+    if (got[2] != ULLONG_MAX) return fail(PHIA_ERANGE, "|h_k[%llu]| >= 2^24", got[2]);
+    if (got[1] != ULLONG_MAX) return fail(PHIA_EINVAL, "nonzero diagonal J_k[%llu][%llu]", got[1], got[1]);
+    if (got[0] != ULLONG_MAX)
+        return fail(PHIA_EINVAL, "J_k is not symmetric at (%llu, %llu)", got[0] / (unsigned long long)N,
+                    got[0] % (unsigned long long)N);
+    *max_abs = (int)got[3];
+    return PHIA_OK;
+}
+
+// phia_create (host J, h) and phia_create_from_device (device J, h): same checks, options
+// and buffers; the checks run where the data lives and the copies are host-to-device or
+// device-to-device.
+int create_dense(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, int32_t frac_bits,
+                 const phia_opts *opts, bool dev) {
+    int rc = common_create(out, N, frac_bits, opts, h_k, !dev);
     if (rc) return rc;
     if (!J_k) return fail(PHIA_EINVAL, "J_k is NULL");
-    // Symmetry, zero diagonal and max |k| over the upper triangle, in 64 x 64 tiles so that
-    // a tile and its mirror both stay in cache (a row-by-column walk misses on every
-    // element of the mirror for large N).
+    phia_opts o{};
+    if (opts) o = *opts;
     int max_abs = 0;
-    constexpr int kTile = 64;
-    for (int i = 0; i < N; ++i)
-        if (J_k[(size_t)i * N + i] != 0) return fail(PHIA_EINVAL, "nonzero diagonal J_k[%d][%d]", i, i);
-    for (int bi = 0; bi < N; bi += kTile) {
-        const int ie = std::min(N, bi + kTile);
-        for (int bj = bi; bj < N; bj += kTile) {
-            const int je = std::min(N, bj + kTile);
-            for (int i = bi; i < ie; ++i) {
-                const int8_t *row = J_k + (size_t)i * N;
-                for (int j = std::max(bj, i + 1); j < je; ++j) {
-                    const int a = row[j], b = J_k[(size_t)j * N + i];
-                    if (a != b) return fail(PHIA_EINVAL, "J_k is not symmetric at (%d, %d)", i, j);
-                    max_abs = std::max(max_abs, std::abs(a));
+    if (dev) {
+        rc = check_dense_on_device(J_k, h_k, N, o, &max_abs);
+        if (rc) return rc;
+    } else {
+        // Symmetry, zero diagonal and max |k| over the upper triangle, in 64 x 64 tiles so
+        // that a tile and its mirror both stay in cache (a row-by-column walk misses on
+        // every element of the mirror for large N).
+        constexpr int kTile = 64;
+        for (int i = 0; i < N; ++i)
+            if (J_k[(size_t)i * N + i] != 0) return fail(PHIA_EINVAL, "nonzero diagonal J_k[%d][%d]", i, i);
+        for (int bi = 0; bi < N; bi += kTile) {
+            const int ie = std::min(N, bi + kTile);
+            for (int bj = bi; bj < N; bj += kTile) {
+                const int je = std::min(N, bj + kTile);
+                for (int i = bi; i < ie; ++i) {
+                    const int8_t *row = J_k + (size_t)i * N;
+                    for (int j = std::max(bj, i + 1); j < je; ++j) {
+                        const int a = row[j], b = J_k[(size_t)j * N + i];
+                        if (a != b) return fail(PHIA_EINVAL, "J_k is not symmetric at (%d, %d)", i, j);
+                        max_abs = std::max(max_abs, std::abs(a));
+                    }
                 }
             }
         }
     }
-    phia_opts o{};
-    if (opts) o = *opts;
     if (o.tile_replicas != 0 && o.tile_replicas != 4 && o.tile_replicas != 8 && o.tile_replicas != 16)
         return fail(PHIA_EINVAL, "tile_replicas must be 0, 4, 8 or 16");
     if (o.coupling_mem < 0 || o.coupling_mem > 2) return fail(PHIA_EINVAL, "coupling_mem must be 0, 1 or 2");
@@ -388,7 +477,8 @@ int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, 
     const size_t NN = (size_t)N * N;
     auto cleanup = [&](int code) { phia_destroy(p); return code; };
     if (cudaMalloc((void **)&p->d_Jk, NN) != cudaSuccess) return cleanup(fail(PHIA_ENOMEM, "J allocation failed"));
-    if (cudaMemcpyAsync(p->d_Jk, J_k, NN, cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
+    if (cudaMemcpyAsync(p->d_Jk, J_k, NN, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream) !=
+        cudaSuccess)
         return cleanup(fail(PHIA_ECUDA, "J upload failed"));
     if (p->large) {
         p->Mpad = round_up(N, 128);
@@ -399,18 +489,37 @@ int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, 
             return cleanup(fail(PHIA_ECUDA, "J operand conversion failed"));
     }
     if (path == PHIA_PATH_FP32) {
-        std::vector<float> jf(NN);
         const float q = ldexpf(1.0f, -frac_bits);
-        for (size_t e = 0; e < NN; ++e) jf[e] = (float)J_k[e] * q;
         if (cudaMalloc((void **)&p->d_Jf, NN * 4) != cudaSuccess)
             return cleanup(fail(PHIA_ENOMEM, "J allocation failed"));
-        if (cudaMemcpy(p->d_Jf, jf.data(), NN * 4, cudaMemcpyHostToDevice) != cudaSuccess)
-            return cleanup(fail(PHIA_ECUDA, "J upload failed"));
+        if (dev) {
+            k_to_f32_kernel<<<1024, 256, 0, p->stream>>>(p->d_Jk, p->d_Jf, (int64_t)NN, q);
+            if (cudaGetLastError() != cudaSuccess) return cleanup(fail(PHIA_ECUDA, "J conversion failed"));
+        } else {
+            std::vector<float> jf(NN);
+            for (size_t e = 0; e < NN; ++e) jf[e] = (float)J_k[e] * q;
+            if (cudaMemcpy(p->d_Jf, jf.data(), NN * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                return cleanup(fail(PHIA_ECUDA, "J upload failed"));
+        }
     }
-    rc = finish_create(p, h_k, &o);
+    rc = finish_create(p, h_k, &o, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
     if (rc) return cleanup(rc);
     *out = p;
     return PHIA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int phia_create(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, int32_t frac_bits,
+                const phia_opts *opts) {
+    return create_dense(out, J_k, h_k, N, frac_bits, opts, false);
+}
+
+int phia_create_from_device(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N, int32_t frac_bits,
+                            const phia_opts *opts) {
+    return create_dense(out, J_k, h_k, N, frac_bits, opts, true);
 }
 
 int phia_create_csr(phia_t **out, const int32_t *row_ptr, const int32_t *col, const int8_t *val_k,

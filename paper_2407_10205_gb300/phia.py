@@ -90,6 +90,7 @@ class TuneResult(ctypes.Structure):
 _P = ctypes.c_void_p
 SIGNATURES = {
     "phia_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
+    "phia_create_from_device": (ctypes.c_int, [ctypes.POINTER(_P), _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "phia_create_csr": (ctypes.c_int, [ctypes.POINTER(_P), _P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "phia_anneal": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64]),
     "phia_best": (ctypes.c_int, [_P, _P, _P]),
@@ -194,6 +195,23 @@ def create(J_k, h_k, frac_bits=0, o: Opts | None = None):
     h = ctypes.c_void_p()
     _check(load().phia_create(ctypes.byref(h), _np_ptr(J_k), _np_ptr(h_k), n, int(frac_bits),
                               ctypes.byref(o) if o is not None else None))
+    return h
+
+
+def create_from_device(J_k, h_k, frac_bits=0, o: Opts | None = None):
+    """J_k: contiguous int8 [N, N] and h_k: contiguous int32 [N] device tensors (anything
+    with data_ptr(), shape, dtype and is_contiguous())."""
+    n = int(h_k.shape[0])
+    if tuple(J_k.shape) != (n, n):
+        raise ValueError("J_k must be N x N")
+    if str(J_k.dtype) != "torch.int8" or str(h_k.dtype) != "torch.int32":
+        raise TypeError("J_k must be int8 and h_k int32")
+    if not (J_k.is_contiguous() and h_k.is_contiguous()):
+        raise ValueError("J_k and h_k must be contiguous")
+    h = ctypes.c_void_p()
+    _check(load().phia_create_from_device(ctypes.byref(h), ctypes.c_void_p(J_k.data_ptr()),
+                                          ctypes.c_void_p(h_k.data_ptr()), n, int(frac_bits),
+                                          ctypes.byref(o) if o is not None else None))
     return h
 
 
@@ -307,6 +325,9 @@ class Annealer:
             row_ptr, col, val = csr
             self.n = len(row_ptr) - 1
             self.h = create_csr(row_ptr, col, val, h_k, frac_bits, o)
+        elif hasattr(J_k, "data_ptr") and getattr(J_k, "is_cuda", False):
+            self.n = int(h_k.shape[0])
+            self.h = create_from_device(J_k, h_k, frac_bits, o)   # device tensors: no host copy
         else:
             self.n = int(np.asarray(h_k).shape[0])
             self.h = create(J_k, h_k, frac_bits, o)
