@@ -141,12 +141,49 @@ struct phia_s {
 
 namespace {
 
+// A handle's device buffers come from one stream-ordered memory pool per device that
+// keeps freed blocks (release threshold at its maximum).  Creating and destroying handles
+// in a loop, as a caller with a new instance per request does, then costs neither
+// cudaMalloc round trips nor the device-wide synchronisation of cudaFree; the pool keeps
+// its peak size reserved for the process.
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
+cudaError_t pool_alloc(void **ptr, size_t bytes, int device, cudaStream_t st) {
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        auto it = g_pools.find(device);
+        if (it == g_pools.end()) {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof props);
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = device;
+            cudaError_t e = cudaMemPoolCreate(&pool, &props);
+            if (e != cudaSuccess) return e;
+            uint64_t keep = UINT64_MAX;
+            e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) return e;
+            g_pools[device] = pool;
+        } else {
+            pool = it->second;
+        }
+    }
+    return cudaMallocFromPoolAsync(ptr, std::max<size_t>(bytes, 16), pool, st);
+}
+
+void pool_free(void *ptr, cudaStream_t st) {
+    if (ptr) cudaFreeAsync(ptr, st);
+}
+
 void free_replicas(phia_t *p) {
-    cudaFree(p->d_S); cudaFree(p->d_Epart); cudaFree(p->d_flags); cudaFree(p->d_X); cudaFree(p->d_V);
+    for (void *b : {(void *)p->d_S, (void *)p->d_Epart, (void *)p->d_flags, (void *)p->d_X, (void *)p->d_V,
+                    (void *)p->d_x, (void *)p->d_v, (void *)p->d_s0, (void *)p->d_s1, (void *)p->d_eacc,
+                    (void *)p->d_best_e, (void *)p->d_best_step, (void *)p->d_hit, (void *)p->d_bits,
+                    (void *)p->d_hit_ns})
+        pool_free(b, p->stream);
     p->d_S = nullptr; p->d_Epart = nullptr; p->d_flags = nullptr; p->d_X = p->d_V = nullptr;
-    cudaFree(p->d_x); cudaFree(p->d_v); cudaFree(p->d_s0); cudaFree(p->d_s1); cudaFree(p->d_eacc);
-    cudaFree(p->d_best_e); cudaFree(p->d_best_step); cudaFree(p->d_hit); cudaFree(p->d_bits);
-    cudaFree(p->d_hit_ns);
     p->d_x = p->d_v = nullptr; p->d_s0 = p->d_s1 = nullptr; p->d_eacc = nullptr;
     p->d_best_e = p->d_best_step = p->d_hit = nullptr; p->d_bits = nullptr; p->d_hit_ns = nullptr;
     p->R_cap = 0;
@@ -159,7 +196,7 @@ int ensure_replicas(phia_t *p, int R) {
     const size_t RN = (size_t)R * p->N;
     bool ok = true;
     auto al = [&](void **ptr, size_t bytes) {
-        if (ok && cudaMalloc(ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) ok = false;
+        if (ok && pool_alloc(ptr, bytes, p->device, p->stream) != cudaSuccess) ok = false;
     };
     if (p->path == PHIA_PATH_FP32) {
         al((void **)&p->d_x, RN * 4); al((void **)&p->d_v, RN * 4);
@@ -255,7 +292,7 @@ int ensure_operand(phia_t *p) {
     if (p->d_Jop) return PHIA_OK;
     p->Mpad = round_up(p->N, 128);
     p->Kbytes = large_kbytes(p->N, p->op);
-    if (cudaMalloc(&p->d_Jop, (size_t)p->Mpad * p->Kbytes) != cudaSuccess)
+    if (pool_alloc(&p->d_Jop, (size_t)p->Mpad * p->Kbytes, p->device, p->stream) != cudaSuccess)
         return fail(PHIA_ENOMEM, "J operand allocation failed");
     CU(launch_convert_operand(p->d_Jk, p->N, p->d_Jop, p->Mpad, p->Kbytes, p->op, p->stream));
     return PHIA_OK;
@@ -317,15 +354,15 @@ int common_create(phia_t **out, int32_t N, int32_t frac_bits, const phia_opts *o
 
 int finish_create(phia_t *p, const int32_t *h_k, const phia_opts *opts,
                   cudaMemcpyKind h_kind = cudaMemcpyHostToDevice) {
-    CU(cudaMalloc((void **)&p->d_hk, (size_t)p->N * 4));
+    CU(pool_alloc((void **)&p->d_hk, (size_t)p->N * 4, p->device, p->stream));
     CU(cudaMemcpyAsync(p->d_hk, h_k, (size_t)p->N * 4, h_kind, p->stream));
-    CU(cudaMalloc((void **)&p->d_min_hit, 8));
-    CU(cudaMalloc((void **)&p->d_start_ns, 8));
+    CU(pool_alloc((void **)&p->d_min_hit, 8, p->device, p->stream));
+    CU(pool_alloc((void **)&p->d_start_ns, 8, p->device, p->stream));
     CU(cudaMemsetAsync(p->d_start_ns, 0, 8, p->stream));
-    CU(cudaMalloc((void **)&p->d_iters, 8));
-    CU(cudaMalloc((void **)&p->d_err, 4));
+    CU(pool_alloc((void **)&p->d_iters, 8, p->device, p->stream));
+    CU(pool_alloc((void **)&p->d_err, 4, p->device, p->stream));
     CU(cudaMemsetAsync(p->d_err, 0, 4, p->stream));
-    CU(cudaMalloc((void **)&p->d_ctl, sizeof(IterCtl)));
+    CU(pool_alloc((void **)&p->d_ctl, sizeof(IterCtl), p->device, p->stream));
     p->graphs = step_graphs_new();
     CU(cudaEventCreate(&p->ev0));
     CU(cudaEventCreate(&p->ev1));
@@ -476,21 +513,22 @@ int create_dense(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N,
     }
     const size_t NN = (size_t)N * N;
     auto cleanup = [&](int code) { phia_destroy(p); return code; };
-    if (cudaMalloc((void **)&p->d_Jk, NN) != cudaSuccess) return cleanup(fail(PHIA_ENOMEM, "J allocation failed"));
+    if (pool_alloc((void **)&p->d_Jk, NN, p->device, p->stream) != cudaSuccess)
+        return cleanup(fail(PHIA_ENOMEM, "J allocation failed"));
     if (cudaMemcpyAsync(p->d_Jk, J_k, NN, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream) !=
         cudaSuccess)
         return cleanup(fail(PHIA_ECUDA, "J upload failed"));
     if (p->large) {
         p->Mpad = round_up(N, 128);
         p->Kbytes = large_kbytes(N, p->op);
-        if (cudaMalloc(&p->d_Jop, (size_t)p->Mpad * p->Kbytes) != cudaSuccess)
+        if (pool_alloc(&p->d_Jop, (size_t)p->Mpad * p->Kbytes, p->device, p->stream) != cudaSuccess)
             return cleanup(fail(PHIA_ENOMEM, "J operand allocation failed"));
         if (launch_convert_operand(p->d_Jk, N, p->d_Jop, p->Mpad, p->Kbytes, p->op, p->stream) != cudaSuccess)
             return cleanup(fail(PHIA_ECUDA, "J operand conversion failed"));
     }
     if (path == PHIA_PATH_FP32) {
         const float q = ldexpf(1.0f, -frac_bits);
-        if (cudaMalloc((void **)&p->d_Jf, NN * 4) != cudaSuccess)
+        if (pool_alloc((void **)&p->d_Jf, NN * 4, p->device, p->stream) != cudaSuccess)
             return cleanup(fail(PHIA_ENOMEM, "J allocation failed"));
         if (dev) {
             k_to_f32_kernel<<<1024, 256, 0, p->stream>>>(p->d_Jk, p->d_Jf, (int64_t)NN, q);
@@ -498,7 +536,9 @@ int create_dense(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N,
         } else {
             std::vector<float> jf(NN);
             for (size_t e = 0; e < NN; ++e) jf[e] = (float)J_k[e] * q;
-            if (cudaMemcpy(p->d_Jf, jf.data(), NN * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            // on the handle's stream, after the pool allocation; a copy from pageable memory
+            // returns once jf has been staged
+            if (cudaMemcpyAsync(p->d_Jf, jf.data(), NN * 4, cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
                 return cleanup(fail(PHIA_ECUDA, "J upload failed"));
         }
     }
@@ -824,9 +864,10 @@ void phia_destroy(phia_t *p) {
     cudaSetDevice(p->device);
     cudaStreamSynchronize(p->stream);
     free_replicas(p);
-    cudaFree(p->d_Jk); cudaFree(p->d_Jf); cudaFree(p->d_hk); cudaFree(p->d_Jop);
+    for (void *b : {(void *)p->d_Jk, (void *)p->d_Jf, (void *)p->d_hk, (void *)p->d_Jop, (void *)p->d_min_hit,
+                    (void *)p->d_iters, (void *)p->d_err, (void *)p->d_ctl, (void *)p->d_start_ns})
+        pool_free(b, p->stream);
     cudaFree(p->d_rowptr); cudaFree(p->d_col); cudaFree(p->d_val);
-    cudaFree(p->d_min_hit); cudaFree(p->d_iters); cudaFree(p->d_err); cudaFree(p->d_ctl); cudaFree(p->d_start_ns);
     step_graphs_free(p->graphs);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
