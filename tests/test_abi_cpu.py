@@ -65,6 +65,35 @@ def test_invalid_instances_rejected(lib):
     assert "e4m3" in phia.last_error()
 
 
+def _batch_rc(lib, insts):
+    import ctypes
+    descs = (phia.InstanceDesc * len(insts))()
+    keep = []
+    for k, c in enumerate(insts):
+        arrs = [np.ascontiguousarray(c.row_ptr, np.int32), np.ascontiguousarray(c.col, np.int32),
+                np.ascontiguousarray(c.val, np.int8), np.ascontiguousarray(c.kh, np.int32)]
+        keep.append(arrs)
+        descs[k] = phia.InstanceDesc(c.n, c.frac_bits, None, *(a.ctypes.data for a in arrs), k, 0, 0)
+    out = ctypes.c_void_p()
+    return lib.phia_batch_create(ctypes.byref(out), len(insts), descs, None)
+
+
+def test_batch_reports_first_invalid_instance(lib):
+    """Batch instances are checked in parallel on the host (before any device call); the
+    lowest-numbered failing instance is the one reported, whatever the thread order."""
+    insts = [ins.erdos_renyi(60 + 7 * k, 0.1, 127, 31, 4, seed=k) for k in range(24)]
+    for bad in (17, 5, 21):              # asymmetric value in three instances
+        c = insts[bad]
+        c.val[0] = np.int8(c.val[0] + 1 if c.val[0] < 100 else c.val[0] - 1)
+    for _ in range(5):
+        assert _batch_rc(lib, insts) == phia.EINVAL
+        assert phia.last_error().startswith("instance 5: CSR is not symmetric")
+    c = insts[2]
+    c.kh[3] = 1 << 24                    # now instance 2 fails first, with ERANGE
+    assert _batch_rc(lib, insts) == phia.ERANGE
+    assert phia.last_error().startswith("instance 2:")
+
+
 def test_zero_spins_rejected(lib):
     import ctypes
     out = ctypes.c_void_p()
