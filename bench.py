@@ -13,11 +13,15 @@ iterations / time.
                (host -> device copy of J, h) + phia_anneal + phia_best (device -> host
                copy of the result) per step, wall clock.
   roofline     dominant kernel, see the roofline block below.
-  cpu_baseline the FP64 oracle on the host cores, bounded sample (rank 0, N = 1 only).
+  cpu_baseline the FP64 oracle on the host cores over the whole default workload (rank 0,
+               N = 1 only).
   comparator   the plain FP32 per-instance GPU path on the same instance and seeds.
+  clocks       SM clock and throttle reasons sampled by NVML every 5 ms inside the timed
+               region (a child process started before the warm-up).
 
 L2 is flushed (256 MB write) between timed steps.  `--impl reference` times the oracle
-(this method has no reference code; the oracle is the reference arm).
+(this method has no reference code; the oracle is the reference arm), 256 replicas x
+2000 iterations per step.
 """
 from __future__ import annotations
 
