@@ -30,7 +30,10 @@
  *    "device" pointers are CUDA global memory on the handle's device, owned by
  *    the caller, and must stay valid until the work enqueued on the handle's
  *    stream has finished (phia_sync).
- *  - A handle owns all device memory it allocates; phia_destroy frees it.
+ *  - A handle owns all device memory it allocates; phia_destroy frees it.  A
+ *    dense handle's buffers come from a stream-ordered memory pool per device that
+ *    the library keeps for the process: freed blocks serve later handles without
+ *    new allocations, so the process keeps its peak handle memory reserved.
  *    Handles are not thread-safe: one thread at a time per handle.
  *  - Work is enqueued on the stream given in phia_opts (NULL = the CUDA legacy
  *    default stream).  Calls that return results to host memory synchronise
