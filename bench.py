@@ -539,6 +539,16 @@ def run_serving(args, w):
     return 0
 
 
+def tts99(t1, p):
+    """Eq. 9 at 99% confidence, its brackets read as grouping: T1 log(0.01) / log(1 - P),
+    T1 itself once P >= 0.99, infinite when P = 0."""
+    if p <= 0.0:
+        return math.inf
+    if p >= 0.99:
+        return t1
+    return t1 * math.log(1.0 - 0.99) / math.log(1.0 - p)
+
+
 def run_tts(args, w):
     """Time to solution (Eq. 9, 99% confidence) of PHIA alone against n on SK instances.
     Per instance: the reference energy is the best found by a long run (ref_replicas x
@@ -565,12 +575,7 @@ def run_tts(args, w):
                 be, _, _, _ = phia.replica_results(A.h, w["replicas"], n)
             p = float(np.mean(be <= ref))
             t1 = st.device_ms * 1e-3 / w["replicas"]
-            if p <= 0.0:
-                tts = math.inf
-            elif p >= 0.99:
-                tts = t1
-            else:
-                tts = t1 * math.log(1.0 - 0.99) / math.log(1.0 - p)
+            tts = tts99(t1, p)
             ps.append(p); ttss.append(tts); t1s.append(t1)
         med = float(np.median(ttss))
         rows.append({"n": n, "iterations": T, "instances": w["instances"], "p_median": float(np.median(ps)),

@@ -1,6 +1,12 @@
 """Host logic of bench.py: the clock sampler's filtering to the timed region and decoding
-of NVML clock-event reasons, and the CPU baseline's JSON fields."""
+of NVML clock-event reasons, the CPU baseline's JSON fields, and the TTS formula (Eq. 9)
+against the oracle's."""
+import math
+
+import pytest
+
 import bench
+import oracle as o
 
 
 def test_clock_sampler_keeps_only_samples_inside_the_region():
@@ -41,3 +47,10 @@ def test_cpu_baseline_fields():
     r = bench.cpu_baseline(sample_replicas=4)
     assert r["kind"] == "oracle" and r["unit"] == bench.METRIC and r["cores"] >= 1
     assert r["value"] > 0 and "4 of the 1024 replicas" in r["sample"]
+
+
+@pytest.mark.parametrize("t1,p", [(2.0, 0.9), (1.0, 0.5), (3e-6, 0.074), (1.0, 0.99), (1.0, 1.0), (1.0, 0.0),
+                                  (1.0, 1e-4)])
+def test_tts99_matches_the_oracle(t1, p):
+    a, b = bench.tts99(t1, p), o.tts(t1, p)
+    assert (math.isinf(a) and math.isinf(b)) or a == pytest.approx(b, rel=1e-12)
