@@ -40,18 +40,24 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # configs[1] of the benchmark plan: the default bench workload
+    # the default workload: N = 200 dense, k and kh in [-7, 7], 1024 replicas x 2000 iterations
     "dense200": dict(N=200, kind="int", kmax=7, hmax=7, seed=1, replicas=1024, iterations=2000,
                      beta0=0.01, beta1=0.1, eps=0.1, gamma=2.0, refresh=50, run_seed=12345,
                      name="N=200 dense, k and kh uniform int [-7,7]; 1024 replicas x 2000 iterations, "
                           "linear beta 0.01->0.1",
                      cmp_iters=2000, cpu_replicas=1024, cpu_iters=2000),
-    # configs[2]: complete graph N=2000, J in {-1,+1}, h = 0
+    # plain PHIA: N = 16 SK instance (seed 0), one replica x 1000 iterations; a latency case
+    # (one CTA), reported as time per iteration
+    "sk16": dict(N=16, kind="pm1", seed=0, replicas=1, iterations=1000,
+                 beta0=0.05, beta1=2.0, eps=0.2, gamma=2.0, refresh=0, run_seed=1,
+                 name="N=16 SK instance (J uniform {-1,+1}, h=0, seed 0); 1 replica x 1000 iterations",
+                 cmp_iters=1000, cpu_replicas=1, cpu_iters=1000),
+    # complete graph N = 2000, J in {-1,+1}, h = 0, 4096 replicas x 5000 iterations
     "dense2000": dict(N=2000, kind="pm1", seed=3, replicas=4096, iterations=5000,
                       beta0=0.005, beta1=0.134, eps=0.1, gamma=2.0, refresh=50, run_seed=777,
                       name="N=2000 complete graph, J uniform {-1,+1}, h=0; 4096 replicas x 5000 iterations",
                       cmp_iters=20, cpu_replicas=64, cpu_iters=20),
-    # configs[3]: 256 Erdos-Renyi instances of uneven N, fixed point (f = 4), one batch
+    # 256 Erdos-Renyi instances of uneven N, fixed point (f = 4), one batch
     "batched_er": dict(kind="batch", count=256, seed=4, replicas=256, iterations=2000,
                        beta0=0.01, beta1=0.18, eps=0.1, gamma=2.0, refresh=50, run_seed=4242,
                        name="256 Erdos-Renyi instances, N ~ U[100,3000], density ~ U[0.006,0.06], J = k/16 "
@@ -64,7 +70,7 @@ WORKLOADS = {
                 name="TTS99 scaling: SK instances (J in {-1,+1}, h = 0), n = 8..1024, 20 instances per n; "
                      "256 replicas x 1000 max(1, n/128) iterations against the best of 1024 replicas x 20 times "
                      "as many"),
-    # configs[4]: serving stream, Poisson arrivals at 200/s over a pool of seeded instances
+    # serving stream, Poisson arrivals at 200/s over a pool of seeded instances
     "serving": dict(kind="serving", pool=32, pool_seed=5, requests=400, arrival_seed=11, rate_hz=200.0,
                     replicas=256, step_cap=5000, max_inflight=64, budget_gb=64, chunk_iters=200,
                     cmp_requests=60, cmp_wall_s=90.0,
@@ -274,7 +280,8 @@ def cpu_baseline(w=None, sample_replicas=None):
                   w["gamma"], refresh=w["refresh"], threads=cores, want_spins=False)
     dt = time.perf_counter() - t0
     su = R * w["N"] * T
-    return {"value": su / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+    # the oracle runs one thread per replica at a time: the threads it actually used
+    return {"value": su / dt, "unit": METRIC, "cores": min(cores, R), "kind": "oracle",
             "sample": f"{R} of the {w['replicas']} replicas x {T} of {w['iterations']} iterations ({dt:.1f} s)"}
 
 
@@ -721,6 +728,7 @@ def run_ours(args):
                        "timed_iterations": Tc, "scaled": Tc != T,
                        "best_energy_k_of_timed_iterations": int(cmp_best)},
         "best_energy_k": int(best_e),
+        "us_per_iteration": ms_per_step * 1e3 / T,
         "wall_s_timed": t_wall,
     }
     if world == 1 and not args.no_cpu_baseline:

@@ -195,6 +195,29 @@ def test_run_invariants_small_sk(gpu_lib, path):
     assert res.stats.spin_updates == R * 16 * 1000
 
 
+@pytest.mark.parametrize("kern", ["resident", "per_iteration", "fp32"])
+def test_config1_single_replica_reaches_ground_state(gpu_lib, kern):
+    """The plain-PHIA case exactly: N = 16 SK, seed 0, one replica, 1000 iterations, FP32 on
+    the GPU and FP64 in the oracle with the same seeds; both reach the exhaustive minimum
+    (2^16 states) and the GPU's returned energy is Eq. 2 on its returned spins."""
+    phia = gpu_lib
+    d = ins.sk_pm1(16, 0)
+    P = _oinst(d)
+    emin, _, _ = o.brute_force(P)
+    if kern == "fp32":
+        h = phia.Annealer(d.k, d.kh, path=phia.PATH_FP32)
+    else:
+        h = phia.Annealer(d.k, d.kh, path=phia.PATH_TC,
+                          tc_kernel=phia.KERNEL_RESIDENT if kern == "resident" else phia.KERNEL_PER_STEP)
+    with h as A:
+        for seed in (1, 2, 3):
+            ref = o.anneal(P, 1, 1000, seed, 0, 0.05, 2.0, 0.2, 2.0)
+            res = A.anneal(phia.schedule(0.05, 2.0, 0.2, 2.0), 1, 1000, seed=seed)
+            assert ref["best_e"][0] == emin == res.energy_k
+            assert o.energy_exact(P, res.spins) == res.energy_k
+            assert res.stats.spin_updates == 16 * 1000
+
+
 def test_short_trajectories_follow_the_oracle(gpu_lib):
     """From identical initial states, 12 iterations on the GPU (FP32) and in the oracle
     (FP64) give the same per-replica best energies for nearly every replica; the few
