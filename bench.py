@@ -1,10 +1,11 @@
 """Benchmark of the PHIA hot path on GB300.
 
 Workload (one bench step = one whole PHIA run, i.e. every row of the hot path over one
-batch): N = 200 dense instance, k_ij and kh_i uniform integers in [-7, 7] (seed 1),
-1024 replicas x 2000 iterations, beta linear 0.01 -> 0.1, eps 0.1, gamma 2, momentum
-refreshed every 50 iterations.  Metric: spin updates per second = replicas * N *
-iterations / time.
+batch): the N = 2000 complete graph, J_ij uniform in {-1,+1}, h = 0 (seed 3), 4096
+replicas x 5000 iterations, beta linear 0.005 -> 0.134, eps 0.1, gamma 2, momentum
+refreshed every 50 iterations, run on the per-iteration tcgen05 kernel (the autotuner's
+only candidate at this N).  Metric: spin updates per second = replicas * N * iterations
+/ time.
 
   value        device time of phia_anneal with the instance resident in HBM (CUDA events
                on the handle's stream), whole job over all ranks (weak scaling: every
@@ -12,16 +13,23 @@ iterations / time.
   e2e          same metric through the public C ABI from host buffers: phia_create
                (host -> device copy of J, h) + phia_anneal + phia_best (device -> host
                copy of the result) per step, wall clock.
-  roofline     dominant kernel, see the roofline block below.
-  cpu_baseline the FP64 oracle on the host cores over the whole default workload (rank 0,
-               N = 1 only).
+  roofline     dominant kernel: the dense field (Eq. 6) is 2 N flops per spin update;
+               achieved = 2 R N^2 per launch / the kernel's mean launch time, against the
+               e4m3 tensor peak (the measured bf16 peak x 2, the nominal e4m3 : bf16 ratio);
+               the HBM fraction of the algorithmic bytes beside it, and the e4m3 / bf16
+               rates this library's own tcgen05 probe (phia_mma_peak) measures on the box.
+  cpu_baseline the FP64 oracle on the host cores over a bounded sample of the workload
+               (rank 0, N = 1 only), extrapolated per spin update.
   comparator   the plain FP32 per-instance GPU path on the same instance and seeds.
   clocks       SM clock and throttle reasons sampled by NVML every 5 ms inside the timed
                region (a child process started before the warm-up).
+  also         (N = 1 only) the other workloads measured the same way, shorter: N = 200
+               dense (1024 x 2000, resident kernel), the 256-instance Erdos-Renyi batch,
+               and the serving stream (p50 / p99 time to target).
 
 L2 is flushed (256 MB write) between timed steps.  `--impl reference` times the oracle
-(this method has no reference code; the oracle is the reference arm), 256 replicas x
-2000 iterations per step.
+(this method has no reference code; the oracle is the reference arm) on a bounded
+sample of the workload per step.
 """
 from __future__ import annotations
 
@@ -40,7 +48,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # the default workload: N = 200 dense, k and kh in [-7, 7], 1024 replicas x 2000 iterations
+    # N = 200 dense, k and kh in [-7, 7], 1024 replicas x 2000 iterations
     "dense200": dict(N=200, kind="int", kmax=7, hmax=7, seed=1, replicas=1024, iterations=2000,
                      beta0=0.01, beta1=0.1, eps=0.1, gamma=2.0, refresh=50, run_seed=12345,
                      name="N=200 dense, k and kh uniform int [-7,7]; 1024 replicas x 2000 iterations, "
@@ -52,11 +60,12 @@ WORKLOADS = {
                  beta0=0.05, beta1=2.0, eps=0.2, gamma=2.0, refresh=0, run_seed=1,
                  name="N=16 SK instance (J uniform {-1,+1}, h=0, seed 0); 1 replica x 1000 iterations",
                  cmp_iters=1000, cpu_replicas=1, cpu_iters=1000),
-    # complete graph N = 2000, J in {-1,+1}, h = 0, 4096 replicas x 5000 iterations
+    # the default workload: complete graph N = 2000, J in {-1,+1}, h = 0, 4096 replicas x
+    # 5000 iterations
     "dense2000": dict(N=2000, kind="pm1", seed=3, replicas=4096, iterations=5000,
                       beta0=0.005, beta1=0.134, eps=0.1, gamma=2.0, refresh=50, run_seed=777,
                       name="N=2000 complete graph, J uniform {-1,+1}, h=0; 4096 replicas x 5000 iterations",
-                      cmp_iters=20, cpu_replicas=64, cpu_iters=20),
+                      cmp_iters=20, cpu_replicas=256, cpu_iters=50),
     # 256 Erdos-Renyi instances of uneven N, fixed point (f = 4), one batch
     "batched_er": dict(kind="batch", count=256, seed=4, replicas=256, iterations=2000,
                        beta0=0.01, beta1=0.18, eps=0.1, gamma=2.0, refresh=50, run_seed=4242,
@@ -77,14 +86,9 @@ WORKLOADS = {
                     name="serving: Poisson 200/s, N log-uniform [64,8192], half dense {-1,+1}, half sparse "
                          "f=8 density 0.01; 256 replicas, step cap 5000, target = oracle best (4 x 200)"),
 }
-WORKLOAD = WORKLOADS["dense200"]
+WORKLOAD = WORKLOADS["dense2000"]
 WORKLOAD_NAME = WORKLOAD["name"]
 METRIC = "spin-updates/s"
-# FP32 operations the update of one spin needs by its formulas (Eqs. 5-8, A7, Eq. 2 via the
-# field): position FMA, sign, field conversion, energy term and accumulate (2), gamma*x,
-# sech^2 via one exp (exp, add, square, divide, scale: 5), beta*gamma*q*sech^2*I (2), -x,
-# *eps, +v.
-ALGO_OPS_PER_UPDATE = 16
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each kernel, from the
 # committed ncu summaries under profiles/; absent once a kernel changed after its capture.
 KERNEL_TRAFFIC_BYTES = {
@@ -267,7 +271,8 @@ class ClockSampler:
 
 def cpu_baseline(w=None, sample_replicas=None):
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of the workload
-    (`sample_replicas` replicas x the workload's sample iterations)."""
+    (`sample_replicas` replicas x the workload's sample iterations), its rate extrapolated
+    per spin update to the whole workload."""
     import oracle
     w = w or WORKLOAD
     R = sample_replicas or w["cpu_replicas"]
@@ -280,32 +285,34 @@ def cpu_baseline(w=None, sample_replicas=None):
                   w["gamma"], refresh=w["refresh"], threads=cores, want_spins=False)
     dt = time.perf_counter() - t0
     su = R * w["N"] * T
+    whole = R == w["replicas"] and T == w["iterations"]
     # the oracle runs one thread per replica at a time: the threads it actually used
     return {"value": su / dt, "unit": METRIC, "cores": min(cores, R), "kind": "oracle",
-            "sample": f"{R} of the {w['replicas']} replicas x {T} of {w['iterations']} iterations ({dt:.1f} s)"}
-
-
-# oracle replicas per step of the reference arm (about 0.6 s on 16 cores)
-REF_REPLICAS_PER_STEP = 256
+            "sample": f"{R} of the {w['replicas']} replicas x {T} of {w['iterations']} iterations ({dt:.1f} s)"
+                      + ("" if whole else ", extrapolated per spin update"),
+            "seconds": dt}
 
 
 def run_reference(args):
+    """The reference arm: the oracle (this paper has no reference code) on the machine's host
+    cores, each step the workload's bounded CPU sample."""
     rank, world, _ = _dist()
     if rank != 0:
         return 0
-    per_step = []
+    per_step, secs = [], []
     cb = None
     for k in range(args.warmup + args.steps):
-        r = cpu_baseline(sample_replicas=REF_REPLICAS_PER_STEP)
+        r = cpu_baseline()
         if k >= args.warmup:
             per_step.append(r["value"])
+            secs.append(r["seconds"])
             cb = r
     val = statistics.median(per_step)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": METRIC, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": REF_REPLICAS_PER_STEP * WORKLOAD["N"] * WORKLOAD["iterations"] / val * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(secs) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "sample_replicas_per_step": REF_REPLICAS_PER_STEP},
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "sample_per_step": cb["sample"].split(" (")[0]},
             "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": val,
                              "unit": METRIC},
             "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -322,45 +329,61 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def _roofline(w, kernel_ms, stats, peaks, src, clocks):
-    """Roofline of the dominant kernel of the workload (see the design doc for the derivations)."""
+def mma_probe(phia):
+    """Dense tcgen05 rates measured on this GPU by the library's own probe (phia_mma_peak):
+    M = 128, N = 256 MMAs from shared memory on every SM, e4m3 and bf16."""
+    out = {}
+    for name, op in (("e4m3", phia.OP_E4M3), ("bf16", phia.OP_BF16)):
+        try:
+            ms, tf = phia.mma_peak(op, 256, 20000)
+            out[name + "_tflops"] = tf
+        except Exception as e:                      # noqa: BLE001 -- reported, not fatal
+            out[name + "_error"] = str(e)
+    return out
+
+
+def _roofline(w, kernel_ms, stats, peaks, src, probe=None):
+    """Roofline of the dominant kernel of a dense workload.  The field (Eq. 6) is a dense
+    contraction of 2 N flops per spin update (2 R N^2 per iteration): achieved = those
+    flops / device time, against the e4m3 tensor peak taken as the measured bf16 burst
+    peak x 2 (the nominal e4m3 : bf16 ratio; the operand here is e4m3 when every |k| <= 16,
+    else bf16 at the measured bf16 peak).  Beside it: the same flops against the rates the
+    library's own tcgen05 probe measured, and for the per-iteration kernel the fraction of
+    HBM bandwidth its algorithmic bytes reach (x and v in and out, 16 B per spin update;
+    the next spins, 1 B; the spins read once, 1 B; J once, N^2 B)."""
     N, R, T = w["N"], w["replicas"], w["iterations"]
     su = R * N * T
-    tensor_peak = 2.0 * float(peaks["bf16_tflops"])
-    tensor_achieved = 2.0 * N * su / (kernel_ms * 1e-3) / 1e12
-    tensor = {"achieved": tensor_achieved, "peak": tensor_peak, "unit": "TFLOP/s",
-              "frac": tensor_achieved / tensor_peak, "peak_source": f"{src} bf16 x 2 (nominal e4m3 : bf16 ratio)"}
-    if stats.tc_kernel in (1, 3, 4):
-        # Resident kernels: one launch per run.  In the tensor-core ones the 2N field flops
-        # per spin update take a few hundred tensor cycles per iteration; the incremental
-        # one gathers only the columns of the spins that changed sign.  The time goes to
-        # the per-spin FP32 update and the per-iteration dependency chain, so the bound
-        # quoted is the FP32 lane-op rate.
-        kname = {1: "tc_small_kernel", 3: "imma_small_kernel", 4: "inc_small_kernel"}[stats.tc_kernel]
-        if stats.tc_kernel == 4:
-            tensor = None
-        sm_mhz = clocks.get("sm_max_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
-        alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e9
-        achieved = ALGO_OPS_PER_UPDATE * su / (kernel_ms * 1e-3) / 1e9
-        return {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
-                "frac": achieved / alu_peak, "traffic": KERNEL_TRAFFIC_BYTES.get(kname),
-                "kernel": kname,
-                "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (derived)", "tensor": tensor}
-    # Per-iteration kernel: per launch it must move x and v in and out (16 B per spin
-    # update), write the next spins (1 B per spin update) and read the spins and J once.
-    launch_ms = kernel_ms / T
-    bytes_per_launch = R * N * 17 + R * N + N * N
-    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
-    peak = float(peaks["hbm_gbs"])
-    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": KERNEL_TRAFFIC_BYTES.get("tc_large_step"), "kernel": "tc_large_step",
-            "launch_ms": launch_ms, "algorithmic_bytes_per_launch": bytes_per_launch,
-            "peak_source": f"{src} HBM copy bandwidth", "tensor": tensor}
+    e4m3 = stats.operand == 1
+    bf16_peak = float(peaks["bf16_tflops"])
+    peak = 2.0 * bf16_peak if e4m3 else bf16_peak
+    achieved = 2.0 * N * su / (kernel_ms * 1e-3) / 1e12
+    kname = {1: "tc_small_kernel", 2: "tc_large_step", 3: "imma_small_kernel",
+             4: "inc_small_kernel"}.get(stats.tc_kernel, "?")
+    out = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": KERNEL_TRAFFIC_BYTES.get(kname), "kernel": kname,
+           "flops_per_spin_update": 2 * N,
+           "peak_source": (f"{src} bf16 {bf16_peak:g} TFLOP/s x 2 (nominal e4m3 : bf16 ratio)" if e4m3
+                           else f"{src} bf16 {bf16_peak:g} TFLOP/s")}
+    if probe:
+        mp = probe.get("e4m3_tflops" if e4m3 else "bf16_tflops")
+        if mp:
+            out["probe_peak"] = mp
+            out["frac_of_probe_peak"] = achieved / mp
+    if stats.tc_kernel == 2:
+        launch_ms = kernel_ms / T
+        bytes_per_launch = R * N * 17 + R * N + N * N
+        hbm = bytes_per_launch / (launch_ms * 1e-3) / 1e9
+        out["launch_ms"] = launch_ms
+        out["hbm"] = {"achieved": hbm, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                      "frac": hbm / float(peaks["hbm_gbs"]), "algorithmic_bytes_per_launch": bytes_per_launch,
+                      "peak_source": f"{src} HBM copy bandwidth"}
+    return out
 
 
-def run_batch(args, w):
-    """Config 4: one phia_batch over all instances; the comparator is the plain FP32
-    per-instance dense path, timed on a sample of instances and scaled by N^2."""
+def measure_batch(args, w, light=False):
+    """The batched workload: one phia_batch over all instances; the comparator is the
+    plain FP32 per-instance dense path, timed on a sample of instances and scaled by N^2.
+    light: no CPU baseline."""
     import torch
     import oracle
     from paper_2407_10205_gb300 import instances as ins
@@ -424,7 +447,7 @@ def run_batch(args, w):
     cores = os.cpu_count() or 1
     tc0 = time.perf_counter()
     su_cpu = 0
-    for k in range(w["cpu_instances"]):
+    for k in range(0 if light else w["cpu_instances"]):
         c = insts[k]
         P = oracle.Instance(c.kh, row_ptr=c.row_ptr, col=c.col, val=c.val, frac_bits=c.frac_bits)
         oracle.anneal(P, R, w["cpu_iters"], w["run_seed"], k, w["beta0"], w["beta1"], w["eps"], w["gamma"],
@@ -454,12 +477,12 @@ def run_batch(args, w):
                        "unit": METRIC, "ms_per_run": cmp_ms,
                        "scaled": f"{w['cmp_instances']} instances x {w['cmp_iters']} iterations, time per N^2"},
         "best_energy_k_instance0": int(best0),
-        "cpu_baseline": {"value": su_cpu / dt_cpu, "unit": METRIC, "cores": cores, "kind": "oracle",
-                         "sample": f"{w['cpu_instances']} instances x {R} replicas x {w['cpu_iters']} iterations "
-                                   f"({dt_cpu:.1f} s)"},
     }
-    print(json.dumps(line))
-    return 0
+    if not light:
+        line["cpu_baseline"] = {"value": su_cpu / dt_cpu, "unit": METRIC, "cores": cores, "kind": "oracle",
+                                "sample": f"{w['cpu_instances']} instances x {R} replicas x {w['cpu_iters']} "
+                                          f"iterations ({dt_cpu:.1f} s), extrapolated per spin update"}
+    return line
 
 
 def _serve_stream(phia, pool, targets, arrivals, w, path, wall_cap_s=None):
@@ -497,8 +520,8 @@ def _serve_stream(phia, pool, targets, arrivals, w, path, wall_cap_s=None):
     return sts, st, complete
 
 
-def run_serving(args, w):
-    """Config 5: a stream of requests through the continuous-batching server."""
+def measure_serving(args, w):
+    """The serving workload: a stream of requests through the continuous-batching server."""
     import torch
     from paper_2407_10205_gb300 import instances as ins
     from paper_2407_10205_gb300 import phia
@@ -542,8 +565,7 @@ def run_serving(args, w):
                 "note": "serving is end to end by construction: host instances in, results out"},
         "clocks": cs.summary(),
     }
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 def tts99(t1, p):
@@ -599,28 +621,12 @@ def run_tts(args, w):
     return 0
 
 
-def run_ours(args):
+def measure_dense(args, w, rank=0, world=1, local=0, with_cpu=True, dist=None):
+    """One dense workload on the tensor-core path: the autotuned kernel timed over
+    args.steps whole runs (after args.warmup), e2e through the C ABI, the FP32 comparator
+    and (optionally) the oracle's CPU baseline.  Returns the JSON line's fields."""
     import torch
-    import torch.distributed as dist
-
-    rank, world, local = _dist()
-    if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
     from paper_2407_10205_gb300 import phia
-    phia.load()
-    w = WORKLOADS[args.workload]
-    if w["kind"] == "batch":
-        return run_batch(args, w)
-    if w["kind"] == "tts":
-        return run_tts(args, w)
-    if w["kind"] == "serving":
-        w = dict(w)
-        if args.max_inflight:
-            w["max_inflight"] = args.max_inflight
-        if args.chunk_iters:
-            w["chunk_iters"] = args.chunk_iters
-        return run_serving(args, w)
     d = _instance(w)
     N, R, T = w["N"], w["replicas"], w["iterations"]
     sched = phia.schedule(w["beta0"], w["beta1"], w["eps"], w["gamma"], refresh=w["refresh"])
@@ -641,7 +647,6 @@ def run_ours(args):
             phia.anneal(A.h, sched, R, T, seed)
             phia.sync(A.h)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        launches = 0
         barrier()
         with cs:
             t_wall = time.perf_counter()
@@ -684,14 +689,13 @@ def run_ours(args):
     # are timed on their first cmp_iters iterations and scaled (labelled).
     Tc = min(T, w["cmp_iters"])
     with phia.Annealer(d.k, d.kh, path=phia.PATH_FP32, stream=stream.cuda_stream) as C:
-        sched_c = sched
-        phia.anneal(C.h, sched_c, R, Tc, seed)
+        phia.anneal(C.h, sched, R, Tc, seed)
         phia.sync(C.h)
         cmp_ms = []
         for _ in range(2):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            phia.anneal(C.h, sched_c, R, Tc, seed)
+            phia.anneal(C.h, sched, R, Tc, seed)
             e1.record(stream)
             stream.synchronize()
             cmp_ms.append(e0.elapsed_time(e1))
@@ -699,10 +703,8 @@ def run_ours(args):
     cmp_run_ms = min(cmp_ms) * T / Tc
     cmp_value = su_step / (cmp_run_ms * 1e-3)
 
-    if rank != 0:
-        return 0
     peaks, src = _peaks()
-    clocks = cs.summary()
+    probe = mma_probe(phia) if with_cpu else None
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -720,9 +722,9 @@ def run_ours(args):
                    "parallelism": f"replicas sharded over {world} GPU(s), no collective"},
         "e2e": {"value": su_step / (e2e_step * 1e-3), "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
-        "roofline": _roofline(w, kernel_ms, st, peaks, src, clocks),
+        "roofline": _roofline(w, kernel_ms, st, peaks, src, probe),
         "gpu_launches": launches,
-        "clocks": clocks,
+        "clocks": cs.summary(),
         "comparator": {"path": "fp32 per-instance, one launch per step", "value": cmp_value, "unit": METRIC,
                        "ms_per_run": cmp_run_ms,
                        "timed_iterations": Tc, "scaled": Tc != T,
@@ -731,8 +733,57 @@ def run_ours(args):
         "us_per_iteration": ms_per_step * 1e3 / T,
         "wall_s_timed": t_wall,
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if probe:
+        line["tensor_probe"] = probe
+    if with_cpu and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
+    return line
+
+
+def _summary(line, keys=("value", "unit", "ms_per_step", "roofline", "e2e", "comparator", "clocks",
+                         "gpu_launches", "serving", "config")):
+    return {k: line[k] for k in keys if k in line}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2407_10205_gb300 import phia
+    phia.load()
+    w = WORKLOADS[args.workload]
+    if w["kind"] == "batch":
+        print(json.dumps(measure_batch(args, w)))
+        return 0
+    if w["kind"] == "tts":
+        return run_tts(args, w)
+    if w["kind"] == "serving":
+        w = dict(w)
+        if args.max_inflight:
+            w["max_inflight"] = args.max_inflight
+        if args.chunk_iters:
+            w["chunk_iters"] = args.chunk_iters
+        print(json.dumps(measure_serving(args, w)))
+        return 0
+    line = measure_dense(args, w, rank, world, local, dist=dist)
+    if rank != 0:
+        return 0
+    if world == 1 and not args.no_extras and args.workload == "dense2000":
+        # the other workloads of the benchmark set, one line each under "also"
+        also = {}
+        for name in ("dense200",):
+            also[name] = _summary(measure_dense(args, WORKLOADS[name], with_cpu=False))
+        also["batched_er"] = _summary(measure_batch(args, WORKLOADS["batched_er"], light=True))
+        sv = dict(WORKLOADS["serving"])
+        sv["requests"] = 200
+        a2 = argparse.Namespace(**vars(args))
+        a2.no_comparator = True
+        also["serving"] = _summary(measure_serving(a2, sv))
+        line["also"] = also
     print(json.dumps(line))
     return 0
 
@@ -753,6 +804,8 @@ def main():
     ap.add_argument("--max-inflight", type=int, default=0, help="serving: request slots (0 = the workload's)")
     ap.add_argument("--chunk-iters", type=int, default=0, help="serving: iterations per chunk (0 = the workload's)")
     ap.add_argument("--no-comparator", action="store_true", help="serving: skip the FP32 comparator runs")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the other workloads reported under 'also'")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warmup + steps anneals of the tensor-core path and nothing else (for ncu)")
     args = ap.parse_args()

@@ -239,25 +239,33 @@ int phia_philox_draws(uint64_t seed, uint32_t instance_id, uint32_t d, int32_t r
  * and cudaFree are forbidden because they can synchronise the device and take unbounded
  * time.  Such callers own every input and output buffer, and this call takes its
  * scratch (the operand copy of J, the spin buffers, the energy sums, a working copy of
- * x and v) from one array of 64 MiB compiled into the library, which every GPU that
- * loads the library holds until the process exits.
+ * x and v, its counters) from one array of 64 MiB compiled into the library.
+ *
+ * When that array is reserved: with CUDA's lazy module loading (the default), a device
+ * reserves the array's 64 MiB when the library's code is first used on it -- in practice
+ * at the first call of this entry point on that device, which also looks up the array's
+ * device address (cudaGetSymbolAddress) -- and holds it until the process exits.  Make
+ * that first call at start-up, before the caller's own pool claims the device's memory,
+ * and before any stream capture.  Later calls reserve nothing more.
  *
  * It runs the tensor-core path with one launch per iteration, exactly as phia_run does
  * on a handle created with tc_kernel = 2, and gives the same results.  All pointers are
- * device memory on the current CUDA device except sched (host): J_k N*N int8 (symmetric,
- * zero diagonal -- not checked here), h_k N int32, x and v replicas*N float32 updated in
- * place, and the records best_energy_k, best_step, hit_step (replicas each) and
- * best_bits (replicas * ceil(N/32)), which reset_best = 1 initialises.  operand:
- * PHIA_OP_E4M3 (every |k| <= 16) or PHIA_OP_BF16 (AUTO means BF16).  stream: cudaStream_t
- * or NULL.  Sizes that need more scratch than the array holds (for example N = 2000 with
- * e4m3 and more than 2048 replicas) return PHIA_ERANGE.  The call allocates nothing:
- * no cudaMalloc, cudaFree or allocating library routine.  The first call on a device
- * looks up the array's device address once (cudaGetSymbolAddress), so make that first
- * call before any stream capture.  It returns after the work has finished (it
- * synchronises the stream), with PHIA_ETIMEOUT if a bounded device wait expired.  All
- * calls share the one array, whose contents the next call overwrites: calls that
- * overlap on the GPU (other threads, other streams) race and must be serialised by the
- * caller. */
+ * device memory on the current CUDA device except sched (host): J_k N*N int8, h_k N
+ * int32, x and v replicas*N float32 updated in place, and the records best_energy_k,
+ * best_step, hit_step (replicas each) and best_bits (replicas * ceil(N/32)), which
+ * reset_best = 1 initialises.  J_k and h_k are checked on the device as phia_create
+ * checks them: asymmetric J or a nonzero diagonal -> PHIA_EINVAL, |h_k| >= 2^24 ->
+ * PHIA_ERANGE.  operand: PHIA_OP_E4M3 (needs every |k| <= 16, else PHIA_ERANGE),
+ * PHIA_OP_BF16, or PHIA_OP_AUTO (e4m3 when every |k| <= 16, else bf16, as phia_create).
+ * stream: cudaStream_t or NULL.  Sizes that need more scratch than the array holds
+ * return PHIA_ERANGE with the largest replica count that fits for that N and operand
+ * (for example N = 2000 with e4m3 fits at most 2304 replicas).  The call allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library routine.  It synchronises the
+ * stream (once after the instance checks, once at the end) and returns after the work
+ * has finished, with PHIA_ETIMEOUT if a bounded device wait expired.  All calls share the
+ * one array, whose contents the next call overwrites (the call clears what must start at
+ * zero): calls that overlap on the GPU (other threads, other streams) race and must be
+ * serialised by the caller. */
 int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N, int32_t frac_bits, int32_t operand,
                      const phia_schedule *sched, int32_t replicas, int64_t t0, int64_t steps,
                      int64_t total_steps, uint64_t seed, uint32_t instance_id, float *x, float *v,
@@ -376,6 +384,33 @@ int phia_server_stats_get(phia_server_t *s, phia_server_stats *out);
 
 /* Stop the loop, free every request's device memory and the streams. */
 void phia_server_destroy(phia_server_t *s);
+
+/* Measurement aid (no counterpart in the paper): dense tensor-core throughput of the
+ * current device for the operand encodings of the field (Eq. 6), so that its roofline
+ * has a denominator measured for its own operand type.  One CTA per SM issues
+ * rounds x 4 tcgen05 MMAs of shape M = 128, N = n (16..256, a multiple of 16), K = one
+ * 128-byte swizzle row split in four (e4m3: K = 32 per MMA, kind::f8f6f4; bf16: K = 16,
+ * kind::f16) from shared memory into one FP32 tensor-memory accumulator.  operand:
+ * PHIA_OP_E4M3 or PHIA_OP_BF16.  stream: cudaStream_t or NULL.  Writes the device time
+ * of the timed launch (after one warm-up launch; CUDA events) to *ms and the achieved
+ * dense rate, 2 * 128 * n * K flops per MMA, to *tflops (host pointers, either may be
+ * NULL).  Allocates a 4-byte status word; synchronises the stream. */
+int phia_mma_peak(int32_t operand, int32_t n, int64_t rounds, void *stream, float *ms, double *tflops);
+
+/* Testing aid for the error path of bounded device waits (Sec. 2.2 gives the FPGA's
+ * fixed schedule and no error handling; this entry point has no counterpart in the
+ * paper).  Every device-side wait of the library's kernels gives up after a time bound,
+ * records the fact and lets the kernel return, so that a lost arrival cannot hang the
+ * GPU; later calls that return results then fail with PHIA_ETIMEOUT and the CUDA context
+ * stays usable.  wait_budget_ns sets that bound for the per-iteration tensor-core kernel
+ * of this handle (0 = the library default of 2 s).  stall_producer = 1, allowed only on a
+ * handle created with tc_kernel = 2, makes that kernel's TMA producer issue no copy at all:
+ * no tensor-core or copy operation is then ever in flight, every wait for a full operand
+ * stage or a finished accumulator runs out after the bound, and the run reports
+ * PHIA_ETIMEOUT.  stall_producer = 0 restores normal runs.  Settings stay on the handle
+ * until changed.  PHIA_EINVAL for a negative bound or a stall flag other than 0/1,
+ * PHIA_ENOTSUP for a stall on any other kernel. */
+int phia_debug_wait(phia_t *p, int64_t wait_budget_ns, int32_t stall_producer);
 
 /* Wait for all work enqueued on the handle's stream. */
 int phia_sync(phia_t *p);

@@ -52,30 +52,6 @@ __global__ void reset_records_kernel(int R, int W, int64_t *best_e, int64_t *bes
     if (idx == 0) *start_ns = phia::globaltimer_ns();   // the run's start on the device clock
 }
 
-// Instance checks of phia_create_from_device, on the device: res[0] = lowest linear index
-// i*N + j (i < j) with k_ij != k_ji, res[1] = lowest i with k_ii != 0, res[2] = lowest i
-// with |kh_i| >= 2^24 (ULLONG_MAX where none), res[3] = max |k_ij| over i < j.
-__global__ void check_dense_kernel(const int8_t *J, const int32_t *h, int N, unsigned long long *res) {
-    const int64_t total = (int64_t)N * N;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned int mx = 0;
-    for (int64_t e = first; e < total; e += stride) {
-        const int i = (int)(e / N), j = (int)(e - (int64_t)i * N);
-        const int k = J[e];
-        if (j > i) {
-            if (k != J[(int64_t)j * N + i]) atomicMin(&res[0], (unsigned long long)e);
-            mx = max(mx, (unsigned int)abs(k));
-        } else if (j == i && k != 0) {
-            atomicMin(&res[1], (unsigned long long)i);
-        }
-    }
-    mx = __reduce_max_sync(0xffffffffu, mx);
-    if ((threadIdx.x & 31) == 0 && mx) atomicMax(&res[3], (unsigned long long)mx);
-    for (int64_t i = first; i < N; i += stride)
-        if (h[i] >= (1 << 24) || h[i] <= -(1 << 24)) atomicMin(&res[2], (unsigned long long)i);
-}
-
 // J = k q in FP32 for the FP32 path, from the device copy of k.
 __global__ void k_to_f32_kernel(const int8_t *k, float *jf, int64_t n, float q) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
@@ -137,6 +113,8 @@ struct phia_s {
     int64_t last_steps = 0;
     int last_launches = 0;
     int last_stop = 0;
+    int64_t wait_ns = 0;                // testing aid (phia_debug_wait): device wait bound, 0 = default
+    int stall_producer = 0;             // testing aid: the per-iteration kernel's TMA producer issues nothing
 };
 
 namespace {
@@ -269,6 +247,8 @@ RunArgs base_args(phia_t *p, int R) {
     a.min_hit = p->d_min_hit; a.replica_iters = p->d_iters; a.err = p->d_err;
     a.tile_rl = p->tile_rl;
     a.coupling_mem = p->coupling_mem;
+    a.wait_ns = p->wait_ns;
+    a.stall_producer = p->stall_producer;
     return a;
 }
 
@@ -410,8 +390,7 @@ int check_dense_on_device(const int8_t *J_k, const int32_t *h_k, int N, const ph
     if (e == cudaSuccess) {
         const int64_t total = (int64_t)N * N;
         const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)sms * 8));
-        check_dense_kernel<<<blocks, 256, 0, st>>>(J_k, h_k, N, res);
-        e = cudaGetLastError();
+        e = launch_check_dense(J_k, h_k, N, res, blocks, st);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(got, res, sizeof got, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -747,6 +726,17 @@ int phia_philox_draws(uint64_t seed, uint32_t instance_id, uint32_t d, int32_t R
                       float *x, float *v, void *stream) {
     if (R < 0 || N < 0) return fail(PHIA_EINVAL, "negative size");
     CU(launch_philox_draws(seed, instance_id, d, R, N, raw, x, v, (cudaStream_t)stream));
+    return PHIA_OK;
+}
+
+int phia_debug_wait(phia_t *p, int64_t wait_budget_ns, int32_t stall_producer) {
+    if (!p) return fail(PHIA_EINVAL, "handle is NULL");
+    if (wait_budget_ns < 0 || stall_producer < 0 || stall_producer > 1)
+        return fail(PHIA_EINVAL, "need wait_budget_ns >= 0 and stall_producer 0 or 1");
+    if (stall_producer && !(p->path == PHIA_PATH_TC && p->large && !p->auto_tile))
+        return fail(PHIA_ENOTSUP, "the stall applies to a handle created with tc_kernel = 2 (per-iteration kernel)");
+    p->wait_ns = wait_budget_ns;
+    p->stall_producer = stall_producer;
     return PHIA_OK;
 }
 

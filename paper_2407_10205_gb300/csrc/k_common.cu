@@ -34,7 +34,37 @@ __global__ void convert_operand_kernel(const int8_t *Jk, int N, uint8_t *Jop, in
     else reinterpret_cast<uint16_t *>(Jop)[idx] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
+// Instance checks on the device: res[0] = lowest linear index i*N + j (i < j) with
+// k_ij != k_ji, res[1] = lowest i with k_ii != 0, res[2] = lowest i with |kh_i| >= 2^24
+// (each left untouched where there is none), res[3] = max |k_ij| over i < j (atomic max).
+__global__ void check_dense_kernel(const int8_t *J, const int32_t *h, int N, unsigned long long *res) {
+    const int64_t total = (int64_t)N * N;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned int mx = 0;
+    for (int64_t e = first; e < total; e += stride) {
+        const int i = (int)(e / N), j = (int)(e - (int64_t)i * N);
+        const int k = J[e];
+        if (j > i) {
+            if (k != J[(int64_t)j * N + i]) atomicMin(&res[0], (unsigned long long)e);
+            mx = max(mx, (unsigned int)abs(k));
+        } else if (j == i && k != 0) {
+            atomicMin(&res[1], (unsigned long long)i);
+        }
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(&res[3], (unsigned long long)mx);
+    for (int64_t i = first; i < N; i += stride)
+        if (h[i] >= (1 << 24) || h[i] <= -(1 << 24)) atomicMin(&res[2], (unsigned long long)i);
+}
+
 }  // namespace
+
+cudaError_t launch_check_dense(const int8_t *J, const int32_t *h, int N, unsigned long long *res, unsigned blocks,
+                               cudaStream_t st) {
+    check_dense_kernel<<<blocks, 256, 0, st>>>(J, h, N, res);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_convert_operand(const int8_t *Jk, int N, void *Jop, int Mpad, int Kbytes, int op, cudaStream_t st) {
     const int esz = op == kOpE4M3 ? 1 : 2;

@@ -1,0 +1,126 @@
+// k_peak.cu -- dense tensor-core throughput of this GPU, measured with the same tcgen05
+// MMA forms the field kernels use (kind::f8f6f4 with e4m3 operands, kind::f16 with bf16
+// operands; M = 128, K-major operands in 128-byte-swizzled shared memory, FP32
+// accumulation in tensor memory).  It gives the roofline of the dense field (Eq. 6) a
+// denominator measured for its own operand type rather than scaled from another.
+//
+// One CTA per SM; one thread issues `rounds` x 4 MMAs (the four 32-byte K steps of one
+// 128-byte swizzle row) of shape 128 x n into one accumulator, then commits and waits
+// (bounded).  The operand tiles hold +-1 encodings; their values do not affect timing.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+
+#include "../../include/phia.h"
+#include "device_common.cuh"
+#include "phia_internal.h"
+
+namespace phia {
+namespace {
+
+constexpr int kPeakThreads = 128;
+constexpr uint32_t kTileA = 128 * 128;   // 128 rows x 128 bytes
+constexpr uint32_t kMaxTileB = 256 * 128;
+
+template <int OP>
+__global__ void __launch_bounds__(kPeakThreads, 1) mma_peak_kernel(int n, int64_t rounds, int32_t *err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + kTileA;
+    __shared__ uint64_t done;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // +1 in the operand encoding (e4m3 0x38, bf16 0x3F80), alternating sign per word
+    const uint32_t w_pos = OP == kOpE4M3 ? 0x38383838u : 0x3F803F80u;
+    const uint32_t w_neg = OP == kOpE4M3 ? 0xB8B8B8B8u : 0xBF80BF80u;
+    uint32_t *w = reinterpret_cast<uint32_t *>(smem);
+    for (uint32_t i = tid; i < (kTileA + (uint32_t)n * 128) / 4; i += kPeakThreads) w[i] = (i & 1) ? w_neg : w_pos;
+    fence_proxy_async_smem();
+    if (warp == 0) {
+        tmem_alloc(&tmem_base, 256);
+        tmem_relinquish();
+    }
+    if (tid == 32) {
+        mbar_init(&done, 1);
+        fence_mbarrier_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    if (tid == 0) {
+        const uint32_t idesc = make_idesc(OP == kOpE4M3 ? 0u : 1u, 128, (uint32_t)n);
+        const uint64_t ad = smem_desc_sw128(smem_u32(sA));
+        const uint64_t bd = smem_desc_sw128(smem_u32(sB));
+        for (int64_t r = 0; r < rounds; ++r) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if constexpr (OP == kOpE4M3) mma_e4m3(tmem, ad + 2 * k, bd + 2 * k, idesc, (r | k) != 0);
+                else mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (r | k) != 0);
+            }
+        }
+        mma_commit(&done);
+        if (!mbar_wait_bounded(&done, 0, kWaitTimeoutNs)) atomicExch(err, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+}
+
+}  // namespace
+}  // namespace phia
+
+using namespace phia;
+
+extern "C" int phia_mma_peak(int32_t operand, int32_t n, int64_t rounds, void *stream, float *ms, double *tflops) {
+    if (operand != PHIA_OP_E4M3 && operand != PHIA_OP_BF16)
+        return set_last_error(PHIA_EINVAL, "phia_mma_peak: operand must be PHIA_OP_E4M3 or PHIA_OP_BF16");
+    if (n < 16 || n > 256 || n % 16 != 0 || rounds < 1)
+        return set_last_error(PHIA_EINVAL, "phia_mma_peak: need n in {16, 32, ..., 256} and rounds >= 1");
+    int dev = 0, sms = 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return set_last_error(PHIA_ECUDA, "phia_mma_peak: device query failed");
+    const size_t smem = 1024 + kTileA + kMaxTileB;
+    int32_t *err = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc((void **)&err, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    auto kern = operand == PHIA_OP_E4M3 ? mma_peak_kernel<kOpE4M3> : mma_peak_kernel<kOpBF16>;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    float t = 0.f;
+    int32_t herr = 0;
+    if (e == cudaSuccess) {
+        kern<<<sms, kPeakThreads, smem, st>>>(n, 1, err);   // warm-up (module load, clocks)
+        e = cudaEventRecord(e0, st);
+    }
+    if (e == cudaSuccess) {
+        kern<<<sms, kPeakThreads, smem, st>>>(n, rounds, err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof herr, cudaMemcpyDeviceToHost);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (err) cudaFree(err);
+    if (e != cudaSuccess) {
+        char msg[256];
+        snprintf(msg, sizeof msg, "phia_mma_peak: %s", cudaGetErrorString(e));
+        return set_last_error(PHIA_ECUDA, msg);
+    }
+    if (herr) return set_last_error(PHIA_ETIMEOUT, "phia_mma_peak: the completion wait expired");
+    const int kstep = operand == PHIA_OP_E4M3 ? 32 : 16;
+    const double flops = 2.0 * 128.0 * n * kstep * 4.0 * (double)rounds * sms;
+    if (ms) *ms = t;
+    if (tflops) *tflops = flops / (t * 1e-3) / 1e12;
+    return PHIA_OK;
+}

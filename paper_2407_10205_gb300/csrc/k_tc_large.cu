@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t t = L.ctl->t, t_first = L.ctl->t_first, t_end = L.ctl->t_end;
     const int KB = L.Kbytes / kBKB;
     const int N = a.N, R = a.R;
+    const uint64_t kWaitNs = a.wait_ns > 0 ? (uint64_t)a.wait_ns : kWaitTimeoutNs;
 
     if (warp == 0) {
         tmem_alloc(&sh->tmem_base, 2 * BN);
@@ -246,8 +247,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = sh->tmem_base;
 
     if (warp == 0) {
-        // TMA producer: the k-blocks of every tile of this CTA through one ring.
-        if (lane == 0) {
+        // TMA producer: the k-blocks of every tile of this CTA through one ring.  With
+        // stall_producer (a testing aid) it issues nothing, so every wait below on a full
+        // stage or a finished accumulator runs out after kWaitNs and the launch reports it.
+        if (lane == 0 && !a.stall_producer) {
             int64_t kg = 0;
             bool ok = true;
             for (int lt = 0; lt < my_tiles && ok; ++lt) {
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int kb = 0; kb < KB; ++kb, ++kg) {
                     const int s = (int)(kg % kStages);
                     if (kg >= kStages &&
-                        (*tout || !mbar_wait_bounded(&sh->empty[s], (uint32_t)((kg / kStages) - 1) & 1u, kWaitTimeoutNs))) {
+                        (*tout || !mbar_wait_bounded(&sh->empty[s], (uint32_t)((kg / kStages) - 1) & 1u, kWaitNs))) {
                         ok = false;
                         break;
                     }
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!ok) *tout = 1;
             // Copies still in flight (only after a timeout) land before the CTA exits.
             for (int64_t k = kg > kStages ? kg - kStages : 0; k < kg; ++k)
-                mbar_wait_bounded(&sh->full[k % kStages], (uint32_t)(k / kStages) & 1u, kWaitTimeoutNs);
+                mbar_wait_bounded(&sh->full[k % kStages], (uint32_t)(k / kStages) & 1u, kWaitNs);
         }
     } else if (warp == 1) {
         // MMA issuer: 4 K-steps of 32 bytes per stage, accumulators alternating per tile.
@@ -278,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (int lt = 0; lt < my_tiles && ok; ++lt) {
                 const int b = lt & 1;
-                if (lt >= 2 && (*tout || !mbar_wait_bounded(&sh->acce[b], (uint32_t)((lt >> 1) - 1) & 1u, kWaitTimeoutNs))) {
+                if (lt >= 2 && (*tout || !mbar_wait_bounded(&sh->acce[b], (uint32_t)((lt >> 1) - 1) & 1u, kWaitNs))) {
                     ok = false;
                     break;
                 }
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t dt = tmem + (uint32_t)(b * BN);
                 for (int kb = 0; kb < KB; ++kb, ++kg) {
                     const int s = (int)(kg % kStages);
-                    if (*tout || !mbar_wait_bounded(&sh->full[s], (uint32_t)(kg / kStages) & 1u, kWaitTimeoutNs)) {
+                    if (*tout || !mbar_wait_bounded(&sh->full[s], (uint32_t)(kg / kStages) & 1u, kWaitNs)) {
                         ok = false;
                         break;
                     }
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!ok) *tout = 1;
             // Every MMA issued has completed before the accumulators are released.
             mma_commit(&sh->drain);
-            mbar_wait_bounded(&sh->drain, 0, kWaitTimeoutNs);
+            mbar_wait_bounded(&sh->drain, 0, kWaitNs);
         }
     } else {
         // Epilogue warps: warp w reads TMEM lane quadrant w % 4 and column group (w - 2) / 4;
@@ -382,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint8_t *sb = Sn + (size_t)rc0 * L.Kbytes + (size_t)i * ESZ;
             // Warp-uniform, as the TMEM loads below are warp-collective.
             const bool ok = __all_sync(0xffffffffu, !*tout && mbar_wait_bounded(&sh->accf[b], (uint32_t)(lt >> 1) & 1u,
-                                                                               kWaitTimeoutNs));
+                                                                               kWaitNs));
             if (!ok) *tout = 1;
             tc_fence_after();
             const uint32_t tbase = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * BN + cg * kColsPerWarp);

@@ -1,6 +1,8 @@
 // noalloc.cu -- phia_run_noalloc: the per-iteration tensor-core path with every piece of
 // scratch memory taken from one fixed array compiled into the library, for callers that
 // cannot allocate device memory (see include/phia.h for who they are and the limits).
+#include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -60,6 +62,36 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 using namespace phia;
 
+namespace phia {
+namespace {
+
+// Scratch layout for N spins, `replicas` replicas and operand `op`: a 256-byte control
+// region (run counters at 0, the iteration control at 64, the instance-check results at
+// 128), then the operand J, 4 spin buffers, energy sums, flags, and the working x, v in
+// the per-iteration kernel's interleaved layout.
+struct NoallocLayout {
+    int Mpad, Kbytes, Rpad;
+    size_t off_jop, off_s, off_e, off_f, off_x, off_v, need;
+};
+
+NoallocLayout noalloc_layout(int N, int replicas, int op) {
+    NoallocLayout L;
+    L.Mpad = round_up(N, 128);
+    L.Kbytes = large_kbytes(N, op);
+    L.Rpad = large_rpad(replicas);
+    L.off_jop = 256;
+    L.off_s = L.off_jop + align256((size_t)L.Mpad * L.Kbytes);
+    L.off_e = L.off_s + align256((size_t)4 * L.Rpad * L.Kbytes);
+    L.off_f = L.off_e + align256((size_t)2 * L.Rpad * sizeof(int64_t));
+    L.off_x = L.off_f + align256((size_t)2 * L.Rpad);
+    L.off_v = L.off_x + align256((size_t)L.Rpad * L.Mpad * 4);
+    L.need = L.off_v + align256((size_t)L.Rpad * L.Mpad * 4);
+    return L;
+}
+
+}  // namespace
+}  // namespace phia
+
 extern "C" int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N, int32_t frac_bits,
                                 int32_t operand, const phia_schedule *sched, int32_t replicas, int64_t t0,
                                 int64_t steps, int64_t total_steps, uint64_t seed, uint32_t instance_id, float *x,
@@ -73,33 +105,27 @@ extern "C" int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N
     if (frac_bits < 0 || frac_bits > 30) return set_last_error(PHIA_EINVAL, "phia_run_noalloc: frac_bits not in [0, 30]");
     if (operand != PHIA_OP_E4M3 && operand != PHIA_OP_BF16 && operand != PHIA_OP_AUTO)
         return set_last_error(PHIA_EINVAL, "phia_run_noalloc: unknown operand");
-    if (!(sched->eps > 0.0f) || !(sched->gamma > 0.0f) || sched->refresh < 0 || (sched->deriv != 0 && sched->deriv != 1))
+    if (!(sched->eps > 0.0f) || !(sched->gamma > 0.0f) || !(sched->beta0 >= 0.0f) || !(sched->beta1 >= 0.0f) ||
+        sched->refresh < 0 || (sched->deriv != 0 && sched->deriv != 1))
         return set_last_error(PHIA_EINVAL, "phia_run_noalloc: invalid schedule");
-    const int op = operand == PHIA_OP_E4M3 ? kOpE4M3 : kOpBF16;   // AUTO: bf16, exact for every int8 k
-
-    // Scratch layout: operand J, 4 spin buffers, energy sums, flags, run counters, and the
-    // working x, v in the kernel's interleaved layout (the caller's x, v are read at the
-    // start and written at the end).
-    const int Mpad = round_up(N, 128), Kbytes = large_kbytes(N, op), Rpad = large_rpad(replicas);
-    const size_t off_jop = 0;
-    const size_t off_s = off_jop + align256((size_t)Mpad * Kbytes);
-    const size_t off_e = off_s + align256((size_t)4 * Rpad * Kbytes);
-    const size_t off_f = off_e + align256((size_t)2 * Rpad * sizeof(int64_t));
-    const size_t off_c = off_f + align256((size_t)2 * Rpad);
-    const size_t off_x = off_c + 256;
-    const size_t off_v = off_x + align256((size_t)Rpad * Mpad * 4);
-    const size_t need = off_v + align256((size_t)Rpad * Mpad * 4);
-    if (need > kScratchBytes) {
-        char msg[256];
+    // A size too large for the scratch whatever the operand is refused before any device work.
+    if (noalloc_layout(N, replicas, operand == PHIA_OP_BF16 ? kOpBF16 : kOpE4M3).need > kScratchBytes) {
+        char msg[320];
+        const int op = operand == PHIA_OP_BF16 ? kOpBF16 : kOpE4M3;
+        int rmax = 0;
+        while (noalloc_layout(N, rmax + 256, op).need <= kScratchBytes) rmax += 256;
         snprintf(msg, sizeof msg,
                  "phia_run_noalloc: N = %d and %d replicas need %zu bytes of scratch; the fixed scratch holds %zu "
-                 "(e.g. N <= 2000 with e4m3 and up to 2048 replicas)",
-                 N, replicas, need, kScratchBytes);
+                 "(with this N and the %s operand at most %d replicas fit)",
+                 N, replicas, noalloc_layout(N, replicas, op).need, kScratchBytes, op == kOpBF16 ? "bf16" : "e4m3",
+                 rmax);
         return set_last_error(PHIA_ERANGE, msg);
     }
 
-    int dev = 0;
+    int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return set_last_error(PHIA_ECUDA, "phia_run_noalloc: no current device");
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return set_last_error(PHIA_ECUDA, "phia_run_noalloc: device query failed");
     uint8_t *base = nullptr;
     int rc = scratch_address(dev, &base);
     if (rc) return rc;
@@ -109,11 +135,57 @@ extern "C" int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N
         snprintf(msg, sizeof msg, "phia_run_noalloc: %s", cudaGetErrorString(e));
         return set_last_error(PHIA_ECUDA, msg);
     };
-    // The array keeps the previous call's contents: clear what must start at zero (the
-    // spin buffers' padding, the energy sums, the flags and the counters).
-    cudaError_t e = cudaMemsetAsync(base + off_s, 0, off_x - off_s, st);
+
+    // The instance checks of phia_create, on the device, into the control region: symmetry,
+    // zero diagonal, |h_k| < 2^24 and max |k| (which decides whether e4m3 is exact).
+    unsigned long long *res = reinterpret_cast<unsigned long long *>(base + 128);
+    cudaError_t e = cudaMemsetAsync(res, 0xFF, 3 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(res + 3, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) {
+        const int64_t total = (int64_t)N * N;
+        const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)sms * 8));
+        e = launch_check_dense(J_k, h_k, N, res, blocks, st);
+    }
+    unsigned long long got[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(got, res, sizeof got, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e);
-    e = launch_convert_operand(J_k, N, base + off_jop, Mpad, Kbytes, op, st);
+    char msg[256];
+    if (got[2] != ULLONG_MAX) {
+        snprintf(msg, sizeof msg, "phia_run_noalloc: |h_k[%llu]| >= 2^24", got[2]);
+        return set_last_error(PHIA_ERANGE, msg);
+    }
+    if (got[1] != ULLONG_MAX) {
+        snprintf(msg, sizeof msg, "phia_run_noalloc: nonzero diagonal J_k[%llu][%llu]", got[1], got[1]);
+        return set_last_error(PHIA_EINVAL, msg);
+    }
+    if (got[0] != ULLONG_MAX) {
+        snprintf(msg, sizeof msg, "phia_run_noalloc: J_k is not symmetric at (%llu, %llu)",
+                 got[0] / (unsigned long long)N, got[0] % (unsigned long long)N);
+        return set_last_error(PHIA_EINVAL, msg);
+    }
+    const int max_abs = (int)got[3];
+    if (operand == PHIA_OP_E4M3 && max_abs > 16) {
+        snprintf(msg, sizeof msg, "phia_run_noalloc: max |k| = %d is not exact in e4m3 (needs <= 16)", max_abs);
+        return set_last_error(PHIA_ERANGE, msg);
+    }
+    // AUTO as in phia_create: e4m3 when every |k| <= 16, else bf16 (exact for every int8 k).
+    const int op = operand == PHIA_OP_BF16 || (operand == PHIA_OP_AUTO && max_abs > 16) ? kOpBF16 : kOpE4M3;
+    const NoallocLayout Ly = noalloc_layout(N, replicas, op);
+    if (Ly.need > kScratchBytes) {
+        int rmax = 0;
+        while (noalloc_layout(N, rmax + 256, op).need <= kScratchBytes) rmax += 256;
+        snprintf(msg, sizeof msg,
+                 "phia_run_noalloc: N = %d and %d replicas need %zu bytes of scratch with the bf16 operand; the "
+                 "fixed scratch holds %zu (at most %d replicas fit)", N, replicas, Ly.need, kScratchBytes, rmax);
+        return set_last_error(PHIA_ERANGE, msg);
+    }
+
+    // The array keeps the previous call's contents: clear what must start at zero (the run
+    // counters, the spin buffers' padding, the energy sums and the flags).
+    e = cudaMemsetAsync(base, 0, 64, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + Ly.off_s, 0, Ly.off_x - Ly.off_s, st);
+    if (e == cudaSuccess) e = launch_convert_operand(J_k, N, base + Ly.off_jop, Ly.Mpad, Ly.Kbytes, op, st);
     if (e != cudaSuccess) return cuda_fail(e);
     const int W = (N + 31) / 32;
     if (reset_best) {
@@ -123,7 +195,7 @@ extern "C" int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e);
     }
-    unsigned long long *counters = reinterpret_cast<unsigned long long *>(base + off_c);
+    unsigned long long *counters = reinterpret_cast<unsigned long long *>(base);
     RunArgs a;
     memset(&a, 0, sizeof a);
     a.N = N;
@@ -147,15 +219,15 @@ extern "C" int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N
     e = cudaMemsetAsync(counters, 0xFF, 8, st);
     if (e != cudaSuccess) return cuda_fail(e);
     LargeBuffers B;
-    B.Jop = base + off_jop;
-    B.S = base + off_s;
-    B.Epart = reinterpret_cast<int64_t *>(base + off_e);
-    B.flags = reinterpret_cast<int8_t *>(base + off_f);
-    B.ctl = reinterpret_cast<IterCtl *>(base + off_c + 64);
+    B.Jop = base + Ly.off_jop;
+    B.S = base + Ly.off_s;
+    B.Epart = reinterpret_cast<int64_t *>(base + Ly.off_e);
+    B.flags = reinterpret_cast<int8_t *>(base + Ly.off_f);
+    B.ctl = reinterpret_cast<IterCtl *>(base + 64);
     B.graphs = nullptr;   // a graph would be an allocation
-    B.X = reinterpret_cast<float *>(base + off_x);
-    B.V = reinterpret_cast<float *>(base + off_v);
-    B.Kbytes = Kbytes; B.Mpad = Mpad; B.Rpad = Rpad;
+    B.X = reinterpret_cast<float *>(base + Ly.off_x);
+    B.V = reinterpret_cast<float *>(base + Ly.off_v);
+    B.Kbytes = Ly.Kbytes; B.Mpad = Ly.Mpad; B.Rpad = Ly.Rpad;
     int launches = 0;
     e = launch_tc_large(B, a, op, st, &launches);
     if (e != cudaSuccess) return cuda_fail(e);

@@ -43,6 +43,9 @@ struct RunArgs {
     int32_t *err;                        // nonzero: a bounded device wait expired
     int32_t tile_rl;                     // tensor-core small path: live replicas per CTA (0 = auto)
     int32_t coupling_mem;                // tensor-core small path: 1 = J in shared, 2 = in tensor memory
+    int64_t wait_ns;                     // per-iteration kernel: bound of each device wait (0 = kWaitTimeoutNs)
+    int32_t stall_producer;              // per-iteration kernel, testing: the TMA producer issues nothing
+    int32_t pad0;
 };
 
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;  // 2 s bound on every device-side wait
@@ -111,6 +114,11 @@ struct LargeBuffers {
 };
 cudaError_t launch_tc_large(const LargeBuffers &B, const RunArgs &a, int op, cudaStream_t st, int *launches);
 cudaError_t launch_convert_operand(const int8_t *Jk, int N, void *Jop, int Mpad, int Kbytes, int op, cudaStream_t st);
+// Device checks of a dense instance into res[4] (initialised by the caller to
+// {ULLONG_MAX, ULLONG_MAX, ULLONG_MAX, 0}): res[0] lowest i*N+j with k_ij != k_ji (i < j),
+// res[1] lowest i with k_ii != 0, res[2] lowest i with |kh_i| >= 2^24, res[3] max |k_ij|.
+cudaError_t launch_check_dense(const int8_t *J, const int32_t *h, int N, unsigned long long *res, unsigned blocks,
+                               cudaStream_t st);
 inline int large_kbytes(int N, int op) { return ((N * (op == kOpE4M3 ? 1 : 2)) + 127) / 128 * 128; }
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 // Replica padding of the per-iteration dense path (its widest tile is 256 replicas).

@@ -119,6 +119,8 @@ SIGNATURES = {
     "phia_server_wait_all": (ctypes.c_int, [_P, ctypes.c_int64]),
     "phia_server_stats_get": (ctypes.c_int, [_P, _P]),
     "phia_server_destroy": (None, [_P]),
+    "phia_debug_wait": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32]),
+    "phia_mma_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P, _P]),
     "phia_sync": (ctypes.c_int, [_P]),
     "phia_destroy": (None, [_P]),
     "phia_last_error": (ctypes.c_char_p, []),
@@ -296,6 +298,18 @@ def run_noalloc(J_k, h_k, frac_bits, operand, sched: Schedule, replicas, t0, ste
                                    int(instance_id) & 0xFFFFFFFF, _dev_ptr(x), _dev_ptr(v), _dev_ptr(best_energy_k),
                                    _dev_ptr(best_step), _dev_ptr(hit_step), _dev_ptr(best_bits),
                                    1 if reset_best else 0, ctypes.c_void_p(int(stream) if stream else None)))
+
+
+def mma_peak(operand, n=256, rounds=20000, stream=None):
+    """(device ms, TFLOP/s) of the tcgen05 throughput probe (phia_mma_peak)."""
+    ms, tf = ctypes.c_float(), ctypes.c_double()
+    _check(load().phia_mma_peak(int(operand), int(n), int(rounds), ctypes.c_void_p(int(stream) if stream else None),
+                                ctypes.byref(ms), ctypes.byref(tf)))
+    return float(ms.value), float(tf.value)
+
+
+def debug_wait(h, wait_budget_ns, stall_producer=False):
+    _check(load().phia_debug_wait(h, int(wait_budget_ns), 1 if stall_producer else 0))
 
 
 def sync(h):

@@ -44,9 +44,18 @@ def test_clock_sampler_without_samples():
 
 
 def test_cpu_baseline_fields():
-    r = bench.cpu_baseline(sample_replicas=4)
+    r = bench.cpu_baseline(bench.WORKLOADS["dense200"], sample_replicas=4)
     assert r["kind"] == "oracle" and r["unit"] == bench.METRIC and r["cores"] >= 1
-    assert r["value"] > 0 and "4 of the 1024 replicas" in r["sample"]
+    assert r["value"] > 0 and "4 of the 1024 replicas" in r["sample"] and "extrapolated" in r["sample"]
+    w = dict(bench.WORKLOADS["sk16"])
+    r = bench.cpu_baseline(w)      # the whole workload: nothing extrapolated
+    assert "1 of the 1 replicas x 1000 of 1000" in r["sample"] and "extrapolated" not in r["sample"]
+
+
+def test_default_workload_is_the_largest_single_gpu_configuration():
+    w = bench.WORKLOAD
+    assert (w["N"], w["replicas"], w["iterations"]) == (2000, 4096, 5000)
+    assert w["cpu_replicas"] * w["cpu_iters"] < w["replicas"] * w["iterations"]
 
 
 @pytest.mark.parametrize("t1,p", [(2.0, 0.9), (1.0, 0.5), (3e-6, 0.074), (1.0, 0.99), (1.0, 1.0), (1.0, 0.0),
