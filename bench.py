@@ -796,7 +796,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dense200", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="dense2000", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile-replicas", type=int, default=0, help="tensor-core replicas per CTA (0 = auto)")
     ap.add_argument("--coupling-mem", type=int, default=0, help="tensor-core: 1 = J in shared, 2 = in tensor memory")

@@ -106,6 +106,23 @@ typedef struct phia_schedule {
                               chosen here (value 1 at 0 and integral 2, as the exact factor);
                               anything else is PHIA_EINVAL */
     int64_t target_k;      /* target energy in units of q */
+    int32_t accept_test;   /* Table 3 state 4: 0 = every trajectory kept (App. A: exact HMC
+                              accepts with probability 1); 1 = Metropolis test on the
+                              Hamiltonian H = beta E(sgn x) + x.x/2 + v.v/2 (Eq. 4, Eq. A6)
+                              at each trajectory end: just before the momentum draw of
+                              iteration t (t % refresh == 0, t > 0), the trajectory
+                              [t - refresh, t) is accepted when u <= exp(-(H_end - H_start)),
+                              both H under beta_{t-1}, u the uniform of Philox counter
+                              (0xFFFFFFFF, replica, t, instance id) word 0; a rejected end
+                              point puts x back to the trajectory's start (the states it
+                              visited still count for the best state).  A call's first
+                              trajectory starts from a state whose energy no iteration of the
+                              call evaluated and is kept untested; the last has no test (no
+                              draw follows it).  Needs refresh > 0 to have any effect.
+                              Resident tcgen05 kernel (tc_kernel 1, J in shared memory) and
+                              the FP32 path only; elsewhere PHIA_ENOTSUP.  Counts:
+                              phia_acceptance. */
+    int32_t reserved;      /* must be 0 */
 } phia_schedule;
 
 typedef struct phia_stats {
@@ -203,6 +220,12 @@ int phia_stats_get(phia_t *p, phia_stats *out);
  * uint32 words, bit (i % 32) of word (i / 32) set when s_i = +1. */
 int phia_replica_results(phia_t *p, int32_t replicas, int64_t *best_energy_k,
                          int64_t *best_step, int64_t *hit_step, uint32_t *best_bits);
+
+/* Acceptance counts of the last run with accept_test = 1 (Table 3, state 4: the
+ * acceptance rate is accepted / proposed), host arrays of `replicas` entries (either may
+ * be NULL): trajectories put to the test and accepted, per replica.  Zero after a run
+ * without the test.  Synchronises the stream. */
+int phia_acceptance(phia_t *p, int32_t replicas, int64_t *proposed, int64_t *accepted);
 
 /* Resumable form of phia_anneal.  Runs iterations t0 .. t0+steps-1 of a run of
  * total_steps iterations (beta_t and the refresh draws depend on the absolute t)

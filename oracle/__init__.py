@@ -63,12 +63,13 @@ class _Sched(ctypes.Structure):
                 ("eps", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("refresh", ctypes.c_int64),
                 ("has_target", ctypes.c_int32), ("stop_at_target", ctypes.c_int32),
-                ("target", ctypes.c_int64), ("deriv", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("target", ctypes.c_int64), ("deriv", ctypes.c_int32), ("accept_test", ctypes.c_int32)]
 
 
 class _RepOut(ctypes.Structure):
     _fields_ = [("best_e", ctypes.c_int64), ("best_step", ctypes.c_int64),
-                ("hit_step", ctypes.c_int64), ("steps_run", ctypes.c_int64)]
+                ("hit_step", ctypes.c_int64), ("steps_run", ctypes.c_int64),
+                ("proposed", ctypes.c_int64), ("accepted", ctypes.c_int64)]
 
 
 def _load():
@@ -103,6 +104,13 @@ def _load():
             lib.orc_step_mode.restype = ctypes.c_int64
             lib.orc_dfactor.argtypes = [ctypes.c_double, ctypes.c_int32]
             lib.orc_dfactor.restype = ctypes.c_double
+            lib.orc_hamiltonian.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_int]
+            lib.orc_hamiltonian.restype = ctypes.c_double
+            lib.orc_metropolis.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            lib.orc_metropolis.restype = ctypes.c_int
+            lib.orc_accept_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
+            lib.orc_accept_uniform.restype = ctypes.c_double
             lib.orc_beta_at.argtypes = [P(_Sched), ctypes.c_int64, ctypes.c_int64]
             lib.orc_beta_at.restype = ctypes.c_double
             lib.orc_anneal_replica.argtypes = [P(_Inst), ctypes.c_int32, P(_Sched), ctypes.c_int64,
@@ -147,10 +155,10 @@ class Instance:
         return math.ldexp(1.0, -self.frac_bits)
 
 
-def _sched(beta0, beta1, eps, gamma, refresh=0, target=None, stop_at_target=False, deriv=0):
+def _sched(beta0, beta1, eps, gamma, refresh=0, target=None, stop_at_target=False, deriv=0, accept_test=0):
     return _Sched(float(beta0), float(beta1), float(eps), float(gamma), int(refresh),
                   0 if target is None else 1, 1 if stop_at_target else 0,
-                  0 if target is None else int(target), int(deriv), 0)
+                  0 if target is None else int(target), int(deriv), int(accept_test))
 
 
 # ----------------------------------------------------------------- wrappers
@@ -244,6 +252,24 @@ def step(P: Instance, x, v, beta, eps, gamma, deriv=0):
     return x, v, s, I, int(e)
 
 
+def hamiltonian(beta, q, e, x, v):
+    """Eq. 4 / Eq. A6: beta q e + x.x/2 + v.v/2 (e = E(sgn x) in units of q)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return float(_load().orc_hamiltonian(float(beta), float(q), int(e), _ptr(x), _ptr(v), int(x.shape[0])))
+
+
+def metropolis(h_start, h_end, u) -> bool:
+    """Table 3 state 4 as a Metropolis test: accept when u <= exp(-(h_end - h_start))."""
+    return bool(_load().orc_metropolis(float(h_start), float(h_end), float(u)))
+
+
+def accept_uniform(seed, inst, r, t) -> float:
+    """The test's uniform before the momentum draw d = t: Philox (0xFFFFFFFF, r, t, inst)
+    word 0 on the 24-bit grid of (0, 1]."""
+    return float(_load().orc_accept_uniform(seed & (2**64 - 1), inst, r, t))
+
+
 def dfactor(y, deriv=0):
     """The derivative factor of Eq. 8 at y = gamma x: 1 - tanh^2(y), or (deriv = 1) the
     quadratic stand-in max(0, 1 - (y / 1.5)^2) (coefficients chosen here: the paper
@@ -256,10 +282,11 @@ def beta_at(t, T, beta0, beta1):
 
 
 def anneal_replica(P: Instance, T, seed, inst_id, r, beta0, beta1, eps, gamma, refresh=0,
-                   target=None, stop_at_target=False, x0=None, v0=None, trace=False, deriv=0):
+                   target=None, stop_at_target=False, x0=None, v0=None, trace=False, deriv=0, accept_test=0):
     """One replica of a PHIA run in FP64.  Returns a dict with best_e, best_step,
-    hit_step, steps_run, best_s, x, v and (optionally) the per-iteration energies."""
-    S = _sched(beta0, beta1, eps, gamma, refresh, target, stop_at_target, deriv)
+    hit_step, steps_run, proposed, accepted (trajectories put to / passing the acceptance
+    test of accept_test = 1), best_s, x, v and (optionally) the per-iteration energies."""
+    S = _sched(beta0, beta1, eps, gamma, refresh, target, stop_at_target, deriv, accept_test)
     out = _RepOut()
     best_s = np.zeros(P.n, dtype=np.int8)
     xo = np.empty(P.n); vo = np.empty(P.n)
@@ -270,17 +297,18 @@ def anneal_replica(P: Instance, T, seed, inst_id, r, beta0, beta1, eps, gamma, r
                                seed & (2**64 - 1), inst_id, r, _ptr(x0a), _ptr(v0a),
                                ctypes.byref(out), _ptr(best_s), _ptr(xo), _ptr(vo), _ptr(tr))
     res = dict(best_e=out.best_e, best_step=out.best_step, hit_step=out.hit_step,
-               steps_run=out.steps_run, best_s=best_s, x=xo, v=vo)
+               steps_run=out.steps_run, proposed=out.proposed, accepted=out.accepted, best_s=best_s, x=xo, v=vo)
     if trace:
         res["trace"] = tr
     return res
 
 
 def anneal(P: Instance, R, T, seed, inst_id, beta0, beta1, eps, gamma, refresh=0,
-           target=None, stop_at_target=False, threads=None, r0=0, want_spins=True, deriv=0):
+           target=None, stop_at_target=False, threads=None, r0=0, want_spins=True, deriv=0, accept_test=0):
     """R replicas (indices r0..r0+R-1) on `threads` host threads.
-    Returns arrays best_e[R], best_step[R], hit_step[R], steps_run[R], best_s[R][n]."""
-    S = _sched(beta0, beta1, eps, gamma, refresh, target, stop_at_target, deriv)
+    Returns arrays best_e[R], best_step[R], hit_step[R], steps_run[R], proposed[R],
+    accepted[R], best_s[R][n]."""
+    S = _sched(beta0, beta1, eps, gamma, refresh, target, stop_at_target, deriv, accept_test)
     outs = (_RepOut * R)()
     best_s = np.zeros((R, P.n), dtype=np.int8) if want_spins else None
     th = threads or os.cpu_count() or 1
@@ -291,6 +319,8 @@ def anneal(P: Instance, R, T, seed, inst_id, beta0, beta1, eps, gamma, refresh=0
                 best_step=np.array([o.best_step for o in outs], dtype=np.int64),
                 hit_step=np.array([o.hit_step for o in outs], dtype=np.int64),
                 steps_run=np.array([o.steps_run for o in outs], dtype=np.int64),
+                proposed=np.array([o.proposed for o in outs], dtype=np.int64),
+                accepted=np.array([o.accepted for o in outs], dtype=np.int64),
                 best_s=best_s)
 
 

@@ -13,7 +13,8 @@
  *   Eq. 4 / A6   H(x,v) = beta E(sgn x) + x.x/2 + v.v/2
  *   Eq. 5, 7, 8  dv/dt = beta * gamma (1 - tanh^2(gamma x)) * I - x
  *   Eq. A7, A8   x <- x + eps v ;  v <- v - eps grad H(x_new)
- *   Table 3      state 5: keep the best state seen so far
+ *   Table 3      state 4: acceptance test on H at the end of a trajectory (optional)
+ *                state 5: keep the best state seen so far
  *   Sec. 2.1     momentum drawn at random at the start of a trajectory;
  *                position prior g(x) is a standard normal (Eq. A3)
  *
@@ -225,7 +226,7 @@ typedef struct {
     int32_t stop_at_target;
     int64_t target;
     int32_t deriv;      /* derivative factor: 0 exact, 1 quadratic stand-in (orc_dfactor) */
-    int32_t pad;
+    int32_t accept_test;/* 0: every trajectory accepted (App. A); 1: Metropolis test on H (orc_metropolis) */
 } orc_sched;
 
 double orc_beta_at(const orc_sched *S, int64_t t, int64_t T)
@@ -240,12 +241,53 @@ typedef struct {
     int64_t best_step;  /* first iteration at which it was seen */
     int64_t hit_step;   /* first iteration with E <= target, or -1 */
     int64_t steps_run;  /* iterations executed */
+    int64_t proposed;   /* trajectories put to the acceptance test (accept_test = 1) */
+    int64_t accepted;   /* of those, accepted */
 } orc_replica_out;
+
+/* Eq. 4 (= Eq. A6): H(x, v) = beta E(sgn x) + x.x / 2 + v.v / 2, with E in units of q
+ * (beta E = beta q e). */
+double orc_hamiltonian(double beta, double q, int64_t e, const double *x, const double *v, int n)
+{
+    double xx = 0.0, vv = 0.0;
+    for (int i = 0; i < n; ++i) {
+        xx += x[i] * x[i];
+        vv += v[i] * v[i];
+    }
+    return beta * q * (double)e + 0.5 * xx + 0.5 * vv;
+}
+
+/* Table 3, state 4 read as the Metropolis test of HMC (App. A: exact dynamics conserve H,
+ * so the test accepts with probability 1; the discretised dynamics of Eq. A7 do not):
+ * the proposed end point of a trajectory is accepted with probability
+ * min(1, exp(-(H_end - H_start))), i.e. when the uniform u in (0, 1] satisfies
+ * u <= exp(-(H_end - H_start)).  Returns 1 to accept. */
+int orc_metropolis(double h_start, double h_end, double u)
+{
+    return u <= exp(-(h_end - h_start)) ? 1 : 0;
+}
+
+/* The uniform of the test that ends at the momentum draw d = t of the next trajectory:
+ * Philox counter (0xFFFFFFFF, r, t, inst) -- a spin index no instance has -- word 0, on
+ * the 24-bit grid of (0, 1]. */
+double orc_accept_uniform(uint64_t seed, uint32_t inst, uint32_t r, uint32_t t)
+{
+    uint32_t ctr[4] = {0xFFFFFFFFu, r, t, inst};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    return orc_u01_open(o[0]);
+}
 
 /* One replica of a PHIA run: initial draw (d = 0), then T iterations of
  * orc_step with the momentum redrawn at trajectory starts; the best state is
- * kept with strict improvement (Table 3, state 5).  x0/v0, when given, replace
- * the initial draw.  x/v out (optional) receive the final state. */
+ * kept with strict improvement (Table 3, state 5).  With S->accept_test = 1 and a
+ * refresh period, each trajectory's end point except the first's is put to the
+ * Metropolis test of orc_metropolis just before the next momentum draw (Table 3,
+ * state 4); a rejected end point sends x back to the trajectory's start (every
+ * state visited still counts for the best state).  The run's last trajectory has
+ * no test: nothing follows it.  x0/v0, when given, replace the initial draw.  x/v
+ * out (optional) receive the final state. */
 void orc_anneal_replica(const orc_inst *P, int32_t frac_bits, const orc_sched *S, int64_t T,
                         uint64_t seed, uint32_t inst_id, uint32_t r,
                         const double *x0, const double *v0,
@@ -256,6 +298,8 @@ void orc_anneal_replica(const orc_inst *P, int32_t frac_bits, const orc_sched *S
     double q = ldexp(1.0, -frac_bits);
     double *x = (double *)malloc(sizeof(double) * (size_t)n);
     double *v = (double *)malloc(sizeof(double) * (size_t)n);
+    double *xs = (double *)malloc(sizeof(double) * (size_t)n);  /* trajectory start (accept_test) */
+    double *vs = (double *)malloc(sizeof(double) * (size_t)n);
     int8_t *s = (int8_t *)malloc((size_t)n);
     int64_t *I = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     for (int j = 0; j < n; ++j) {
@@ -270,11 +314,44 @@ void orc_anneal_replica(const orc_inst *P, int32_t frac_bits, const orc_sched *S
     out->best_step = -1;
     out->hit_step = -1;
     out->steps_run = 0;
+    out->proposed = 0;
+    out->accepted = 0;
+    int64_t e_prev = 0;      /* E of the last iteration */
+    int64_t e_start = 0;     /* E(sgn x) at the start of the current trajectory */
+    int has_start = 0;       /* the current trajectory's start state is known (not the first) */
     for (int64_t t = 0; t < T; ++t) {
-        if (S->refresh > 0 && t > 0 && t % S->refresh == 0)
+        if (S->refresh > 0 && t > 0 && t % S->refresh == 0) {
+            if (S->accept_test == 1) {
+                /* End of the trajectory that ran iterations [t - refresh, t): test its end
+                 * point against its start under the Hamiltonian of its last iteration.  The
+                 * first trajectory starts from the initial draw, whose energy no iteration
+                 * evaluated; it is accepted as it stands. */
+                if (has_start) {
+                    double beta_end = orc_beta_at(S, t - 1, T);
+                    double h_start = orc_hamiltonian(beta_end, q, e_start, xs, vs, n);
+                    double h_end = orc_hamiltonian(beta_end, q, e_prev, x, v, n);
+                    double u = orc_accept_uniform(seed, inst_id, r, (uint32_t)t);
+                    out->proposed += 1;
+                    if (orc_metropolis(h_start, h_end, u)) {
+                        out->accepted += 1;
+                        e_start = e_prev;
+                    } else {
+                        memcpy(x, xs, sizeof(double) * (size_t)n);   /* back to the start point */
+                    }
+                } else {
+                    e_start = e_prev;
+                    has_start = 1;
+                }
+            }
             for (int j = 0; j < n; ++j) orc_draw(seed, inst_id, r, (uint32_t)j, (uint32_t)t, NULL, &v[j]);
+            if (S->accept_test == 1) {
+                memcpy(xs, x, sizeof(double) * (size_t)n);
+                memcpy(vs, v, sizeof(double) * (size_t)n);
+            }
+        }
         double beta = orc_beta_at(S, t, T);
         int64_t e = orc_step_mode(P, q, beta, S->eps, S->gamma, S->deriv, x, v, s, I);
+        e_prev = e;
         if (energy_trace) energy_trace[t] = e;
         out->steps_run = t + 1;
         int frozen = S->stop_at_target && out->hit_step >= 0;
@@ -290,7 +367,7 @@ void orc_anneal_replica(const orc_inst *P, int32_t frac_bits, const orc_sched *S
     }
     if (x_out) memcpy(x_out, x, sizeof(double) * (size_t)n);
     if (v_out) memcpy(v_out, v, sizeof(double) * (size_t)n);
-    free(x); free(v); free(s); free(I);
+    free(x); free(v); free(xs); free(vs); free(s); free(I);
 }
 
 /* ------------------------------------------------------ threaded replicas */

@@ -101,6 +101,11 @@ struct phia_s {
     int64_t *d_eacc = nullptr;
     int64_t *d_best_e = nullptr, *d_best_step = nullptr, *d_hit = nullptr;
     uint32_t *d_bits = nullptr;
+    int64_t *d_prop = nullptr, *d_acc = nullptr;   // acceptance test counts per replica (Table 3, state 4)
+    float *d_xstart = nullptr;          // FP32 path with the acceptance test: trajectory start positions
+    int64_t *d_elast = nullptr, *d_estart = nullptr;
+    float *d_xxs = nullptr, *d_vvs = nullptr;
+    int32_t *d_hass = nullptr;
     uint64_t *d_hit_ns = nullptr;       // %globaltimer of each replica's first hit
     uint64_t *d_start_ns = nullptr;     // %globaltimer when the run's records were reset
     // run counters
@@ -159,8 +164,11 @@ void free_replicas(phia_t *p) {
     for (void *b : {(void *)p->d_S, (void *)p->d_Epart, (void *)p->d_flags, (void *)p->d_X, (void *)p->d_V,
                     (void *)p->d_x, (void *)p->d_v, (void *)p->d_s0, (void *)p->d_s1, (void *)p->d_eacc,
                     (void *)p->d_best_e, (void *)p->d_best_step, (void *)p->d_hit, (void *)p->d_bits,
-                    (void *)p->d_hit_ns})
+                    (void *)p->d_hit_ns, (void *)p->d_prop, (void *)p->d_acc, (void *)p->d_xstart,
+                    (void *)p->d_elast, (void *)p->d_estart, (void *)p->d_xxs, (void *)p->d_vvs, (void *)p->d_hass})
         pool_free(b, p->stream);
+    p->d_prop = p->d_acc = nullptr; p->d_xstart = nullptr; p->d_elast = p->d_estart = nullptr;
+    p->d_xxs = p->d_vvs = nullptr; p->d_hass = nullptr;
     p->d_S = nullptr; p->d_Epart = nullptr; p->d_flags = nullptr; p->d_X = p->d_V = nullptr;
     p->d_x = p->d_v = nullptr; p->d_s0 = p->d_s1 = nullptr; p->d_eacc = nullptr;
     p->d_best_e = p->d_best_step = p->d_hit = nullptr; p->d_bits = nullptr; p->d_hit_ns = nullptr;
@@ -179,7 +187,13 @@ int ensure_replicas(phia_t *p, int R) {
     if (p->path == PHIA_PATH_FP32) {
         al((void **)&p->d_x, RN * 4); al((void **)&p->d_v, RN * 4);
         al((void **)&p->d_s0, RN); al((void **)&p->d_s1, RN);
+        al((void **)&p->d_xstart, RN * 4);
+        al((void **)&p->d_elast, (size_t)R * 8); al((void **)&p->d_estart, (size_t)R * 8);
+        al((void **)&p->d_xxs, (size_t)R * 4); al((void **)&p->d_vvs, (size_t)R * 4);
+        al((void **)&p->d_hass, (size_t)R * 4);
     }
+    al((void **)&p->d_prop, (size_t)R * 8);
+    al((void **)&p->d_acc, (size_t)R * 8);
     if (p->large) {
         const size_t Rp = (size_t)large_rpad(R);
         al((void **)&p->d_S, 4 * Rp * p->Kbytes);
@@ -226,6 +240,8 @@ int check_sched(const phia_schedule *s) {
     if (!(s->beta0 >= 0.0f) || !(s->beta1 >= 0.0f)) return fail(PHIA_EINVAL, "beta0 and beta1 must be >= 0");
     if (s->refresh < 0) return fail(PHIA_EINVAL, "refresh must be >= 0");
     if (s->deriv != 0 && s->deriv != 1) return fail(PHIA_EINVAL, "schedule.deriv must be 0 or 1");
+    if (s->accept_test != 0 && s->accept_test != 1) return fail(PHIA_EINVAL, "schedule.accept_test must be 0 or 1");
+    if (s->reserved != 0) return fail(PHIA_EINVAL, "schedule.reserved must be 0");
     return PHIA_OK;
 }
 
@@ -314,8 +330,10 @@ cudaError_t launch_path(phia_t *p, const RunArgs &a, int *launches) {
     // covers the same sizes.
     if (p->path == PHIA_PATH_TC && p->inc && !a.field_mode) return launch_inc_small(a, p->stream, launches);
     if (p->path == PHIA_PATH_TC) return launch_tc_small(a, p->op, p->stream, launches);
-    if (p->path == PHIA_PATH_FP32)
-        return launch_fp32_run(a, p->d_x, p->d_v, p->d_s0, p->d_s1, p->d_eacc, p->stream, launches);
+    if (p->path == PHIA_PATH_FP32) {
+        Fp32Metro m{p->d_xstart, p->d_elast, p->d_estart, p->d_xxs, p->d_vvs, p->d_hass};
+        return launch_fp32_run(a, p->d_x, p->d_v, p->d_s0, p->d_s1, p->d_eacc, m, p->stream, launches);
+    }
     return cudaErrorNotSupported;
 }
 
@@ -578,13 +596,24 @@ static int run_impl(phia_t *p, const phia_schedule *sched, int32_t R, int64_t t0
     if (p->batch) return batch_run(p->batch, sched, R, t0, steps, total, seed, x_in, x_out, v_in, v_out, reset,
                                    nullptr, nullptr, nullptr);
     if (R < 1) return fail(PHIA_EINVAL, "replicas must be >= 1");
+    if (sched->accept_test == 1 && p->path == PHIA_PATH_TC) {
+        // The acceptance test runs in the resident tcgen05 kernel with J in shared memory.
+        if (p->auto_tile && p->N <= tc_small_max_n(p->op)) {
+            p->large = p->imma = p->inc = false;
+            p->coupling_mem = 1;
+        } else if (p->large || p->imma || p->inc || p->coupling_mem == 2) {
+            return fail(PHIA_ENOTSUP, "schedule.accept_test = 1 runs on the resident tcgen05 kernel with J in shared "
+                                      "memory (tc_kernel 1, N <= %d with this operand) or the FP32 path",
+                        tc_small_max_n(p->op));
+        }
+    }
     if (steps < 1) return fail(PHIA_EINVAL, "steps must be >= 1");
     if (t0 < 0 || total < t0 + steps) return fail(PHIA_EINVAL, "need 0 <= t0 and t0 + steps <= total_steps");
     if (total > (int64_t)1 << 31) return fail(PHIA_ERANGE, "total_steps must be < 2^31 (Philox counter word)");
     CU(cudaSetDevice(p->device));
     if (!reset && (!p->ran || p->R_last != R))
         return fail(PHIA_ESTATE, "reset_best = 0 needs a previous run with the same replica count");
-    if (reset) {
+    if (reset && sched->accept_test == 0) {
         rc = apply_tuned(p, R);
         if (rc) return rc;
     }
@@ -597,7 +626,12 @@ static int run_impl(phia_t *p, const phia_schedule *sched, int32_t R, int64_t t0
     CU(cudaMemsetAsync(p->d_min_hit, 0xFF, 8, p->stream));
     CU(cudaMemsetAsync(p->d_iters, 0, 8, p->stream));
     CU(cudaMemsetAsync(p->d_err, 0, 4, p->stream));
+    CU(cudaMemsetAsync(p->d_prop, 0, (size_t)R * 8, p->stream));
+    CU(cudaMemsetAsync(p->d_acc, 0, (size_t)R * 8, p->stream));
     RunArgs a = base_args(p, R);
+    a.accept_test = sched->accept_test;
+    a.proposed = p->d_prop;
+    a.accepted = p->d_acc;
     a.t0 = t0; a.nsteps = steps; a.T_total = total;
     a.beta0 = sched->beta0; a.beta1 = sched->beta1; a.eps = sched->eps; a.gamma = sched->gamma;
     a.refresh = sched->refresh;
@@ -793,6 +827,18 @@ int phia_best(phia_t *p, int64_t *energy_k, int8_t *spins) {
         CU(cudaMemcpy(w.data(), p->d_bits + (size_t)r * p->W, (size_t)p->W * 4, cudaMemcpyDeviceToHost));
         for (int i = 0; i < p->N; ++i) spins[i] = ((w[i >> 5] >> (i & 31)) & 1u) ? 1 : -1;
     }
+    return PHIA_OK;
+}
+
+int phia_acceptance(phia_t *p, int32_t R, int64_t *proposed, int64_t *accepted) {
+    if (!p) return fail(PHIA_EINVAL, "handle is NULL");
+    if (p->batch) return fail(PHIA_ENOTSUP, "the acceptance test does not run on the CSR path");
+    std::vector<int64_t> be, bs, hs;
+    int rc = fetch_records(p, be, bs, hs);
+    if (rc) return rc;
+    if (R != p->R_last) return fail(PHIA_EINVAL, "replicas (%d) differs from the last run (%d)", R, p->R_last);
+    if (proposed) CU(cudaMemcpy(proposed, p->d_prop, (size_t)R * 8, cudaMemcpyDeviceToHost));
+    if (accepted) CU(cudaMemcpy(accepted, p->d_acc, (size_t)R * 8, cudaMemcpyDeviceToHost));
     return PHIA_OK;
 }
 

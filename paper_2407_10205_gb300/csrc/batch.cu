@@ -347,8 +347,11 @@ int batch_run(phia_batch_s *b, const phia_schedule *sched, int32_t R_real, int64
     const bool field_mode = spins_in != nullptr;
     if (!field_mode) {
         if (!sched) return bfail(PHIA_EINVAL, "schedule is NULL");
-        if (!(sched->eps > 0.0f) || !(sched->gamma > 0.0f) || sched->refresh < 0 || (sched->deriv != 0 && sched->deriv != 1))
+        if (!(sched->eps > 0.0f) || !(sched->gamma > 0.0f) || sched->refresh < 0 || (sched->deriv != 0 && sched->deriv != 1) ||
+            sched->reserved != 0)
             return bfail(PHIA_EINVAL, "invalid schedule");
+        if (sched->accept_test != 0)
+            return bfail(PHIA_ENOTSUP, "schedule.accept_test = 1 runs on the resident tcgen05 and FP32 paths only");
         if (steps < 1 || t0 < 0 || total < t0 + steps) return bfail(PHIA_EINVAL, "need steps >= 1, t0 + steps <= total");
         if (total > ((int64_t)1 << 31)) return bfail(PHIA_ERANGE, "total_steps must be < 2^31");
     }

@@ -51,6 +51,17 @@ __device__ __forceinline__ float draw_v(uint64_t seed, uint32_t inst, uint32_t r
     return box_muller(o.z, o.w);
 }
 
+// The uniform of the acceptance test (Table 3, state 4) of the trajectory that ends just
+// before the momentum draw d = t: counter (0xFFFFFFFF, r, t, inst) -- a spin index no
+// instance has -- word 0, on the 24-bit grid of (0, 1].
+__device__ __forceinline__ float accept_uniform(uint64_t seed, uint32_t inst, uint32_t r, uint32_t t) {
+    return u01_open(draw_raw(seed, inst, r, 0xFFFFFFFFu, t).x);
+}
+
+// Metropolis decision on the change dH = H_end - H_start of the Hamiltonian of Eq. 4:
+// accept when u <= exp(-dH) (always when dH <= 0).
+__device__ __forceinline__ bool metropolis_accept(float dH, float u) { return u <= expf(-dH); }
+
 // ------------------------------------------------------------------ HMC update
 
 // Eq. 8's derivative factor 1 - tanh^2(y) = sech^2(y), evaluated through the identity

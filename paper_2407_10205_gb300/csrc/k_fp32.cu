@@ -72,6 +72,9 @@ __global__ void __launch_bounds__(256) fp32_step(const RunArgs a, int64_t t, flo
     const float bgq = beta * a.gamma;   // J and h already carry q here
     const bool more = t + 1 < a.t0 + a.nsteps;
     const bool refresh_next = more && refresh_at(t + 1, a.refresh);
+    // With the acceptance test, a trajectory end leaves the refresh and the next position
+    // to fp32_metropolis, which first decides whether x goes back to the start.
+    const bool advance = more && !(refresh_next && a.accept_test == 1);
 #pragma unroll
     for (int q = 0; q < kRows; ++q) {
         const int r = r0 + ty * kRows + q;
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(256) fp32_step(const RunArgs a, int64_t t, flo
             } else {
                 float vi = momentum_update(v[idx], x[idx], I, a.eps, bgq, a.gamma, a.deriv);
                 float xi = x[idx];
-                if (more) {
+                if (advance) {
                     if (refresh_next) vi = draw_v(a.seed, a.inst, (uint32_t)r, (uint32_t)i, (uint32_t)(t + 1));
                     xi = xi + a.eps * vi;
                     x[idx] = xi;
@@ -104,7 +107,7 @@ __global__ void __launch_bounds__(256) fp32_step(const RunArgs a, int64_t t, flo
 }
 
 // Energy of iteration t per replica, best-state and target records (one warp per replica).
-__global__ void fp32_record(const RunArgs a, int64_t t, const int8_t *s_cur, int64_t *e_acc) {
+__global__ void fp32_record(const RunArgs a, int64_t t, const int8_t *s_cur, int64_t *e_acc, int64_t *e_last) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= a.R) return;
     const int r = warp;
@@ -113,6 +116,7 @@ __global__ void fp32_record(const RunArgs a, int64_t t, const int8_t *s_cur, int
     int imp = 0;
     if (lane == 0) {
         e_acc[r] = 0;
+        if (e_last) e_last[r] = E;
         const bool frozen = a.stop_at_target && a.hit_step[r] >= 0;
         if (!frozen && E < a.best_e[r]) {
             a.best_e[r] = E;
@@ -132,6 +136,92 @@ __global__ void fp32_record(const RunArgs a, int64_t t, const int8_t *s_cur, int
         const uint32_t bits = __ballot_sync(0xffffffffu, plus);
         if (lane == 0) a.best_bits[(size_t)r * a.W + w] = bits;
     }
+}
+
+// Sum of a float over the block (blockDim.x a multiple of 32, at most 1024); every thread
+// gets the result.
+__device__ float block_sum(float val, float *scratch) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+    __syncthreads();
+    if (lane == 0) scratch[w] = val;
+    __syncthreads();
+    float s = 0.0f;
+    for (int k = 0; k < nw; ++k) s += scratch[k];
+    return s;
+}
+
+// End of a trajectory before iteration t (t % refresh == 0) with the acceptance test
+// (Table 3, state 4): one block per replica.  H = beta E + x.x/2 + v.v/2 (Eq. 4) of the
+// end point (E of iteration t-1) against the start point's, both under beta_{t-1}; the
+// test uses the uniform of counter (0xFFFFFFFF, r, t, inst).  A rejection puts x back to
+// the start.  Then the momentum draw d = t, the new start's x.x and v.v, and the first
+// position update and sign of the new trajectory.  The call's first trajectory is kept
+// untested (its start energy was never evaluated).
+__global__ void fp32_metropolis(const RunArgs a, int64_t t, float *x, float *v, int8_t *s_next, Fp32Metro m) {
+    __shared__ float red[32];
+    __shared__ int revert;
+    const int r = blockIdx.x, N = a.N;
+    float xx = 0.0f, vv = 0.0f;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const float xi = x[(size_t)r * N + i], vi = v[(size_t)r * N + i];
+        xx += xi * xi;
+        vv += vi * vi;
+    }
+    xx = block_sum(xx, red);
+    vv = block_sum(vv, red);
+    if (threadIdx.x == 0) {
+        const long long e_end = m.e_last[r];
+        int rev = 0;
+        if (m.has_start[r]) {
+            const float beta = beta_at(t - 1, inv_tm1_of(a.T_total), a.beta0, a.beta1);
+            const float dH = beta * a.q * (float)(e_end - m.e_start[r]) + 0.5f * (xx - m.xx_start[r]) +
+                             0.5f * (vv - m.vv_start[r]);
+            const bool acc = metropolis_accept(dH, accept_uniform(a.seed, a.inst, (uint32_t)r, (uint32_t)t));
+            a.proposed[r] += 1;
+            if (acc) {
+                a.accepted[r] += 1;
+                m.e_start[r] = e_end;
+            } else {
+                rev = 1;
+            }
+        } else {
+            m.e_start[r] = e_end;
+            m.has_start[r] = 1;
+        }
+        revert = rev;
+    }
+    __syncthreads();
+    const bool rev = revert != 0;
+    float sx = 0.0f, sv = 0.0f;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const size_t idx = (size_t)r * N + i;
+        float xi = rev ? m.x_start[idx] : x[idx];
+        const float vi = draw_v(a.seed, a.inst, (uint32_t)r, (uint32_t)i, (uint32_t)t);
+        m.x_start[idx] = xi;
+        sx += xi * xi;
+        sv += vi * vi;
+        xi = xi + a.eps * vi;
+        x[idx] = xi;
+        v[idx] = vi;
+        s_next[idx] = xi >= 0.0f ? 1 : -1;
+    }
+    sx = block_sum(sx, red);
+    sv = block_sum(sv, red);
+    if (threadIdx.x == 0) {
+        m.xx_start[r] = sx;
+        m.vv_start[r] = sv;
+    }
+}
+
+// Start of a call with the acceptance test: counts and start flags cleared.
+__global__ void fp32_metro_reset(const RunArgs a, Fp32Metro m) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.R) return;
+    a.proposed[r] = 0;
+    a.accepted[r] = 0;
+    m.has_start[r] = 0;
 }
 
 // Field-only mode: energies of the given spins, accumulator reset.
@@ -159,7 +249,7 @@ __global__ void fp32_count(const RunArgs a, int64_t iters) {
 }  // namespace
 
 cudaError_t launch_fp32_run(const RunArgs &a, float *x, float *v, int8_t *s0, int8_t *s1, int64_t *e_acc,
-                            cudaStream_t st, int *launches) {
+                            const Fp32Metro &metro, cudaStream_t st, int *launches) {
     const int64_t RN = (int64_t)a.R * a.N;
     const int eb = 256;
     const unsigned eg = (unsigned)((RN + eb - 1) / eb);
@@ -170,6 +260,7 @@ cudaError_t launch_fp32_run(const RunArgs &a, float *x, float *v, int8_t *s0, in
     if (a.field_mode) {
         // Field only: spins in, field/energy out through the same step kernel.
         RunArgs f = a;
+        f.accept_test = 0;
         f.nsteps = 1;
         fp32_step<<<grid, block, 0, st>>>(f, a.t0, x, v, a.spins_in, s1, e_acc);
         fp32_field_energy<<<(a.R + 255) / 256, 256, 0, st>>>(f, e_acc);
@@ -179,11 +270,20 @@ cudaError_t launch_fp32_run(const RunArgs &a, float *x, float *v, int8_t *s0, in
     }
     fp32_prologue<<<eg, eb, 0, st>>>(a, x, v, s0);
     ++n;
+    const bool metro_on = a.accept_test == 1;
+    if (metro_on) {
+        fp32_metro_reset<<<(a.R + 255) / 256, 256, 0, st>>>(a, metro);
+        ++n;
+    }
     int8_t *cur = s0, *nxt = s1;
     for (int64_t t = a.t0; t < a.t0 + a.nsteps; ++t) {
         fp32_step<<<grid, block, 0, st>>>(a, t, x, v, cur, nxt, e_acc);
-        fp32_record<<<rg, 256, 0, st>>>(a, t, cur, e_acc);
+        fp32_record<<<rg, 256, 0, st>>>(a, t, cur, e_acc, metro_on ? metro.e_last : nullptr);
         n += 2;
+        if (metro_on && t + 1 < a.t0 + a.nsteps && a.refresh > 0 && (t + 1) % a.refresh == 0) {
+            fp32_metropolis<<<a.R, 256, 0, st>>>(a, t + 1, x, v, nxt, metro);
+            ++n;
+        }
         int8_t *tmp = cur; cur = nxt; nxt = tmp;
     }
     fp32_epilogue<<<eg, eb, 0, st>>>(a, x, v);

@@ -41,6 +41,18 @@ struct SmallShared {
     int32_t improved[2][kNB];              // by iteration parity
 };
 
+// State of the acceptance test (Table 3, state 4; kernels with METRO only), after SmallShared.
+struct MetroShared {
+    float hx[kMaxWarps][kMaxRPT];   // per-warp sums of x.x at a trajectory's end point
+    float hv[kMaxWarps][kMaxRPT];   // ... of v.v
+    float sx[kMaxWarps][kMaxRPT];   // per-warp sums of x.x at the current trajectory's start
+    float sv[kMaxWarps][kMaxRPT];   // ... of v.v
+    long long e_start[kNB];         // E(sgn x) at the current trajectory's start
+    int32_t has_start[kNB];         // start known (not the call's first trajectory)
+    int32_t revert[kNB];            // the trajectory that just ended was rejected
+    int32_t prop[kNB], acc[kNB];    // tests and acceptances
+};
+
 template <int OP>
 __device__ __forceinline__ uint8_t *operand_ptr(uint8_t *base, int row, int col, uint32_t sbo) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
@@ -130,7 +142,14 @@ __device__ __forceinline__ void tmem_ld2_sync(uint32_t t0, uint32_t t1, float (&
 // control warps follow: lane 0 of control warp m issues the field MMAs of output tile m
 // (in parallel with the other tiles' issue), the first RL lanes of control warp 0 keep
 // the records, so MMA issue and records overlap the epilogue warps' work.
-template <int MT, int OP, int CH, int RPT, bool AT, int DERIV>
+// METRO: the acceptance test of Table 3, state 4 (schedule accept_test = 1).  At the last
+// iteration t of a trajectory the epilogue warps leave out the refresh and the next
+// position and store warp sums of x.x and v.v instead; control warp 0 decides per replica
+// after the records (dH under beta_t, uniform of counter (0xFFFFFFFF, r, t + 1)); after a
+// second barrier the epilogue warps put rejected positions back to the trajectory start,
+// draw the momentum d = t + 1, keep the new start and its sums, and write the next spins;
+// the next field MMAs go out after a third barrier.
+template <int MT, int OP, int CH, int RPT, bool AT, int DERIV, bool METRO>
 __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_small_kernel(const RunArgs a, int Kpad) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
     constexpr int RL = CH * RPT;
@@ -149,6 +168,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
     uint8_t *sA = smem;
     uint8_t *sB = AT ? smem : sA + MT * 128 * Kbytes;
     SmallShared *sm = reinterpret_cast<SmallShared *>(sB + kNB * Kbytes);
+    MetroShared *ms = reinterpret_cast<MetroShared *>(sm + 1);   // METRO kernels only
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool ctl = warp >= NEPI;         // control warps
@@ -188,6 +208,12 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
         sm->best_step[tid] = rec ? a.best_step[r] : -1;
         sm->hit[tid] = rec ? a.hit_step[r] : -1;
         sm->hit_ns[tid] = (rec && a.hit_ns) ? a.hit_ns[r] : 0ull;
+        if constexpr (METRO) {
+            ms->has_start[tid] = 0;
+            ms->revert[tid] = 0;
+            ms->prop[tid] = 0;
+            ms->acc[tid] = 0;
+        }
     }
     if (tid == 0) sm->stop[0] = sm->stop[1] = 0;
     tc_fence_before();
@@ -224,6 +250,9 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
     uint8_t *my_b = operand_ptr<OP>(sB, ctl ? 0 : ch * RPT, live_i ? i : 0, SBO);
     const int32_t hki = live_i ? a.hk[i] : 0;
     float x[RPT], v[RPT];
+    float xs[RPT];     // METRO: positions at the current trajectory's start
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) xs[k] = 0.0f;
     uint32_t cur = 0;  // bit k: spin i of replica ch*RPT+k is +1 in the B of this iteration
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
@@ -330,6 +359,29 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
                     const int r = rbase + ch * RPT + k;
                     if (live_i && r < a.R && a.field_out) a.field_out[(size_t)r * N + i] = Ik[k];
                 }
+            } else if (METRO && it + 1 < nit && a.refresh > 0 && rc == 0) {
+                // Last iteration of a trajectory under the acceptance test: the update of v,
+                // then warp sums of x.x and v.v of the end point; refresh and position wait
+                // for the decision.
+                if (live_i) {
+                    const float bgq = beta_at(t, inv_tm1, a.beta0, a.beta1) * gq;
+#pragma unroll
+                    for (int k = 0; k < RPT; ++k) v[k] = DERIV == 1 ? momentum_quad(v[k], x[k], (float)Ik[k], eps, bgq, gamma)
+                                                                    : momentum_exact(v[k], x[k], (float)Ik[k], eps, bgq, gamma);
+                }
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) {
+                    float px = live_i ? x[k] * x[k] : 0.0f, pv = live_i ? v[k] * v[k] : 0.0f;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        px += __shfl_xor_sync(0xffffffffu, px, o);
+                        pv += __shfl_xor_sync(0xffffffffu, pv, o);
+                    }
+                    if (lane == 0) {
+                        ms->hx[warp][k] = px;
+                        ms->hv[warp][k] = pv;
+                    }
+                }
             } else if (live_i) {
                 const float bgq = beta_at(t, inv_tm1, a.beta0, a.beta1) * gq;
                 const bool more = it + 1 < nit;
@@ -360,9 +412,11 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
         }
         phase ^= 1u;
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
+        const bool tested = METRO && !a.field_mode && it + 1 < nit && a.refresh > 0 && rc == 0;
         if (ctl) {
-            // Next iteration's field first: B holds its spins and every TMEM read is done.
-            if (lane == 0 && it + 1 < nit) issue_field(cw);
+            // Next iteration's field first: B holds its spins and every TMEM read is done
+            // (after a trajectory end under the acceptance test, once the spins are written).
+            if (lane == 0 && it + 1 < nit && !tested) issue_field(cw);
             // Records of iteration t (Table 3, state 5), one lane per replica column.
             if (cw == 0 && lane < RL) {
                 const int c = lane, r = rbase + c;
@@ -385,6 +439,39 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
                         sm->hit_ns[c] = globaltimer_ns();
                         if (a.stop_at_target) atomicMin(a.min_hit, (unsigned long long)t);
                     }
+                    if (tested) {
+                        // Table 3, state 4: H = beta E + x.x/2 + v.v/2 (Eq. 4) of the end point
+                        // against the start, both under beta_t.
+                        float xx = 0.0f, vv = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < 4 * MT; ++j) {
+                            xx += ms->hx[(c / RPT) * 4 * MT + j][c % RPT];
+                            vv += ms->hv[(c / RPT) * 4 * MT + j][c % RPT];
+                        }
+                        int rev = 0;
+                        if (ms->has_start[c]) {
+                            float sx = 0.0f, sv = 0.0f;
+#pragma unroll
+                            for (int j = 0; j < 4 * MT; ++j) {
+                                sx += ms->sx[(c / RPT) * 4 * MT + j][c % RPT];
+                                sv += ms->sv[(c / RPT) * 4 * MT + j][c % RPT];
+                            }
+                            const float beta = beta_at(t, inv_tm1, a.beta0, a.beta1);
+                            const float dH = beta * a.q * (float)(E - ms->e_start[c]) + 0.5f * (xx - sx) +
+                                             0.5f * (vv - sv);
+                            ms->prop[c] += 1;
+                            if (metropolis_accept(dH, accept_uniform(a.seed, a.inst, (uint32_t)r, (uint32_t)(t + 1)))) {
+                                ms->acc[c] += 1;
+                                ms->e_start[c] = E;
+                            } else {
+                                rev = 1;
+                            }
+                        } else {
+                            ms->e_start[c] = E;
+                            ms->has_start[c] = 1;
+                        }
+                        ms->revert[c] = rev;
+                    }
                 }
                 sm->improved[it & 1][c] = imp;
             }
@@ -401,6 +488,45 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
                     const uint32_t bits = __ballot_sync(0xffffffffu, live_i && ((prv >> k) & 1u));
                     if (lane == 0 && word < a.W) a.best_bits[(size_t)(rbase + c) * a.W + word] = bits;
                 }
+            }
+        }
+        if constexpr (METRO) {
+            if (tested) {
+                // The decision is in shared memory: rejected replicas go back to the start,
+                // then the momentum draw d = t + 1, the new start and its sums, and the next
+                // position and spins; the field MMAs follow once B holds them.
+                __syncthreads();
+                if (!ctl) {
+#pragma unroll
+                    for (int k = 0; k < RPT; ++k) {
+                        const int c = ch * RPT + k;
+                        if (live_i) {
+                            if (ms->revert[c]) x[k] = xs[k];
+                            v[k] = draw_v(a.seed, a.inst, (uint32_t)(rbase + c), (uint32_t)i, (uint32_t)(t + 1));
+                            xs[k] = x[k];
+                        }
+                        float px = live_i ? x[k] * x[k] : 0.0f, pv = live_i ? v[k] * v[k] : 0.0f;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            px += __shfl_xor_sync(0xffffffffu, px, o);
+                            pv += __shfl_xor_sync(0xffffffffu, pv, o);
+                        }
+                        if (lane == 0) {
+                            ms->sx[warp][k] = px;
+                            ms->sv[warp][k] = pv;
+                        }
+                        if (live_i) {
+                            x[k] = x[k] + eps * v[k];
+                            const bool plus = x[k] >= 0.0f;
+                            put_spin<OP>(my_b + k * 16, plus);
+                            nxt |= (uint32_t)plus << k;
+                        }
+                    }
+                    fence_proxy_async_smem();
+                    tc_fence_before();
+                }
+                __syncthreads();
+                if (ctl && lane == 0) issue_field(cw);
             }
         }
         prv = cur;
@@ -442,6 +568,10 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
             a.best_step[r] = sm->best_step[lane];
             a.hit_step[r] = sm->hit[lane];
             if (a.hit_ns) a.hit_ns[r] = sm->hit_ns[lane];
+            if constexpr (METRO) {
+                a.proposed[r] = ms->prop[lane];
+                a.accepted[r] = ms->acc[lane];
+            }
         }
     }
     if (ctl && cw == 0 && lane == 0) {
@@ -460,13 +590,15 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
     }
 }
 
-template <int MT, int OP, int CH, int RPT, bool AT = false>
+template <int MT, int OP, int CH, int RPT, bool AT = false, bool METRO = false>
 cudaError_t launch_cfg(const RunArgs &a, int Kpad, cudaStream_t st) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
     constexpr int RL = CH * RPT;
-    const size_t smem = (size_t)((AT ? 0 : MT * 128) + kNB) * Kpad * ESZ + sizeof(SmallShared) + 16;
+    const size_t smem = (size_t)((AT ? 0 : MT * 128) + kNB) * Kpad * ESZ + sizeof(SmallShared) +
+                        (METRO ? sizeof(MetroShared) : 0) + 16;
     // The derivative mode is a template parameter: the update loop stays straight-line.
-    auto kern = a.deriv == 1 ? tc_small_kernel<MT, OP, CH, RPT, AT, 1> : tc_small_kernel<MT, OP, CH, RPT, AT, 0>;
+    auto kern = a.deriv == 1 ? tc_small_kernel<MT, OP, CH, RPT, AT, 1, METRO>
+                             : tc_small_kernel<MT, OP, CH, RPT, AT, 0, METRO>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (a.R + RL - 1) / RL;
@@ -492,16 +624,18 @@ int tc_small_tile_replicas(int R, int requested) {
 
 namespace {
 
-template <int MT, int OP, bool AT>
+template <int MT, int OP, bool AT, bool METRO = false>
 cudaError_t launch_at(const RunArgs &a, int Kpad, cudaStream_t st) {
     const int rl = tc_small_tile_replicas(a.R, a.tile_rl);
-    if (rl == 16) return launch_cfg<MT, OP, 2, 8, AT>(a, Kpad, st);
-    if (rl == 8) return launch_cfg<MT, OP, 2, 4, AT>(a, Kpad, st);
-    return launch_cfg<MT, OP, 1, 4, AT>(a, Kpad, st);
+    if (rl == 16) return launch_cfg<MT, OP, 2, 8, AT, METRO>(a, Kpad, st);
+    if (rl == 8) return launch_cfg<MT, OP, 2, 4, AT, METRO>(a, Kpad, st);
+    return launch_cfg<MT, OP, 1, 4, AT, METRO>(a, Kpad, st);
 }
 
 template <int MT, int OP>
 cudaError_t launch_mt(const RunArgs &a, int Kpad, cudaStream_t st) {
+    // The acceptance test (with trajectories to test) runs with J in shared memory.
+    if (a.accept_test == 1 && a.refresh > 0 && !a.field_mode) return launch_at<MT, OP, false, true>(a, Kpad, st);
     if (a.coupling_mem == 2) return launch_at<MT, OP, true>(a, Kpad, st);
     return launch_at<MT, OP, false>(a, Kpad, st);
 }

@@ -106,8 +106,10 @@ extern "C" int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N
     if (operand != PHIA_OP_E4M3 && operand != PHIA_OP_BF16 && operand != PHIA_OP_AUTO)
         return set_last_error(PHIA_EINVAL, "phia_run_noalloc: unknown operand");
     if (!(sched->eps > 0.0f) || !(sched->gamma > 0.0f) || !(sched->beta0 >= 0.0f) || !(sched->beta1 >= 0.0f) ||
-        sched->refresh < 0 || (sched->deriv != 0 && sched->deriv != 1))
+        sched->refresh < 0 || (sched->deriv != 0 && sched->deriv != 1) || sched->reserved != 0)
         return set_last_error(PHIA_EINVAL, "phia_run_noalloc: invalid schedule");
+    if (sched->accept_test != 0)
+        return set_last_error(PHIA_ENOTSUP, "phia_run_noalloc: schedule.accept_test = 1 is not supported here");
     // A size too large for the scratch whatever the operand is refused before any device work.
     if (noalloc_layout(N, replicas, operand == PHIA_OP_BF16 ? kOpBF16 : kOpE4M3).need > kScratchBytes) {
         char msg[320];

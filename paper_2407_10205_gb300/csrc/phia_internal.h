@@ -45,7 +45,8 @@ struct RunArgs {
     int32_t coupling_mem;                // tensor-core small path: 1 = J in shared, 2 = in tensor memory
     int64_t wait_ns;                     // per-iteration kernel: bound of each device wait (0 = kWaitTimeoutNs)
     int32_t stall_producer;              // per-iteration kernel, testing: the TMA producer issues nothing
-    int32_t pad0;
+    int32_t accept_test;                 // Table 3 state 4: 1 = Metropolis test on H at trajectory ends
+    int64_t *proposed, *accepted;        // [R] per-replica counts of the test (accept_test = 1)
 };
 
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;  // 2 s bound on every device-side wait
@@ -197,9 +198,18 @@ int inc_small_max_n();
 int inc_small_tile_replicas(int N, int requested);
 cudaError_t launch_inc_small(const RunArgs &a, cudaStream_t st, int *launches);
 
-// Plain FP32 per-step path (the comparator).
+// Plain FP32 per-step path (the comparator).  `metro` holds the acceptance test's
+// per-replica state (used when a.accept_test = 1): the trajectory's start position
+// [R][N], the last iteration's energy, the start's energy and x.x, v.v sums, whether a
+// start is known.
+struct Fp32Metro {
+    float *x_start;
+    int64_t *e_last, *e_start;
+    float *xx_start, *vv_start;
+    int32_t *has_start;
+};
 cudaError_t launch_fp32_run(const RunArgs &a, float *x, float *v, int8_t *s0, int8_t *s1,
-                            int64_t *e_acc, cudaStream_t st, int *launches);
+                            int64_t *e_acc, const Fp32Metro &metro, cudaStream_t st, int *launches);
 
 // Philox draws for testing.
 cudaError_t launch_philox_draws(uint64_t seed, uint32_t inst, uint32_t d, int R, int N, uint32_t *raw,

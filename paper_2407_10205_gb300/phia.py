@@ -43,7 +43,7 @@ class Schedule(ctypes.Structure):
     _fields_ = [("beta0", ctypes.c_float), ("beta1", ctypes.c_float), ("eps", ctypes.c_float),
                 ("gamma", ctypes.c_float), ("refresh", ctypes.c_int32), ("has_target", ctypes.c_int32),
                 ("stop_at_target", ctypes.c_int32), ("deriv", ctypes.c_int32),
-                ("target_k", ctypes.c_int64)]
+                ("target_k", ctypes.c_int64), ("accept_test", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -97,6 +97,7 @@ SIGNATURES = {
     "phia_autotune": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "phia_stats_get": (ctypes.c_int, [_P, _P]),
     "phia_replica_results": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P]),
+    "phia_acceptance": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "phia_run": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                 ctypes.c_uint64, _P, _P, ctypes.c_int32]),
     "phia_init_state": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint64, _P, _P]),
@@ -170,11 +171,14 @@ def _dev_ptr(t):
 DERIV_EXACT, DERIV_QUADRATIC = 0, 1
 
 
+ACCEPT_ALL, ACCEPT_METROPOLIS = 0, 1
+
+
 def schedule(beta0, beta1, eps, gamma, refresh=0, target=None, stop_at_target=False,
-             deriv=DERIV_EXACT) -> Schedule:
+             deriv=DERIV_EXACT, accept_test=ACCEPT_ALL) -> Schedule:
     return Schedule(float(beta0), float(beta1), float(eps), float(gamma), int(refresh),
                     0 if target is None else 1, 1 if stop_at_target else 0, int(deriv),
-                    0 if target is None else int(target))
+                    0 if target is None else int(target), int(accept_test), 0)
 
 
 MEM_AUTO, MEM_SHARED, MEM_TENSOR = 0, 1, 2
@@ -260,6 +264,14 @@ def replica_results(h, replicas: int, n: int):
     bits = np.empty((replicas, W), dtype=np.uint32)
     _check(load().phia_replica_results(h, int(replicas), _np_ptr(be), _np_ptr(bs), _np_ptr(hs), _np_ptr(bits)))
     return be, bs, hs, bits
+
+
+def acceptance(h, replicas: int):
+    """(proposed, accepted) per replica of the last run (phia_acceptance)."""
+    prop = np.empty(replicas, dtype=np.int64)
+    acc = np.empty(replicas, dtype=np.int64)
+    _check(load().phia_acceptance(h, int(replicas), _np_ptr(prop), _np_ptr(acc)))
+    return prop, acc
 
 
 def unpack_bits(bits, n: int) -> np.ndarray:

@@ -342,3 +342,110 @@ def test_tts_definition():
     assert o.tts(2.0, 0.99) == 2.0 and o.tts(2.0, 1.0) == 2.0
     assert o.tts(1.0, 0.5) == pytest.approx(math.log(0.01) / math.log(0.5))
     assert o.tts(1.0, 0.0) == math.inf
+
+
+# ------------------------------------------------------------------ acceptance test (Table 3, state 4)
+
+def test_metropolis_two_spin_hand_case():
+    """Hamiltonian (Eq. 4 / A6) and the Metropolis decision on the hand-worked 2-spin case
+    of tests/golden/metropolis_two_spin.txt: one proposal always accepted (dH < 0), the
+    reverse one accepted only below exp(-dH); fixed point scales E, not H."""
+    g = read_golden("metropolis_two_spin.txt")
+    k = np.array(g["k"].split(), dtype=np.int8).reshape(2, 2)
+    P = _dense(k, [0, 0])
+    beta = float(g["beta"])
+    xA, vA, xB, vB = f64(g["xA"]), f64(g["vA"]), f64(g["xB"]), f64(g["vB"])
+    sA, sB = np.sign(xA).astype(np.int8), np.sign(xB).astype(np.int8)
+    assert o.energy_exact(P, sA) == int(g["EA"]) and o.energy_exact(P, sB) == int(g["EB"])
+    HA = o.hamiltonian(beta, 1.0, int(g["EA"]), xA, vA)
+    HB = o.hamiltonian(beta, 1.0, int(g["EB"]), xB, vB)
+    assert HA == float(g["HA"]) and HB == float(g["HB"])
+    # fixed point: k = 2 with q = 1/2 is the same physical instance
+    P2 = o.Instance(np.zeros(2, dtype=np.int32), k=(2 * k).astype(np.int8), frac_bits=1)
+    eA2 = o.energy_exact(P2, sA)
+    assert eA2 == 2 * int(g["EA"]) and o.hamiltonian(beta, P2.q, eA2, xA, vA) == HA
+    thr = float(g["exp_minus_dH"])
+    for u in (1.0, 0.5, 0.0143, 0.0142, 2.0 ** -24):
+        assert o.metropolis(HA, HB, u)                      # dH < 0: always
+    assert not o.metropolis(HB, HA, 0.5)
+    assert o.metropolis(HB, HA, 0.0142) and not o.metropolis(HB, HA, 0.0143)
+    assert abs(math.exp(-(HA - HB)) - thr) < 1e-15
+    assert o.metropolis(HA, HA, 1.0)                          # dH = 0: accepted even at u = 1
+
+
+def test_accept_uniform_is_philox_word0_on_the_24_bit_grid():
+    """The test's uniform: Philox4x32-10 word 0 of counter (0xFFFFFFFF, r, t, inst), mapped
+    like every other uniform onto {1, ..., 2^24} / 2^24."""
+    seed, inst, r, t = 0x0123456789ABCDEF, 7, 3, 50
+    w = o.philox4x32_10([0xFFFFFFFF, r, t, inst], [seed & 0xFFFFFFFF, seed >> 32])[0]
+    u = o.accept_uniform(seed, inst, r, t)
+    assert u == ((w >> 8) + 1) / 2.0 ** 24 and 0.0 < u <= 1.0
+
+
+def _metropolis_run_by_composition(P, T, seed, inst, r, b0, b1, eps, gamma, refresh):
+    """The run with the acceptance test spelled out from the oracle's single steps and
+    draws: a test at every momentum draw t (t % refresh == 0, t > 0) except the first, of
+    the trajectory [t - refresh, t) under beta_{t-1}, with the uniform of draw t; a
+    rejection puts x back to the trajectory's start."""
+    n = P.n
+    x = np.array([o.draw(seed, inst, r, j, 0)[0] for j in range(n)])
+    v = np.array([o.draw(seed, inst, r, j, 0)[1] for j in range(n)])
+    es, xs, vs, e_start, have, prop, acc = [], None, None, None, False, 0, 0
+    e = None
+    for t in range(T):
+        if t > 0 and t % refresh == 0:
+            if have:
+                be = o.beta_at(t - 1, T, b0, b1)
+                prop += 1
+                if o.accept_uniform(seed, inst, r, t) <= math.exp(-(o.hamiltonian(be, P.q, e, x, v)
+                                                                       - o.hamiltonian(be, P.q, e_start, xs, vs))):
+                    acc += 1
+                    e_start = e
+                else:
+                    x = xs.copy()
+            else:
+                e_start, have = e, True
+            v = np.array([o.draw(seed, inst, r, j, t)[1] for j in range(n)])
+            xs, vs = x.copy(), v.copy()
+        x, v, s, I, e = o.step(P, x, v, o.beta_at(t, T, b0, b1), eps, gamma)
+        es.append(e)
+    return es, x, v, prop, acc
+
+
+def test_metropolis_run_is_composition_of_steps_and_tests():
+    d = ins.dense_int(10, 5, 5, seed=31)
+    P = _dense(d.k, d.kh)
+    T, seed, inst, refresh = 23, 17, 2, 4
+    b0, b1, eps, gamma = 0.2, 1.5, 0.35, 2.0
+    total_rej = 0
+    for r in range(6):
+        res = o.anneal_replica(P, T, seed, inst, r, b0, b1, eps, gamma, refresh=refresh, trace=True, accept_test=1)
+        es, x, v, prop, acc = _metropolis_run_by_composition(P, T, seed, inst, r, b0, b1, eps, gamma, refresh)
+        assert list(res["trace"]) == es
+        assert np.array_equal(res["x"], x) and np.array_equal(res["v"], v)
+        assert res["proposed"] == prop == 4 and res["accepted"] == acc      # tests at t = 8, 12, 16, 20
+        total_rej += prop - acc
+    assert total_rej > 0, "choose a case with rejections"
+
+
+def test_metropolis_without_trajectories_changes_nothing():
+    """With refresh = 0 the run is one trajectory and no test happens."""
+    d = ins.dense_int(9, 5, 5, seed=3)
+    P = _dense(d.k, d.kh)
+    a = o.anneal_replica(P, 40, 1, 0, 0, 0.1, 1.0, 0.3, 2.0, refresh=0, trace=True, accept_test=1)
+    b = o.anneal_replica(P, 40, 1, 0, 0, 0.1, 1.0, 0.3, 2.0, refresh=0, trace=True, accept_test=0)
+    assert np.array_equal(a["trace"], b["trace"]) and a["proposed"] == 0
+
+
+def test_metropolis_beta_zero_acceptance_tends_to_one():
+    """beta = 0: per spin the map is symplectic Euler on a unit oscillator, which keeps
+    x^2 + v^2 + eps x v, so dH = (eps / 2) sum_i (x_i v_i |start - x_i v_i |end) -> 0 with
+    eps: the acceptance rate goes to 1 (App. A: exact dynamics accept everything), and
+    falls below 1 when eps is large."""
+    d = ins.dense_int(8, 5, 5, seed=4)
+    P = _dense(d.k, d.kh)
+    rates = {}
+    for eps in (0.001, 0.8):
+        res = o.anneal(P, 32, 201, 5, 0, 0.0, 0.0, eps, 2.0, refresh=4, accept_test=1)
+        rates[eps] = res["accepted"].sum() / res["proposed"].sum()
+    assert rates[0.001] >= 0.99 and rates[0.8] < rates[0.001]
