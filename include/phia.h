@@ -221,6 +221,42 @@ int phia_stats_get(phia_t *p, phia_stats *out);
 int phia_replica_results(phia_t *p, int32_t replicas, int64_t *best_energy_k,
                          int64_t *best_step, int64_t *hit_step, uint32_t *best_bits);
 
+/* ---------------------------------------------------------------- vanilla GAHMC
+ * The exact dynamics of H(x, v) = beta E(sgn x) + x.x/2 + v.v/2 (Eq. 4, App. A) solved by
+ * zero crossings -- the Gaussian-augmented HMC of the paper's reference [Pakman &
+ * Paninski 2013] that Sec. 2.1 names as the exact alternative to PHIA's approximate
+ * gradient and Sec. 3.2 uses as an ablation.  Inside an orthant every coordinate rotates
+ * on the unit circle (x cos t + v sin t); where x_j reaches 0 the spin flips if the
+ * kinetic energy of that coordinate pays the energy step beta q dE, dE = 2 s_j I_j
+ * (speed reduced to sqrt(A^2 - 2 beta q dE)), else it is reflected.  With a travel time
+ * <= pi each spin meets its wall at most once per trajectory; events are taken in time
+ * order (ties: lower spin index first).  Replicas are independent (one warp each).
+ * Random numbers as phia_anneal: the initial draw d = 0, the momentum of trajectory
+ * k > 0 from draw d = k. */
+typedef struct phia_gahmc_schedule {
+    float beta0;           /* inverse temperature of the first trajectory */
+    float beta1;           /* of the last (linear in between) */
+    float travel;          /* time per trajectory, 0 < travel <= pi */
+    int32_t has_target;    /* 1: record the first trajectory whose states reach E <= target_k */
+    int64_t target_k;      /* units of q */
+} phia_gahmc_schedule;
+
+/* Run `trajectories` GAHMC trajectories for `replicas` replicas of a dense handle
+ * (N <= 1024; any dense path -- it reads the stored int8 couplings).  x, v: device
+ * [replicas][N] float32 or NULL: on entry the initial state (NULL: the Philox draw d = 0),
+ * on return the final state.  counts: device [replicas][2] int64 (crossings, reflections)
+ * or NULL.  events: device [replicas][events_cap] int32 or NULL: the first events_cap wall
+ * events of each replica in order, j for a crossing of spin j and -(j + 1) for a
+ * reflection; entries past a replica's events are left untouched.  The per-replica
+ * records (phia_best, phia_replica_results, phia_stats_get) hold the best energy over
+ * every visited state (the initial one and one per crossing), with best_step and
+ * hit_step counted in trajectories (0 = already in the initial state or trajectory 0);
+ * spin_updates counts N per replica and trajectory.  Asynchronous.  PHIA_ENOTSUP for a
+ * CSR handle or N > 1024; PHIA_EINVAL for travel outside (0, pi], negative beta or
+ * trajectories < 1. */
+int phia_gahmc(phia_t *p, const phia_gahmc_schedule *sched, int32_t replicas, int64_t trajectories,
+               uint64_t seed, float *x, float *v, int64_t *counts, int32_t *events, int32_t events_cap);
+
 /* Acceptance counts of the last run with accept_test = 1 (Table 3, state 4: the
  * acceptance rate is accepted / proposed), host arrays of `replicas` entries (either may
  * be NULL): trajectories put to the test and accepted, per replica.  Zero after a run

@@ -66,6 +66,17 @@ class _Sched(ctypes.Structure):
                 ("target", ctypes.c_int64), ("deriv", ctypes.c_int32), ("accept_test", ctypes.c_int32)]
 
 
+class _GahmcSched(ctypes.Structure):
+    _fields_ = [("beta0", ctypes.c_double), ("beta1", ctypes.c_double), ("travel", ctypes.c_double),
+                ("trajectories", ctypes.c_int64), ("has_target", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("target", ctypes.c_int64)]
+
+
+class _GahmcOut(ctypes.Structure):
+    _fields_ = [("best_e", ctypes.c_int64), ("best_traj", ctypes.c_int64), ("crossings", ctypes.c_int64),
+                ("reflections", ctypes.c_int64), ("hit_traj", ctypes.c_int64)]
+
+
 class _RepOut(ctypes.Structure):
     _fields_ = [("best_e", ctypes.c_int64), ("best_step", ctypes.c_int64),
                 ("hit_step", ctypes.c_int64), ("steps_run", ctypes.c_int64),
@@ -111,6 +122,12 @@ def _load():
             lib.orc_metropolis.restype = ctypes.c_int
             lib.orc_accept_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
             lib.orc_accept_uniform.restype = ctypes.c_double
+            lib.orc_gahmc_cross_time.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int8]
+            lib.orc_gahmc_cross_time.restype = ctypes.c_double
+            lib.orc_gahmc_replica.argtypes = [P(_Inst), ctypes.c_int32, P(_GahmcSched), ctypes.c_uint64,
+                                              ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                              P(_GahmcOut), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
             lib.orc_beta_at.argtypes = [P(_Sched), ctypes.c_int64, ctypes.c_int64]
             lib.orc_beta_at.restype = ctypes.c_double
             lib.orc_anneal_replica.argtypes = [P(_Inst), ctypes.c_int32, P(_Sched), ctypes.c_int64,
@@ -322,6 +339,36 @@ def anneal(P: Instance, R, T, seed, inst_id, beta0, beta1, eps, gamma, refresh=0
                 proposed=np.array([o.proposed for o in outs], dtype=np.int64),
                 accepted=np.array([o.accepted for o in outs], dtype=np.int64),
                 best_s=best_s)
+
+
+def gahmc_cross_time(x0, v0, s) -> float:
+    """Time in [0, pi] at which x0 cos t + v0 sin t leaves the orthant of sign s."""
+    return float(_load().orc_gahmc_cross_time(float(x0), float(v0), int(s)))
+
+
+def gahmc_replica(P: Instance, K, seed, inst_id, r, beta0, beta1, travel, target=None, x0=None, v0=None,
+                  events_cap=0):
+    """One replica of vanilla GAHMC (exact zero crossings, Sec. 2.1 / 3.2) in FP64: K
+    trajectories of time `travel`.  Returns best_e, best_traj, crossings, reflections,
+    hit_traj, best_s, x, v, s and (events_cap > 0) the first events: j for a crossing of
+    spin j, -(j + 1) for a reflection."""
+    S = _GahmcSched(float(beta0), float(beta1), float(travel), int(K), 0 if target is None else 1, 0,
+                    0 if target is None else int(target))
+    out = _GahmcOut()
+    n = P.n
+    best_s = np.zeros(n, dtype=np.int8)
+    s = np.zeros(n, dtype=np.int8)
+    xo, vo = np.empty(n), np.empty(n)
+    ev = np.full(max(events_cap, 1), np.iinfo(np.int32).min, dtype=np.int32)
+    x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+    v0a = None if v0 is None else np.ascontiguousarray(v0, dtype=np.float64)
+    _load().orc_gahmc_replica(ctypes.byref(P._c), P.frac_bits, ctypes.byref(S), seed & (2**64 - 1), inst_id, r,
+                              _ptr(x0a), _ptr(v0a), ctypes.byref(out), _ptr(best_s), _ptr(xo), _ptr(vo), _ptr(s),
+                              _ptr(ev) if events_cap > 0 else None, int(events_cap))
+    nev = out.crossings + out.reflections
+    return dict(best_e=out.best_e, best_traj=out.best_traj, crossings=out.crossings, reflections=out.reflections,
+                hit_traj=out.hit_traj, best_s=best_s, x=xo, v=vo, s=s,
+                events=ev[:min(events_cap, nev)] if events_cap > 0 else None)
 
 
 def tts(t1: float, p: float, target_conf: float = 0.99) -> float:

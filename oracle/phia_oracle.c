@@ -17,6 +17,8 @@
  *                state 5: keep the best state seen so far
  *   Sec. 2.1     momentum drawn at random at the start of a trajectory;
  *                position prior g(x) is a standard normal (Eq. A3)
+ *   Sec. 2.1, 3.2  vanilla GAHMC: the exact solution of the dynamics by zero
+ *                crossings (the method PHIA approximates; the paper's ablation)
  *
  * Fixed point (Sec. 2.2, coefficients held as fixed-point constants):
  * J_ij = k_ij * q and h_i = kh_i * q with q = 2^-f, int8 k and int32 kh.
@@ -419,4 +421,162 @@ void orc_anneal_replicas(const orc_inst *P, int32_t frac_bits, const orc_sched *
     for (int t = 0; t < threads; ++t) pthread_join(tid[t], NULL);
     free(tid);
     pthread_mutex_destroy(&pool.mu);
+}
+
+/* ---------------------------------------------------------- vanilla GAHMC */
+
+/* The exact solution of the dynamics of H(x, v) = beta E(sgn x) + x.x/2 + v.v/2 (Eq. 4,
+ * App. A) by zero crossings -- the Gaussian-augmented HMC of the paper's reference
+ * [Pakman & Paninski 2013] that Sec. 2.1 names as the exact alternative to the
+ * approximate gradient and Sec. 3.2 uses as an ablation.
+ *
+ * Inside an orthant sgn x = s is fixed and the potential is x.x/2 (+ a constant), so each
+ * coordinate moves on the unit circle: x_i(t) = x_i cos t + v_i sin t,
+ * v_i(t) = -x_i sin t + v_i cos t.  When x_j reaches 0 the potential would jump by
+ * dU = beta q dE with dE = E(s with s_j flipped) - E(s) = 2 s_j I_j (Eqs. 2, 6; units of
+ * q).  Energy conservation decides: the speed there is A_j = sqrt(x_j^2 + v_j^2); if
+ * A_j^2 / 2 > dU the coordinate crosses into the other orthant with speed
+ * sqrt(A_j^2 - 2 dU) (s_j flips, the field follows), else it is reflected (speed A_j,
+ * direction reversed).  Either way x_j = 0 afterwards, so its next zero is exactly pi
+ * later: with a travel time <= pi each coordinate meets the wall at most once per
+ * trajectory, at the time its start state fixes.  The events are taken in time order
+ * (ties: lower index first); each decision uses the field left by the earlier ones.
+ *
+ * A run: the initial draw (Philox d = 0, as PHIA), then `trajectories` trajectories of
+ * time `travel` each; trajectory k > 0 starts with the momentum draw d = k; beta is
+ * linear from beta0 (k = 0) to beta1 (k = K - 1).  The best energy over every state
+ * visited (the initial one and one per crossing) is kept with strict improvement;
+ * best_traj is the trajectory in which it was first reached (0 for the initial state). */
+typedef struct {
+    double beta0, beta1;
+    double travel;          /* time per trajectory, 0 < travel <= pi */
+    int64_t trajectories;
+    int32_t has_target;
+    int32_t pad;
+    int64_t target;
+} orc_gahmc_sched;
+
+typedef struct {
+    int64_t best_e;
+    int64_t best_traj;
+    int64_t crossings;
+    int64_t reflections;
+    int64_t hit_traj;       /* first trajectory reaching E <= target (0: the initial state), or -1 */
+} orc_gahmc_out;
+
+/* First time t in [0, pi] at which x(t) = x0 cos t + v0 sin t leaves the orthant of sign
+ * s (the zero of x with x moving from sign s to -s). */
+double orc_gahmc_cross_time(double x0, double v0, int8_t s)
+{
+    /* x(t) = 0 where (cos t, sin t) is parallel to (v0, -x0); of the two roots per period
+     * the one where x goes from s to -s has s * v(t) < 0. */
+    return s > 0 ? atan2(x0, -v0) : atan2(-x0, v0);
+}
+
+void orc_gahmc_replica(const orc_inst *P, int32_t frac_bits, const orc_gahmc_sched *S, uint64_t seed,
+                       uint32_t inst_id, uint32_t r, const double *x0, const double *v0, orc_gahmc_out *out,
+                       int8_t *best_s, double *x_out, double *v_out, int8_t *s_out, int32_t *events,
+                       int64_t events_cap)
+{
+    int n = P->n;
+    double q = ldexp(1.0, -frac_bits);
+    double *x = (double *)malloc(sizeof(double) * (size_t)n);
+    double *v = (double *)malloc(sizeof(double) * (size_t)n);
+    double *tev = (double *)malloc(sizeof(double) * (size_t)n);
+    double *vnew = (double *)malloc(sizeof(double) * (size_t)n);
+    int *order = (int *)malloc(sizeof(int) * (size_t)n);
+    int8_t *s = (int8_t *)malloc((size_t)n);
+    int64_t *I = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    for (int j = 0; j < n; ++j) {
+        if (x0 && v0) {
+            x[j] = x0[j];
+            v[j] = v0[j];
+        } else {
+            orc_draw(seed, inst_id, r, (uint32_t)j, 0u, &x[j], &v[j]);
+        }
+        s[j] = orc_sgn(x[j]);
+    }
+    orc_field(P, s, I);
+    int64_t e = orc_energy_exact(P, s);
+    out->best_e = e;
+    out->best_traj = 0;
+    out->crossings = 0;
+    out->reflections = 0;
+    out->hit_traj = (S->has_target && e <= S->target) ? 0 : -1;
+    if (best_s) memcpy(best_s, s, (size_t)n);
+    int64_t nev = 0;
+    int64_t K = S->trajectories;
+    double T = S->travel;
+    for (int64_t k = 0; k < K; ++k) {
+        if (k > 0)
+            for (int j = 0; j < n; ++j) orc_draw(seed, inst_id, r, (uint32_t)j, (uint32_t)k, NULL, &v[j]);
+        double beta = K > 1 ? S->beta0 + (S->beta1 - S->beta0) * (double)k / (double)(K - 1) : S->beta0;
+        /* event times of this trajectory, in order (insertion sort: plain and stable) */
+        int m = 0;
+        for (int j = 0; j < n; ++j) {
+            tev[j] = orc_gahmc_cross_time(x[j], v[j], s[j]);
+            vnew[j] = 0.0;
+            if (tev[j] < T) {
+                int p = m++;
+                while (p > 0 && (tev[order[p - 1]] > tev[j])) {
+                    order[p] = order[p - 1];
+                    --p;
+                }
+                order[p] = j;
+            }
+        }
+        for (int a = 0; a < m; ++a) {
+            int j = order[a];
+            double A = sqrt(x[j] * x[j] + v[j] * v[j]);      /* speed at the wall */
+            int64_t dE = 2 * (int64_t)s[j] * I[j];             /* flip identity (Eqs. 2, 6) */
+            double dU = beta * q * (double)dE;
+            if (0.5 * A * A > dU) {
+                int8_t sn = (int8_t)(-s[j]);
+                vnew[j] = (double)sn * sqrt(A * A - 2.0 * dU);  /* moving into the orthant of sn */
+                s[j] = sn;
+                for (int i = 0; i < n; ++i) {
+                    int64_t kij;
+                    if (P->k) {
+                        kij = P->k[(int64_t)i * n + j];
+                    } else {
+                        kij = 0;
+                        for (int32_t p2 = P->row_ptr[i]; p2 < P->row_ptr[i + 1]; ++p2)
+                            if (P->col[p2] == j) kij = P->val[p2];
+                    }
+                    I[i] += 2 * kij * sn;
+                }
+                e += dE;
+                out->crossings += 1;
+                if (events && nev < events_cap) events[nev] = j;
+                if (e < out->best_e) {
+                    out->best_e = e;
+                    out->best_traj = k;
+                    if (best_s) memcpy(best_s, s, (size_t)n);
+                }
+                if (S->has_target && out->hit_traj < 0 && e <= S->target) out->hit_traj = k;
+            } else {
+                vnew[j] = (double)s[j] * A;                      /* reflected back into its orthant */
+                out->reflections += 1;
+                if (events && nev < events_cap) events[nev] = -(j + 1);
+            }
+            ++nev;
+        }
+        /* every coordinate to the end of the trajectory */
+        for (int j = 0; j < n; ++j) {
+            if (tev[j] < T) {
+                double u = T - tev[j];
+                x[j] = vnew[j] * sin(u);
+                v[j] = vnew[j] * cos(u);
+            } else {
+                double xj = x[j] * cos(T) + v[j] * sin(T);
+                double vj = -x[j] * sin(T) + v[j] * cos(T);
+                x[j] = xj;
+                v[j] = vj;
+            }
+        }
+    }
+    if (x_out) memcpy(x_out, x, sizeof(double) * (size_t)n);
+    if (v_out) memcpy(v_out, v, sizeof(double) * (size_t)n);
+    if (s_out) memcpy(s_out, s, (size_t)n);
+    free(x); free(v); free(tev); free(vnew); free(order); free(s); free(I);
 }

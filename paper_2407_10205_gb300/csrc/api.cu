@@ -830,6 +830,43 @@ int phia_best(phia_t *p, int64_t *energy_k, int8_t *spins) {
     return PHIA_OK;
 }
 
+int phia_gahmc(phia_t *p, const phia_gahmc_schedule *sched, int32_t R, int64_t K, uint64_t seed, float *x, float *v,
+               int64_t *counts, int32_t *events, int32_t events_cap) {
+    if (!p || !sched) return fail(PHIA_EINVAL, "NULL argument");
+    if (p->batch) return fail(PHIA_ENOTSUP, "GAHMC runs on dense handles");
+    if (p->N > gahmc_max_n()) return fail(PHIA_ENOTSUP, "GAHMC handles N <= %d (N = %d)", gahmc_max_n(), p->N);
+    if (R < 1 || K < 1) return fail(PHIA_EINVAL, "need replicas >= 1 and trajectories >= 1");
+    if (K > ((int64_t)1 << 31)) return fail(PHIA_ERANGE, "trajectories must be < 2^31 (Philox counter word)");
+    if (!(sched->travel > 0.0f) || !(sched->travel <= 3.14159265f))
+        return fail(PHIA_EINVAL, "travel must be in (0, pi]");
+    if (!(sched->beta0 >= 0.0f) || !(sched->beta1 >= 0.0f)) return fail(PHIA_EINVAL, "beta0 and beta1 must be >= 0");
+    if (events && events_cap < 1) return fail(PHIA_EINVAL, "events_cap must be >= 1 with an events array");
+    CU(cudaSetDevice(p->device));
+    int rc = ensure_replicas(p, R);
+    if (rc) return rc;
+    rc = reset_records(p, R);
+    if (rc) return rc;
+    CU(cudaMemsetAsync(p->d_iters, 0, 8, p->stream));
+    CU(cudaMemsetAsync(p->d_err, 0, 4, p->stream));
+    CU(cudaMemsetAsync(p->d_prop, 0, (size_t)R * 8, p->stream));
+    CU(cudaMemsetAsync(p->d_acc, 0, (size_t)R * 8, p->stream));
+    RunArgs a = base_args(p, R);
+    a.beta0 = sched->beta0; a.beta1 = sched->beta1;
+    a.seed = seed;
+    a.x_in = x; a.v_in = v; a.x_out = x; a.v_out = v;
+    a.has_target = sched->has_target; a.target = sched->target_k;
+    CU(cudaEventRecord(p->ev0, p->stream));
+    cudaError_t e = launch_gahmc(a, sched->travel, K, counts, events, events_cap, p->stream);
+    if (e != cudaSuccess) return fail(PHIA_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    CU(cudaEventRecord(p->ev1, p->stream));
+    p->ran = true;
+    p->R_last = R;
+    p->last_steps = K;
+    p->last_launches = 2;
+    p->last_stop = 0;
+    return PHIA_OK;
+}
+
 int phia_acceptance(phia_t *p, int32_t R, int64_t *proposed, int64_t *accepted) {
     if (!p) return fail(PHIA_EINVAL, "handle is NULL");
     if (p->batch) return fail(PHIA_ENOTSUP, "the acceptance test does not run on the CSR path");

@@ -211,6 +211,11 @@ struct Fp32Metro {
 cudaError_t launch_fp32_run(const RunArgs &a, float *x, float *v, int8_t *s0, int8_t *s1,
                             int64_t *e_acc, const Fp32Metro &metro, cudaStream_t st, int *launches);
 
+// Vanilla GAHMC (exact zero crossings), one warp per replica; records into a's arrays.
+int gahmc_max_n();
+cudaError_t launch_gahmc(const RunArgs &a, float travel, int64_t K, int64_t *counts, int32_t *events,
+                         int32_t events_cap, cudaStream_t st);
+
 // Philox draws for testing.
 cudaError_t launch_philox_draws(uint64_t seed, uint32_t inst, uint32_t d, int R, int N, uint32_t *raw,
                                 float *x, float *v, cudaStream_t st);

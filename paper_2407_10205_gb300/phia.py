@@ -80,6 +80,16 @@ class ServerStats(ctypes.Structure):
                 ("ttt_admit_p99_s", ctypes.c_double), ("elapsed_s", ctypes.c_double), ("used_bytes", ctypes.c_int64)]
 
 
+class GahmcSchedule(ctypes.Structure):
+    _fields_ = [("beta0", ctypes.c_float), ("beta1", ctypes.c_float), ("travel", ctypes.c_float),
+                ("has_target", ctypes.c_int32), ("target_k", ctypes.c_int64)]
+
+
+def gahmc_schedule(beta0, beta1, travel=1.5707963267948966, target=None) -> GahmcSchedule:
+    return GahmcSchedule(float(beta0), float(beta1), float(travel), 0 if target is None else 1,
+                         0 if target is None else int(target))
+
+
 class TuneResult(ctypes.Structure):
     _fields_ = [("tc_kernel", ctypes.c_int32), ("tile_replicas", ctypes.c_int32), ("coupling_mem", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("best_us_per_iter", ctypes.c_float),
@@ -98,6 +108,8 @@ SIGNATURES = {
     "phia_stats_get": (ctypes.c_int, [_P, _P]),
     "phia_replica_results": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P]),
     "phia_acceptance": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "phia_gahmc": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, _P, _P, _P, _P,
+                                  ctypes.c_int32]),
     "phia_run": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                 ctypes.c_uint64, _P, _P, ctypes.c_int32]),
     "phia_init_state": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint64, _P, _P]),
@@ -264,6 +276,14 @@ def replica_results(h, replicas: int, n: int):
     bits = np.empty((replicas, W), dtype=np.uint32)
     _check(load().phia_replica_results(h, int(replicas), _np_ptr(be), _np_ptr(bs), _np_ptr(hs), _np_ptr(bits)))
     return be, bs, hs, bits
+
+
+def gahmc(h, sched: GahmcSchedule, replicas, trajectories, seed, x=None, v=None, counts=None, events=None):
+    """phia_gahmc: vanilla GAHMC (exact zero crossings) on a dense handle.  x, v, counts,
+    events: optional device tensors ([R][N] float32, [R][2] int64, [R][cap] int32)."""
+    cap = int(events.shape[1]) if events is not None else 0
+    _check(load().phia_gahmc(h, ctypes.byref(sched), int(replicas), int(trajectories), int(seed) & (2**64 - 1),
+                             _dev_ptr(x), _dev_ptr(v), _dev_ptr(counts), _dev_ptr(events), cap))
 
 
 def acceptance(h, replicas: int):

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PAIRS = [("phia_opts", phia.Opts), ("phia_schedule", phia.Schedule), ("phia_stats", phia.Stats),
          ("phia_tune_result", phia.TuneResult), ("phia_instance_desc", phia.InstanceDesc),
          ("phia_server_opts", phia.ServerOpts), ("phia_request_status", phia.RequestStatus),
-         ("phia_server_stats", phia.ServerStats)]
+         ("phia_server_stats", phia.ServerStats), ("phia_gahmc_schedule", phia.GahmcSchedule)]
 
 
 def test_struct_layouts_match_the_header(tmp_path):

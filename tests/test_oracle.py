@@ -449,3 +449,81 @@ def test_metropolis_beta_zero_acceptance_tends_to_one():
         res = o.anneal(P, 32, 201, 5, 0, 0.0, 0.0, eps, 2.0, refresh=4, accept_test=1)
         rates[eps] = res["accepted"].sum() / res["proposed"].sum()
     assert rates[0.001] >= 0.99 and rates[0.8] < rates[0.001]
+
+
+# ------------------------------------------------------------------ vanilla GAHMC (exact zero crossings)
+
+def test_gahmc_two_spin_hand_case():
+    g = read_golden("gahmc_two_spin.txt")
+    k = np.array(g["k"].split(), dtype=np.int8).reshape(2, 2)
+    P = _dense(k, [0, 0])
+    x0, v0 = f64(g["x0"]), f64(g["v0"])
+    tc = f64(g["t_cross"])
+    assert abs(o.gahmc_cross_time(x0[0], v0[0], 1) - tc[0]) < 1e-9
+    assert abs(o.gahmc_cross_time(x0[1], v0[1], -1) - tc[1]) < 1e-9
+    b = float(g["beta"])
+    res = o.gahmc_replica(P, 1, 0, 0, 0, b, b, float(g["travel"]), x0=x0, v0=v0, events_cap=8)
+    assert list(res["events"]) == [int(t) for t in g["events"].split()]
+    assert np.allclose(res["x"], f64(g["x_end"]), atol=2e-9) and np.allclose(res["v"], f64(g["v_end"]), atol=2e-9)
+    assert list(res["s"]) == [int(t) for t in g["s_end"].split()]
+    assert res["best_e"] == int(g["best_e"]) and res["best_traj"] == 0
+    assert res["crossings"] == 1 and res["reflections"] == 1
+
+
+def test_gahmc_one_spin_threshold():
+    """One spin in a field h = 1 (E = -s): leaving s = +1 costs dE = 2, so the wall is
+    crossed exactly when A^2 / 2 > 2 beta (A = speed at the wall, here 1)."""
+    P = o.Instance(np.array([1], dtype=np.int32), k=np.zeros((1, 1), dtype=np.int8))
+    for beta, crosses in ((0.2, True), (0.24, True), (0.26, False), (1.0, False)):
+        res = o.gahmc_replica(P, 1, 0, 0, 0, beta, beta, 3.0, x0=[1.0], v0=[0.0], events_cap=2)
+        assert list(res["events"]) == ([0] if crosses else [-1])
+        w = -math.sqrt(1.0 - 4 * beta) if crosses else 1.0          # outgoing velocity
+        u = 3.0 - math.pi / 2
+        assert abs(res["x"][0] - w * math.sin(u)) < 1e-12 and abs(res["v"][0] - w * math.cos(u)) < 1e-12
+
+
+def test_gahmc_beta_zero_is_free_rotation():
+    """beta = 0: no potential step, every wall is crossed at unchanged speed, so each
+    coordinate rotates freely: x(T) = x cos T + v sin T, v(T) = -x sin T + v cos T, and
+    the spins end as sgn x(T)."""
+    d = ins.dense_int(12, 5, 5, seed=6)
+    P = _dense(d.k, d.kh)
+    g = np.random.default_rng(1)
+    x0, v0 = g.standard_normal(12), g.standard_normal(12)
+    T = 2.2
+    res = o.gahmc_replica(P, 1, 0, 0, 0, 0.0, 0.0, T, x0=x0, v0=v0)
+    assert np.allclose(res["x"], x0 * math.cos(T) + v0 * math.sin(T), atol=1e-12)
+    assert np.allclose(res["v"], -x0 * math.sin(T) + v0 * math.cos(T), atol=1e-12)
+    assert np.array_equal(res["s"], np.where(res["x"] >= 0, 1, -1)) and res["reflections"] == 0
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_gahmc_conserves_h_within_a_trajectory(seed):
+    """App. A: the exact dynamics conserve H = beta E(sgn x) + x.x/2 + v.v/2 (Eq. 4):
+    across one trajectory (fixed beta, no momentum draw) H at the end equals H at the
+    start, crossings and reflections included; the tracked energy equals Eq. 2."""
+    d = ins.dense_int(20, 7, 7, seed=10 + seed)
+    P = _dense(d.k, d.kh, f=2)
+    g = np.random.default_rng(seed)
+    x0, v0 = g.standard_normal(20), 2.0 * g.standard_normal(20)
+    beta = 0.4
+    s0 = np.where(x0 >= 0, 1, -1).astype(np.int8)
+    h0 = o.hamiltonian(beta, P.q, o.energy_exact(P, s0), x0, v0)
+    res = o.gahmc_replica(P, 1, 0, 0, 0, beta, beta, math.pi, x0=x0, v0=v0)
+    assert res["crossings"] > 0 and res["reflections"] > 0
+    e_end = o.energy_exact(P, res["s"])
+    assert abs(o.hamiltonian(beta, P.q, e_end, res["x"], res["v"]) - h0) < 1e-10
+    assert o.energy_exact(P, res["best_s"]) == res["best_e"] <= o.energy_exact(P, s0)
+
+
+def test_gahmc_run_reaches_ground_state_and_keeps_consistent_records():
+    d = ins.sk_pm1(16, 0)
+    P = _dense(d.k, d.kh)
+    emin, _, _ = o.brute_force(P)
+    hits = 0
+    for r in range(16):
+        res = o.gahmc_replica(P, 200, 3, 0, r, 0.05, 1.5, math.pi / 2, target=emin)
+        assert res["best_e"] >= emin and o.energy_exact(P, res["best_s"]) == res["best_e"]
+        hits += res["best_e"] == emin
+        assert (res["hit_traj"] >= 0) == (res["best_e"] == emin)
+    assert hits >= 8
