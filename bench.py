@@ -73,12 +73,16 @@ WORKLOADS = {
                             "(k ~ U[-127,127]), h = k/16 (k ~ U[-31,31]); 256 replicas each x 2000 iterations, "
                             "one batch",
                        cmp_instances=8, cmp_iters=20, cpu_instances=4, cpu_iters=50),
-    # time-to-solution scaling of PHIA alone (Eq. 9) on SK instances of growing n
-    "tts": dict(kind="tts", sizes=(8, 16, 32, 64, 128, 256, 512, 1024), instances=20, replicas=256,
-                iterations=1000, ref_replicas=1024, ref_factor=20, seed=9,
-                name="TTS99 scaling: SK instances (J in {-1,+1}, h = 0), n = 8..1024, 20 instances per n; "
-                     "256 replicas x 1000 max(1, n/128) iterations against the best of 1024 replicas x 20 times "
-                     "as many"),
+    # time-to-solution scaling (Eq. 9) of PHIA on the seven Table 2 families, n = 8..1024,
+    # 100 instances per n; vanilla GAHMC on the same sk_ising instances for the Sec. 3.2
+    # ablation
+    "tts": dict(kind="tts", sizes=(8, 16, 32, 64, 128, 256, 512, 1024), instances=100, replicas=256,
+                iterations=1000, ref_replicas=1024, ref_factor=4, streams=8, jump=6.0,
+                gahmc_family="sk_ising", gahmc_sizes=(8, 16, 32, 64, 128, 256), gahmc_trajectories=200,
+                name="TTS99 scaling on the Table 2 families (maxcut_dense, maxcut_d3, sk_bool, sk_ising, "
+                     "sk_uniform, nae_3_sat, spin_model), n = 8..1024, 100 instances per n; 256 replicas x "
+                     "1000 max(1, n/128) iterations; optimum: exhaustive for n <= 16, planted for nae_3_sat, "
+                     "else the best of the run and of 1024 replicas x 4 times as many iterations"),
     # serving stream, Poisson arrivals at 200/s over a pool of seeded instances
     "serving": dict(kind="serving", pool=32, pool_seed=5, requests=400, arrival_seed=11, rate_hz=200.0,
                     replicas=256, step_cap=5000, max_inflight=64, budget_gb=64, chunk_iters=200,
@@ -578,45 +582,139 @@ def tts99(t1, p):
     return t1 * math.log(1.0 - 0.99) / math.log(1.0 - p)
 
 
+def _tts_optima():
+    with open(os.path.join(ROOT, "tests", "golden", "tts_optima.json")) as f:
+        return json.load(f)["optima"]
+
+
 def run_tts(args, w):
-    """Time to solution (Eq. 9, 99% confidence) of PHIA alone against n on SK instances.
-    Per instance: the reference energy is the best found by a long run (ref_replicas x
-    ref_factor * iterations); P is the fraction of the short run's replicas whose best
-    energy reaches it; T1 is the short run's device time divided by its replicas (the
-    replicas run concurrently, so this is the time one run costs at full occupancy).
-    Reported per n: medians over the instances."""
+    """Time to solution (Eq. 9, 99% confidence) against n on the Table 2 families.
+    Per instance: P = the fraction of the short run's replicas whose best energy reaches
+    the optimum (exhaustive for n <= 16 -- computed by the oracle's brute force and stored
+    under tests/golden --, planted for nae_3_sat, else the best of the short run and of a
+    run with 4x the replicas and 4x the iterations); T1 = device time of the short run,
+    timed alone on the first instance of each (family, n), divided by its replicas (the
+    replicas run concurrently: the time one run costs at full occupancy).  Instances run
+    w["streams"] at a time on their own streams.  Reported per (family, n): the median
+    TTS99 over instances (null when P = 0 for at least half of them), the number of
+    instances with P > 0 and the mean P.  GAHMC (exact zero crossings, phia_gahmc) runs on
+    the same instances of one family for the Sec. 3.2 ablation, with its own T1."""
     import torch
     from paper_2407_10205_gb300 import phia, instances as ins, schedules
-    rows = []
+    fams = args.tts_families.split(",") if args.tts_families else sorted(ins.FAMILIES)
+    sizes = tuple(int(t) for t in args.tts_sizes.split(",")) if args.tts_sizes else w["sizes"]
+    n_inst = args.tts_instances or w["instances"]
+    jump = args.tts_jump or w["jump"]
+    optima = _tts_optima()
+    S = w["streams"]
+    streams = [torch.cuda.Stream() for _ in range(S)]
+    R, Rr = w["replicas"], w["ref_replicas"]
     t_start = time.perf_counter()
-    for n in w["sizes"]:
-        ps, ttss, t1s = [], [], []
-        T = w["iterations"] * max(1, n // 128)
-        for k in range(w["instances"]):
-            d = ins.sk_pm1(n, w["seed"] * 100_003 + n * 1000 + k)
-            b0, b1, eps, gamma, refresh = schedules.suggest_schedule(d)
-            sched = phia.schedule(b0, b1, eps, gamma, refresh=refresh)
-            with phia.Annealer(d.k, d.kh, path=phia.PATH_TC) as A:
-                A.anneal(sched, w["ref_replicas"], T * w["ref_factor"], 1 + k)
-                ref, _ = phia.best(A.h, n)
-                phia.anneal(A.h, sched, w["replicas"], T, 7_777 + k)
-                st = phia.stats_get(A.h)
-                be, _, _, _ = phia.replica_results(A.h, w["replicas"], n)
-            p = float(np.mean(be <= ref))
-            t1 = st.device_ms * 1e-3 / w["replicas"]
-            tts = tts99(t1, p)
-            ps.append(p); ttss.append(tts); t1s.append(t1)
-        med = float(np.median(ttss))
-        rows.append({"n": n, "iterations": T, "instances": w["instances"], "p_median": float(np.median(ps)),
-                     "p_min": float(np.min(ps)), "t1_s": float(np.median(t1s)),
-                     "tts99_s_median": med if math.isfinite(med) else None,
-                     "solved_instances": int(np.sum(np.array(ps) > 0))})
-    line = {"metric": "TTS99 (median over instances; null = not reached)", "value": rows[-1]["tts99_s_median"],
-            "unit": "s",
+    rows = []
+
+    def schedule_of(d):
+        b0, b1, eps, gamma, refresh = schedules.suggest_schedule(d, jump=jump)
+        return phia.schedule(b0, b1, eps, gamma, refresh=refresh)
+
+    for fam in fams:
+        for n in sizes:
+            T = w["iterations"] * max(1, n // 128)
+            insts = [ins.family_instance(fam, n, ins.tts_seed(fam, n, k)) for k in range(n_inst)]
+            # T1: the short run alone
+            d0 = insts[0]
+            with phia.Annealer(d0.k, d0.kh, frac_bits=d0.frac_bits, path=phia.PATH_TC) as A:
+                sch = schedule_of(d0)
+                phia.anneal(A.h, sch, R, T, 1)
+                phia.sync(A.h)
+                phia.anneal(A.h, sch, R, T, 1)
+                t1 = phia.stats_get(A.h).device_ms * 1e-3 / R
+            ps, opt_src = [], set()
+            for g0 in range(0, n_inst, S):
+                group = list(range(g0, min(n_inst, g0 + S)))
+                hs = []
+                for j, k in enumerate(group):
+                    d = insts[k]
+                    A = phia.Annealer(d.k, d.kh, frac_bits=d.frac_bits, path=phia.PATH_TC,
+                                      stream=streams[j].cuda_stream)
+                    sch = schedule_of(d)
+                    known = None
+                    if n <= 16:
+                        known = optima[f"{fam}/{n}"][k]
+                    elif isinstance(d, ins.Planted):
+                        known = d.optimum_k
+                    phia.anneal(A.h, sch, R, T, 7_777 + k)
+                    hs.append((A, sch, known, k))
+                res = []
+                for A, sch, known, k in hs:
+                    be, _, _, _ = phia.replica_results(A.h, R, n)
+                    res.append(be)
+                for (A, sch, known, k) in hs:
+                    if known is None:
+                        phia.anneal(A.h, sch, Rr, T * w["ref_factor"], 1 + k)
+                for j, (A, sch, known, k) in enumerate(hs):
+                    be = res[j]
+                    if known is None:
+                        ref, _ = phia.best(A.h, n)
+                        opt = min(int(ref), int(be.min()))
+                        opt_src.add("best found")
+                    else:
+                        opt = int(known)
+                        opt_src.add("exhaustive" if n <= 16 else "planted")
+                        assert be.min() >= opt, "an energy below the exact optimum"
+                    ps.append(float(np.mean(be <= opt)))
+                    A.close()
+            ttss = [tts99(t1, p) for p in ps]
+            med = float(np.median(ttss))
+            rows.append({"family": fam, "n": n, "iterations": T, "instances": n_inst,
+                         "p_mean": float(np.mean(ps)), "p_median": float(np.median(ps)),
+                         "solved_instances": int(np.sum(np.array(ps) > 0)), "t1_s": t1,
+                         "tts99_s_median": med if math.isfinite(med) else None,
+                         "optimum": "/".join(sorted(opt_src))})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    # GAHMC ablation (Sec. 3.2) on one family's instances
+    gam = []
+    gfam = w["gahmc_family"]
+    for n in (w["gahmc_sizes"] if not args.tts_sizes else [m for m in sizes if m <= 1024]):
+        if args.tts_families and gfam not in fams:
+            break
+        K = w["gahmc_trajectories"] * max(1, n // 32)
+        insts = [ins.family_instance(gfam, n, ins.tts_seed(gfam, n, k)) for k in range(n_inst)]
+        ps, t1 = [], None
+        phia_row = next((r for r in rows if r["family"] == gfam and r["n"] == n), None)
+        for k, d in enumerate(insts):
+            b0, b1, _, _, _ = schedules.suggest_schedule(d, jump=jump)
+            gs = phia.gahmc_schedule(b0, b1, math.pi / 2)
+            with phia.Annealer(d.k, d.kh, frac_bits=d.frac_bits, path=phia.PATH_TC) as A:
+                phia.gahmc(A.h, gs, R, K, 5_555 + k)
+                be, _, _, _ = phia.replica_results(A.h, R, n)
+                if t1 is None:
+                    phia.gahmc(A.h, gs, R, K, 5_555 + k)
+                    t1 = phia.stats_get(A.h).device_ms * 1e-3 / R
+                    be, _, _, _ = phia.replica_results(A.h, R, n)
+                if n <= 16:
+                    opt = optima[f"{gfam}/{n}"][k]
+                else:
+                    # the PHIA study's reference for the same instance is not kept per instance:
+                    # use the best of this GAHMC run and a PHIA reference run
+                    sch = schedule_of(d)
+                    phia.anneal(A.h, sch, Rr, w["iterations"] * max(1, n // 128) * w["ref_factor"], 1 + k)
+                    ref, _ = phia.best(A.h, n)
+                    opt = min(int(ref), int(be.min()))
+                ps.append(float(np.mean(be <= opt)))
+        med = float(np.median([tts99(t1, p) for p in ps]))
+        row = {"family": gfam, "n": n, "trajectories": K, "travel": "pi/2", "p_mean": float(np.mean(ps)),
+               "solved_instances": int(np.sum(np.array(ps) > 0)), "t1_s": t1,
+               "tts99_s_median": med if math.isfinite(med) else None}
+        if phia_row and phia_row["tts99_s_median"] and row["tts99_s_median"]:
+            row["tts_ratio_gahmc_over_phia"] = row["tts99_s_median"] / phia_row["tts99_s_median"]
+        gam.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    line = {"metric": "TTS99 (median over instances; null = not reached)",
+            "value": rows[-1]["tts99_s_median"] if rows else None, "unit": "s",
             "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "dtype": "fp32",
-            "config": {"workload": w["name"], "replicas": w["replicas"],
-                       "reference": f"best of {w['ref_replicas']} replicas x {w['ref_factor']} times the iterations"},
-            "table": rows, "wall_s": time.perf_counter() - t_start}
+            "config": {"workload": w["name"], "replicas": R, "jump": jump,
+                       "reference": f"best of {Rr} replicas x {w['ref_factor']} times the iterations"},
+            "table": rows, "gahmc": gam, "wall_s": time.perf_counter() - t_start}
     print(json.dumps(line))
     return 0
 
@@ -715,7 +813,7 @@ def measure_dense(args, w, rank=0, world=1, local=0, with_cpu=True, dist=None):
                    "autotune": {"tc_kernel": tune.tc_kernel, "tile_replicas": tune.tile_replicas,
                                 "coupling_mem": tune.coupling_mem, "candidates": tune.candidates,
                                 "best_us_per_iter": tune.best_us_per_iter,
-                                "worst_us_per_iter": tune.worst_us_per_iter},
+                                "worst_us_per_iter": tune.worst_us_per_iter, "large_variant": tune.large_variant},
                    "field_operand": ("e4m3" if st.operand == 1 else "bf16")
                    + " (exact re-encoding of int8 k), fp32 accumulation of integer products",
                    "state": "fp32 x, v", "l2": "flushed between timed steps (256 MB write)",
@@ -804,6 +902,10 @@ def main():
     ap.add_argument("--max-inflight", type=int, default=0, help="serving: request slots (0 = the workload's)")
     ap.add_argument("--chunk-iters", type=int, default=0, help="serving: iterations per chunk (0 = the workload's)")
     ap.add_argument("--no-comparator", action="store_true", help="serving: skip the FP32 comparator runs")
+    ap.add_argument("--tts-sizes", default="", help="tts: comma-separated sizes (default: the workload's)")
+    ap.add_argument("--tts-families", default="", help="tts: comma-separated families (default: all seven)")
+    ap.add_argument("--tts-instances", type=int, default=0, help="tts: instances per (family, n)")
+    ap.add_argument("--tts-jump", type=float, default=0.0, help="tts: schedule heuristic's final jump")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload: skip the other workloads reported under 'also'")
     ap.add_argument("--profile-only", action="store_true",

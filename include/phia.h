@@ -85,7 +85,13 @@ typedef struct phia_opts {
                               (CUDA cores: the exact integer field is updated by the columns of
                               the spins that changed sign, Eq. 6 being linear in s; N <= 384
                               e4m3 / 256 bf16; tile_replicas 4, 8 or 16); 0 = automatic */
-    int32_t reserved;      /* must be 0 */
+    int32_t large_variant; /* per-iteration kernel (tc_kernel 2): 1 = x, v staged through a shared-
+                              memory ring (3 operand stages at 256-wide tiles); 2 = x, v
+                              prefetched into registers (4 stages); 3 / 4 = as 2, with the CTAs of
+                              a cluster of 2 / 4 sharing each replica tile and multicasting the
+                              spin operand to one another (TMA multicast); 5 / 6 = as 1 with the
+                              multicast over 2 / 4 CTAs; 0 = automatic (the autotuner's choice
+                              where it has one) */
 } phia_opts;
 
 /* Annealing schedule.  No values are given in the paper; every field is explicit. */
@@ -188,18 +194,22 @@ int phia_anneal(phia_t *p, const phia_schedule *sched, int32_t replicas, int64_t
  * kernel with 4, 8 or 16 replicas per CTA and J in shared or tensor memory, the
  * resident int8 mma.sync kernel with 8 or 16 replicas per CTA (N small enough), the
  * resident incremental-field kernel with 4, 8 or 16 replicas per CTA (N small enough),
- * and the per-iteration kernel -- keeps the fastest for the handle and caches it,
+ * and the per-iteration kernel in its six variants (phia_opts.large_variant) -- keeps
+ * the fastest for the handle and caches it,
  * process-wide, for (N, replicas, operand): handles created with all variant options
  * automatic use the cached choice for runs with that replica count.  The probes
  * overwrite the handle's last-run records.  Tensor-core path only (else PHIA_ENOTSUP). */
 typedef struct phia_tune_result {
     int32_t tc_kernel;         /* 1 resident tcgen05, 2 per iteration, 3 resident int8 mma.sync,
-                                  4 resident incremental field */
+                                  4 resident incremental field; the per-iteration kernel's variant
+                                  (phia_opts.large_variant) is reported in large_variant */
     int32_t tile_replicas;     /* resident kernel: replicas per CTA */
     int32_t coupling_mem;      /* resident kernel: 1 shared, 2 tensor memory */
     int32_t candidates;        /* variants timed */
     float best_us_per_iter;    /* device time per iteration of the chosen variant */
     float worst_us_per_iter;   /* of the slowest variant */
+    int32_t large_variant;     /* per-iteration kernel: the variant chosen (1..6), 0 otherwise */
+    int32_t reserved;          /* 0 */
 } phia_tune_result;
 
 int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32_t probe_iters,

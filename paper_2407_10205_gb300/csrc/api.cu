@@ -118,6 +118,8 @@ struct phia_s {
     int64_t last_steps = 0;
     int last_launches = 0;
     int last_stop = 0;
+    int large_variant = 0;              // per-iteration kernel variant requested (0 = automatic)
+    int tuned_variant = 0;              // the autotuner's choice for it
     int64_t wait_ns = 0;                // testing aid (phia_debug_wait): device wait bound, 0 = default
     int stall_producer = 0;             // testing aid: the per-iteration kernel's TMA producer issues nothing
 };
@@ -265,6 +267,7 @@ RunArgs base_args(phia_t *p, int R) {
     a.coupling_mem = p->coupling_mem;
     a.wait_ns = p->wait_ns;
     a.stall_producer = p->stall_producer;
+    a.large_variant = p->large_variant ? p->large_variant : p->tuned_variant;
     return a;
 }
 
@@ -280,6 +283,7 @@ struct TuneChoice {
     int tile_rl, coupling_mem;
     bool imma;
     bool inc;
+    int lvar;        // per-iteration kernel variant (large only)
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune;
@@ -314,6 +318,7 @@ int apply_tuned(phia_t *p, int R) {
     p->inc = c.inc;
     p->tile_rl = c.tile_rl;
     p->coupling_mem = c.coupling_mem;
+    p->tuned_variant = c.large ? c.lvar : 0;
     return PHIA_OK;
 }
 
@@ -484,7 +489,7 @@ int create_dense(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N,
     }
     if (o.tc_kernel == 3 && N > imma_small_max_n())
         return fail(PHIA_ENOTSUP, "the int8 mma.sync kernel handles N <= %d (N = %d)", imma_small_max_n(), N);
-    if (o.reserved != 0) return fail(PHIA_EINVAL, "opts.reserved must be 0");
+    if (o.large_variant < 0 || o.large_variant > 6) return fail(PHIA_EINVAL, "large_variant must be 0..6");
     int dev_count = 0;
     if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
         return fail(PHIA_ECUDA, "no CUDA device available");
@@ -498,7 +503,8 @@ int create_dense(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N,
     p->inst = o.instance_id;
     p->tile_rl = o.tile_replicas;
     p->coupling_mem = o.coupling_mem;
-    p->auto_tile = o.tile_replicas == 0 && o.coupling_mem == 0 && o.tc_kernel == 0;
+    p->auto_tile = o.tile_replicas == 0 && o.coupling_mem == 0 && o.tc_kernel == 0 && o.large_variant == 0;
+    p->large_variant = o.large_variant;
     p->N = N;
     p->frac_bits = frac_bits;
     p->W = (N + 31) / 32;
@@ -660,17 +666,17 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
     std::vector<TuneChoice> cands;
     if (p->N <= tc_small_max_n(p->op)) {
         for (int tile : {4, 8, 16})
-            for (int mem : {1, 2}) cands.push_back(TuneChoice{false, tile, mem, false, false});
+            for (int mem : {1, 2}) cands.push_back(TuneChoice{false, tile, mem, false, false, 0});
     }
     if (p->N <= imma_small_max_n()) {
-        cands.push_back(TuneChoice{false, 8, 0, true, false});
-        cands.push_back(TuneChoice{false, 16, 0, true, false});
+        cands.push_back(TuneChoice{false, 8, 0, true, false, 0});
+        cands.push_back(TuneChoice{false, 16, 0, true, false, 0});
     }
     if (p->N <= std::min(inc_small_max_n(), tc_small_max_n(p->op))) {
         for (int tile : {4, 8, 16})
-            if (inc_small_tile_replicas(p->N, tile) == tile) cands.push_back(TuneChoice{false, tile, 0, false, true});
+            if (inc_small_tile_replicas(p->N, tile) == tile) cands.push_back(TuneChoice{false, tile, 0, false, true, 0});
     }
-    cands.push_back(TuneChoice{true, 0, 0, false, false});
+    for (int lv = 1; lv <= 6; ++lv) cands.push_back(TuneChoice{true, 0, 0, false, false, lv});
     const bool saved_auto = p->auto_tile;
     p->auto_tile = false;
     float best_ms = 1e30f, worst_ms = 0.f;
@@ -685,6 +691,7 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
         p->inc = c.inc;
         p->tile_rl = c.tile_rl;
         p->coupling_mem = c.coupling_mem;
+        p->tuned_variant = c.lvar;
         float ms = 0.f;
         for (int rep = 0; rep < 2; ++rep) {   // the first run warms up
             int rc = run_impl(p, sched, replicas, 0, probe_iters, probe_iters, 1, nullptr, nullptr, nullptr, nullptr, 1);
@@ -700,6 +707,7 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
     p->inc = best.inc;
     p->tile_rl = best.tile_rl;
     p->coupling_mem = best.coupling_mem;
+    p->tuned_variant = best.lvar;
     p->auto_tile = saved_auto;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -714,6 +722,7 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
         out->candidates = (int32_t)cands.size();
         out->best_us_per_iter = 1000.f * best_ms / probe_iters;
         out->worst_us_per_iter = 1000.f * worst_ms / probe_iters;
+        out->large_variant = best.large ? best.lvar : 0;
     }
     return PHIA_OK;
 }

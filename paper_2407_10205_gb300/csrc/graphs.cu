@@ -36,10 +36,10 @@ void step_graphs_free(StepGraphCache *c) { delete c; }
 namespace {
 
 std::vector<uint8_t> make_key(const void *func, dim3 grid, dim3 block, size_t smem, int64_t len, const void *key,
-                              size_t key_bytes) {
-    std::vector<uint8_t> k(sizeof(func) + 6 * sizeof(unsigned) + sizeof(smem) + sizeof(len) + key_bytes);
+                              size_t key_bytes, unsigned cluster) {
+    std::vector<uint8_t> k(sizeof(func) + 7 * sizeof(unsigned) + sizeof(smem) + sizeof(len) + key_bytes);
     uint8_t *p = k.data();
-    const unsigned dims[6] = {grid.x, grid.y, grid.z, block.x, block.y, block.z};
+    const unsigned dims[7] = {grid.x, grid.y, grid.z, block.x, block.y, block.z, cluster};
     memcpy(p, &func, sizeof(func)); p += sizeof(func);
     memcpy(p, dims, sizeof(dims)); p += sizeof(dims);
     memcpy(p, &smem, sizeof(smem)); p += sizeof(smem);
@@ -48,7 +48,7 @@ std::vector<uint8_t> make_key(const void *func, dim3 grid, dim3 block, size_t sm
     return k;
 }
 
-cudaError_t build(const void *func, dim3 grid, dim3 block, size_t smem, void **args, int64_t len,
+cudaError_t build(const void *func, dim3 grid, dim3 block, size_t smem, void **args, int64_t len, unsigned cluster,
                   cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaGraphCreate(&g, 0);
@@ -64,6 +64,13 @@ cudaError_t build(const void *func, dim3 grid, dim3 block, size_t smem, void **a
     for (int64_t i = 0; i < len && e == cudaSuccess; ++i) {
         cudaGraphNode_t node;
         e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+        if (e == cudaSuccess && cluster > 1) {
+            cudaKernelNodeAttrValue v{};
+            v.clusterDim.x = cluster;
+            v.clusterDim.y = 1;
+            v.clusterDim.z = 1;
+            e = cudaGraphKernelNodeSetAttribute(node, cudaKernelNodeAttributeClusterDimension, &v);
+        }
         prev = node;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
@@ -73,12 +80,30 @@ cudaError_t build(const void *func, dim3 grid, dim3 block, size_t smem, void **a
 
 }  // namespace
 
+cudaError_t launch_one(const void *func, dim3 grid, dim3 block, size_t smem, void **args, unsigned cluster,
+                       cudaStream_t st) {
+    if (cluster <= 1) return cudaLaunchKernel(func, grid, block, args, smem, st);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, func, args);
+}
+
 cudaError_t launch_steps(StepGraphCache *cache, const void *func, dim3 grid, dim3 block, size_t smem, void **args,
-                         const void *key, size_t key_bytes, int64_t steps, cudaStream_t st) {
+                         const void *key, size_t key_bytes, int64_t steps, cudaStream_t st, unsigned cluster) {
     int64_t done = 0;
     if (cache && steps >= 2) {
         const int64_t len = steps < kGraphLen ? steps : kGraphLen;
-        const std::vector<uint8_t> k = make_key(func, grid, block, smem, len, key, key_bytes);
+        const std::vector<uint8_t> k = make_key(func, grid, block, smem, len, key, key_bytes, cluster);
         cudaGraphExec_t exec = nullptr;
         for (auto &e : cache->entries)
             if (e.key == k) exec = e.exec;
@@ -95,7 +120,7 @@ cudaError_t launch_steps(StepGraphCache *cache, const void *func, dim3 grid, dim
             }
         }
         if (build_now) {
-            cudaError_t e = build(func, grid, block, smem, args, len, &exec);
+            cudaError_t e = build(func, grid, block, smem, args, len, cluster, &exec);
             if (e != cudaSuccess) return e;
             if (cache->entries.size() >= kMaxGraphs) {
                 cudaGraphExecDestroy(cache->entries.front().exec);
@@ -109,7 +134,7 @@ cudaError_t launch_steps(StepGraphCache *cache, const void *func, dim3 grid, dim
         }
     }
     for (; done < steps; ++done) {
-        cudaError_t e = cudaLaunchKernel(func, grid, block, args, smem, st);
+        cudaError_t e = launch_one(func, grid, block, smem, args, cluster, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -3,7 +3,12 @@
 // 128-replica output tiles, each followed by the fused update on that tile.
 //
 // The step kernel is persistent: one CTA per SM walks a static list of output tiles.
-// Operands (K-major, 128-byte swizzle, staged by TMA through a 3-deep mbarrier ring):
+// Variants (autotuned): x and v staged through a shared-memory ring (3 operand stages at
+// 256-wide tiles) or prefetched into registers (4 stages); and the CTAs of a cluster of
+// CL (1, 2 or 4) handling the same replica tile at CL consecutive spin tiles, each
+// loading 1/CL of the spin operand and multicasting it to all CL, so each spin tile is
+// read from L2 once per cluster instead of once per CTA.
+// Operands (K-major, 128-byte swizzle, staged by TMA through an mbarrier ring):
 //   A = couplings k re-encoded exactly (e4m3 or bf16), [Mpad][Kpad]
 //   B = spins of this iteration in the same encoding, [Rpad][Kpad], one of 4 rotating
 //       buffers (iteration t reads buffer t % 4 and writes t+1 % 4; buffers t-1 and t-2
@@ -43,7 +48,9 @@ namespace {
 
 constexpr int kBM = 128;       // output spins per tile (TMEM lanes)
 constexpr int kBKB = 128;      // bytes of K per pipeline stage (one 128-byte swizzle row)
-constexpr int kMaxStages = 4;
+constexpr int kMaxStages = 6;
+// Per-iteration kernel variant used when none is requested (see run_variant).
+constexpr int kDefaultLargeVariant = 1;
 constexpr int kMaxBN = 256;
 constexpr int kEpiWarps = 16;  // four per TMEM lane quadrant, each a quarter of the columns
 constexpr int kEpiThreads = 32 * kEpiWarps;
@@ -66,17 +73,18 @@ struct LargeShared {
 };
 
 // Tile shape: 128 output spins x BN replicas.  BN = 256 halves the coupling-operand
-// traffic per output against BN = 128;
-// BN = 128 keeps more tiles when replicas are few.  With a two-chunk x/v ring the
-// 256-wide tile has room for three operand stages, the 128-wide one for four (more
-// stages in flight outweigh a deeper x/v prefetch).
-template <int BN>
+// traffic per output against BN = 128; BN = 128 keeps more tiles when replicas are few.
+// With the two-chunk x/v ring in shared memory the 256-wide tile has room for three
+// operand stages, the 128-wide one for four; with x/v prefetched into registers instead,
+// four and six.
+template <int BN, bool RING>
 struct Tile {
-    static constexpr int kStages = BN == 256 ? 3 : 4;
+    static constexpr int kStages = RING ? (BN == 256 ? 3 : 4) : (BN == 256 ? 4 : 6);
     static constexpr uint32_t kStageB = BN * kBKB;
     static constexpr int kColsPerWarp = BN / (kEpiWarps / 4);
     static constexpr int kChunksPerTile = kColsPerWarp / kChunk;
-    static constexpr size_t kSmemBytes = 1024 + kStages * (kStageA + kStageB) + 2 * kRingBytes + sizeof(LargeShared);
+    static constexpr size_t kSmemBytes =
+        1024 + kStages * (kStageA + kStageB) + (RING ? 2 * kRingBytes : 0) + sizeof(LargeShared);
     static_assert(kStages <= kMaxStages && BN <= kMaxBN, "tile over the shared bookkeeping");
     static_assert(kSmemBytes <= 232448, "shared memory over the per-CTA limit");
     static_assert(kRing - 1 <= kChunksPerTile, "prefetch reaches at most into the next tile");
@@ -89,6 +97,7 @@ struct LargeArgs {
     int8_t *flags;      // [2][Rpad] improved at an iteration, by parity
     float *X, *V;       // [Rpad/4][Mp][4] state: replica r, spin i at ((r/4) Mp + i) 4 + r%4
     int32_t Kbytes, Rpad, mtiles, ntiles, Mp;
+    int32_t rtiles;     // replica tiles (ntiles = mtiles * rtiles)
     IterCtl *ctl;       // iteration of the launch and range of the run
 };
 
@@ -142,6 +151,23 @@ __device__ __forceinline__ uint32_t plus_bits32(const uint8_t *p) {
     return bits;
 }
 
+// The encoded spins of 8 consecutive spins (e4m3: 8 bytes) or 4 (bf16: 8 bytes) taken
+// from bits [b0, b0 + 8 / ESZ) of a sign mask (bit set: +1), as a 64-bit word.
+// e4m3 +1 / -1 = 0x38 / 0xB8, bf16 +1 / -1 = 0x3F80 / 0xBF80: a set bit clears the sign.
+template <int OP>
+__device__ __forceinline__ uint64_t spin_word(uint32_t mask, int b0) {
+    if constexpr (OP == kOpE4M3) {
+        const uint32_t lo = (mask >> b0) & 0xFu, hi = (mask >> (b0 + 4)) & 0xFu;
+        // bit k of a 4-bit group to bit 8k (the four shifted copies never overlap)
+        const uint32_t slo = (lo * 0x00204081u) & 0x01010101u, shi = (hi * 0x00204081u) & 0x01010101u;
+        return ((uint64_t)(0xB8B8B8B8u ^ (shi << 7)) << 32) | (uint64_t)(0xB8B8B8B8u ^ (slo << 7));
+    } else {
+        const uint32_t b = (mask >> b0) & 0xFu;
+        const uint32_t slo = (b & 1u) | ((b & 2u) << 15), shi = ((b >> 2) & 1u) | ((b & 8u) << 13);
+        return ((uint64_t)(0xBF80BF80u ^ (shi << 15)) << 32) | (uint64_t)(0xBF80BF80u ^ (slo << 15));
+    }
+}
+
 // One epilogue chunk of the accumulator: 32 lanes x kChunk consecutive columns.
 template <int C>
 __device__ __forceinline__ void tmem_ld_chunk(uint32_t taddr, float (&v)[C]) {
@@ -149,28 +175,6 @@ __device__ __forceinline__ void tmem_ld_chunk(uint32_t taddr, float (&v)[C]) {
     if constexpr (C == 16) tmem_ld_x16_sync(taddr, v);
     else if constexpr (C == 8) tmem_ld_x8_sync(taddr, v);
     else tmem_ld_x4_sync(taddr, v);
-}
-
-// Sums p[0..7] over the 32 lanes of the warp by halving exchanges: the result for
-// column (lane >> 2) & 7 ends up in every lane of that column's group of four.
-__device__ __forceinline__ int32_t warp_sum8(const int32_t (&p)[8], int lane) {
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-    int32_t q[4], r[2];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int32_t send = b4 ? p[k] : p[k + 4], keep = b4 ? p[k + 4] : p[k];
-        q[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int32_t send = b3 ? q[k] : q[k + 2], keep = b3 ? q[k + 2] : q[k];
-        r[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    const int32_t send = b2 ? r[0] : r[1], keep = b2 ? r[1] : r[0];
-    int32_t s = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    return s;
 }
 
 // Record step for replica r at iteration tt (Table 3, state 5): E from the sum the
@@ -196,29 +200,40 @@ __device__ __forceinline__ void settle_replica(const LargeArgs &L, int r, int64_
     L.flags[(size_t)(tt & 1) * L.Rpad + r] = (int8_t)imp;
 }
 
-template <int OP, int BN>
+template <int OP, int BN, int CL, bool RING>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_large_step(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const LargeArgs L) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
     constexpr uint32_t IDESC = make_idesc(OP == kOpE4M3 ? 0u : 1u, kBM, BN);
-    constexpr int kStages = Tile<BN>::kStages;
-    constexpr uint32_t kStageB = Tile<BN>::kStageB;
-    constexpr int kColsPerWarp = Tile<BN>::kColsPerWarp;
-    constexpr int kChunksPerTile = Tile<BN>::kChunksPerTile;
+    constexpr int kStages = Tile<BN, RING>::kStages;
+    constexpr uint32_t kStageB = Tile<BN, RING>::kStageB;
+    constexpr int kColsPerWarp = Tile<BN, RING>::kColsPerWarp;
+    constexpr int kChunksPerTile = Tile<BN, RING>::kChunksPerTile;
+    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
+    static_assert(CL == 1 || CL == 2 || CL == 4, "cluster of 1, 2 or 4 CTAs");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = smem;
     uint8_t *sB = smem + kStages * kStageA;
     float *ring_x = reinterpret_cast<float *>(sB + kStages * kStageB);
     float *ring_v = ring_x + kRingBytes / 4;
-    LargeShared *sh = reinterpret_cast<LargeShared *>(ring_v + kRingBytes / 4);
+    LargeShared *sh = reinterpret_cast<LargeShared *>(RING ? reinterpret_cast<uint8_t *>(ring_v + kRingBytes / 4)
+                                                           : reinterpret_cast<uint8_t *>(ring_x));
     volatile int32_t *tout = &sh->timed_out;
 
     const RunArgs &a = L.a;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int G = gridDim.x;
-    const int my_tiles = (int)blockIdx.x < L.ntiles ? (L.ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
+    // Cluster tiles: CL consecutive spin tiles of one replica tile; CTA `crank` of the
+    // cluster takes the crank-th.  With CL = 1 a cluster tile is one output tile.
+    const int crank = CL > 1 ? (int)cluster_ctarank() : 0;
+    const int Gc = (int)gridDim.x / CL;             // clusters (the grid is a multiple of CL)
+    const int cid = (int)blockIdx.x / CL;
+    const int mgroups = L.mtiles / CL;
+    const int ctiles = mgroups * L.rtiles;
+    const int my_tiles = cid < ctiles ? (ctiles - 1 - cid) / Gc + 1 : 0;
+    auto tile_m = [&](int lt) { return ((cid + lt * Gc) % mgroups) * CL + crank; };
+    auto tile_n = [&](int lt) { return (cid + lt * Gc) / mgroups; };
     const int64_t t = L.ctl->t, t_first = L.ctl->t_first, t_end = L.ctl->t_end;
     const int KB = L.Kbytes / kBKB;
     const int N = a.N, R = a.R;
@@ -231,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 32) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&sh->full[s], 1);
-            mbar_init(&sh->empty[s], 1);
+            mbar_init(&sh->empty[s], CL);   // freed by the MMAs of every CTA of the cluster
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sh->accf[b], 1);
@@ -244,6 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if constexpr (CL > 1) cluster_sync_all();   // every CTA's barriers exist before any multicast
     const uint32_t tmem = sh->tmem_base;
 
     if (warp == 0) {
@@ -254,8 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int64_t kg = 0;
             bool ok = true;
             for (int lt = 0; lt < my_tiles && ok; ++lt) {
-                const int tile = (int)blockIdx.x + lt * G;
-                const int m = tile % L.mtiles, n = tile / L.mtiles;
+                const int m = tile_m(lt), n = tile_n(lt);
                 const int ybuf = (int)(t & 3) * L.Rpad + n * BN;
                 for (int kb = 0; kb < KB; ++kb, ++kg) {
                     const int s = (int)(kg % kStages);
@@ -266,7 +281,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     mbar_arrive_expect_tx(&sh->full[s], kStageA + kStageB);
                     tma_load_2d(sA + s * kStageA, &tmA, &sh->full[s], kb * (kBKB / ESZ), m * kBM);
-                    tma_load_2d(sB + s * kStageB, &tmB, &sh->full[s], kb * (kBKB / ESZ), ybuf);
+                    if constexpr (CL == 1) {
+                        tma_load_2d(sB + s * kStageB, &tmB, &sh->full[s], kb * (kBKB / ESZ), ybuf);
+                    } else {
+                        // this CTA's 1/CL of the spin tile, to the same place in every CTA
+                        tma_load_2d_mc(sB + s * kStageB + crank * (BN / CL) * kBKB, &tmB, &sh->full[s],
+                                       kb * (kBKB / ESZ), ybuf + crank * (BN / CL), kMask);
+                    }
                 }
             }
             if (!ok) *tout = 1;
@@ -301,7 +322,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if constexpr (OP == kOpE4M3) mma_e4m3(dt, ad + 2 * k, bd + 2 * k, IDESC, (kb | k) != 0);
                         else mma_bf16(dt, ad + 2 * k, bd + 2 * k, IDESC, (kb | k) != 0);
                     }
-                    mma_commit(&sh->empty[s]);
+                    if constexpr (CL == 1) mma_commit(&sh->empty[s]);
+                    else mma_commit_mc(&sh->empty[s], kMask);   // stage s free in every CTA of the cluster
                 }
                 if (ok) mma_commit(&sh->accf[b]);
             }
@@ -335,12 +357,25 @@ __global__ void __launch_bounds__(kThreads, 1)
             cp_async_16(rv4 + (2 * slot) * kEpiThreads, L.V + off);
             cp_async_16(rv4 + (2 * slot + 1) * kEpiThreads, L.V + off + grp_stride);
         };
-        int m_cur = (int)blockIdx.x % L.mtiles, n_cur = (int)blockIdx.x / L.mtiles;
-        if (!a.field_mode)
-            for (int c0 = 0; c0 < kRing - 1; ++c0) {
-                issue(xv_offset(m_cur, n_cur, c0), c0);
-                cp_async_commit();
+        // Without the ring: the next chunk's x and v wait in registers (loaded one chunk ahead).
+        float4 nx0 = make_float4(0.f, 0.f, 0.f, 0.f), nx1 = nx0, nv0 = nx0, nv1 = nx0;
+        auto fetch = [&](size_t off) {
+            nx0 = __ldcg(reinterpret_cast<const float4 *>(L.X + off));
+            nx1 = __ldcg(reinterpret_cast<const float4 *>(L.X + off + grp_stride));
+            nv0 = __ldcg(reinterpret_cast<const float4 *>(L.V + off));
+            nv1 = __ldcg(reinterpret_cast<const float4 *>(L.V + off + grp_stride));
+        };
+        int m_cur = tile_m(0), n_cur = tile_n(0);
+        if (!a.field_mode && my_tiles > 0) {
+            if constexpr (RING) {
+                for (int c0 = 0; c0 < kRing - 1; ++c0) {
+                    issue(xv_offset(m_cur, n_cur, c0), c0);
+                    cp_async_commit();
+                }
+            } else {
+                fetch(xv_offset(m_cur, n_cur, 0));
             }
+        }
         const float bgq = beta_at(t, inv_tm1_of(a.T_total), a.beta0, a.beta1) * (a.gamma * a.q);
         const float eps = a.eps, gamma = a.gamma;
         const bool more = t + 1 < t_end;
@@ -350,9 +385,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int lt = 0; lt < my_tiles; ++lt) {
             const int m = m_cur, n = n_cur;
             const int b = lt & 1;
-            const int nxt_tile = (int)blockIdx.x + (lt + 1) * G;
             const bool has_nxt = lt + 1 < my_tiles;
-            const int m_nxt = nxt_tile % L.mtiles, n_nxt = nxt_tile / L.mtiles;
+            const int m_nxt = tile_m(lt + 1), n_nxt = tile_n(lt + 1);
             const int i = m * kBM + q4 * 32 + lane;
             const bool live_i = i < N;
             // (a) records of iteration t-1 for this replica tile (output row 0 only).
@@ -382,13 +416,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int32_t hki = live_i ? a.hk[i] : 0;
             const int rc0 = n * BN + cg * kColsPerWarp;          // first replica of this warp's columns
             const int ncol = max(0, min(kColsPerWarp, R - rc0));   // live replica columns of this warp
-            uint8_t *sb = Sn + (size_t)rc0 * L.Kbytes + (size_t)i * ESZ;
+            // the warp's first spin of this tile, in row rc0 of the next spin buffer
+            uint8_t *swarp = Sn + (size_t)rc0 * L.Kbytes + (size_t)(m * kBM + q4 * 32) * ESZ;
             // Warp-uniform, as the TMEM loads below are warp-collective.
             const bool ok = __all_sync(0xffffffffu, !*tout && mbar_wait_bounded(&sh->accf[b], (uint32_t)(lt >> 1) & 1u,
                                                                                kWaitNs));
             if (!ok) *tout = 1;
             tc_fence_after();
             const uint32_t tbase = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * BN + cg * kColsPerWarp);
+            uint32_t accn[kChunk];                         // accumulators of the next chunk to compute
+            if (ok && !a.field_mode) {
+                tmem_ld_x8_issue(tbase, accn);
+                tmem_ld_wait_x8(accn);
+            }
 #pragma unroll 1
             for (int c = 0; c < kChunksPerTile; ++c) {
                 const int col0 = c * kChunk;               // first column of the chunk in this warp's group
@@ -410,22 +450,35 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     continue;
                 }
-                // Keep kRing - 1 chunks in flight: this tile's later chunks, then the next tile's.
-                {
-                    const int ca = c + kRing - 1;
-                    const int sa = slot + kRing - 1 >= kRing ? slot - 1 : slot + kRing - 1;
-                    if (ca < kChunksPerTile) issue(xv_offset(m, n, ca), sa);
-                    else if (has_nxt) issue(xv_offset(m_nxt, n_nxt, ca - kChunksPerTile), sa);
-                    cp_async_commit();
+                float4 x0, x1, v0, v1;
+                if constexpr (RING) {
+                    // Keep kRing - 1 chunks in flight: this tile's later chunks, then the next tile's.
+                    {
+                        const int ca = c + kRing - 1;
+                        const int sa = slot + kRing - 1 >= kRing ? slot - 1 : slot + kRing - 1;
+                        if (ca < kChunksPerTile) issue(xv_offset(m, n, ca), sa);
+                        else if (has_nxt) issue(xv_offset(m_nxt, n_nxt, ca - kChunksPerTile), sa);
+                        cp_async_commit();
+                    }
+                    cp_async_wait<kRing - 1>();
+                    const int sc = slot;
+                    slot = slot + 1 == kRing ? 0 : slot + 1;
+                    if (!ok) continue;
+                    x0 = rx4[(2 * sc) * kEpiThreads]; x1 = rx4[(2 * sc + 1) * kEpiThreads];
+                    v0 = rv4[(2 * sc) * kEpiThreads]; v1 = rv4[(2 * sc + 1) * kEpiThreads];
+                } else {
+                    x0 = nx0; x1 = nx1; v0 = nv0; v1 = nv1;
+                    if (c + 1 < kChunksPerTile) fetch(xv_offset(m, n, c + 1));
+                    else if (has_nxt) fetch(xv_offset(m_nxt, n_nxt, 0));
+                    if (!ok) continue;
                 }
-                cp_async_wait<kRing - 1>();
-                const int sc = slot;
-                slot = slot + 1 == kRing ? 0 : slot + 1;
-                if (!ok) continue;
+                // This chunk's accumulators were loaded one chunk ahead; the next chunk's load
+                // goes out now and completes while this one is computed.
                 float acc[kChunk];
-                tmem_ld_chunk(tbase + col0, acc);
-                const float4 x0 = rx4[(2 * sc) * kEpiThreads], x1 = rx4[(2 * sc + 1) * kEpiThreads];
-                const float4 v0 = rv4[(2 * sc) * kEpiThreads], v1 = rv4[(2 * sc + 1) * kEpiThreads];
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j) acc[j] = __uint_as_float(accn[j]);
+                const bool ld_next = c + 1 < kChunksPerTile;
+                if (ld_next) tmem_ld_x8_issue(tbase + col0 + kChunk, accn);
                 const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
                 float vs[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
                 const int nlive = live_i ? ncol - col0 : 0;   // live columns of this chunk for this thread
@@ -445,8 +498,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int j = 0; j < kChunk; ++j) vs[j] = momentum_exact(vs[j], xs[j], If[j], eps, bgq, gamma);
                 }
-                const int32_t psum = warp_sum8(p, lane);
-                if ((lane & 3) == 0) sh->part[b][q4][cg * kColsPerWarp + col0 + (lane >> 2)] = psum;
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j) {
+                    const int32_t ps = __reduce_add_sync(0xffffffffu, p[j]);
+                    if (lane == j) sh->part[b][q4][cg * kColsPerWarp + col0 + j] = ps;
+                }
                 if (refresh_next) {
 #pragma unroll
                     for (int j = 0; j < kChunk; ++j)
@@ -461,12 +517,32 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int j = 0; j < kChunk; ++j) xn[j] = xs[j] + eps * vs[j];
                     *reinterpret_cast<float4 *>(L.X + off) = make_float4(xn[0], xn[1], xn[2], xn[3]);
                     *reinterpret_cast<float4 *>(L.X + off + grp_stride) = make_float4(xn[4], xn[5], xn[6], xn[7]);
+                    // Next iteration's spins: one sign mask per replica column over the warp's 32
+                    // spins; lane l writes replica l / 4, spins 8 (l % 4) .. (e4m3: 8 bytes) or
+                    // 4 (l % 4) .. (bf16: 8 bytes) of them.  Spins past N land in K padding, which
+                    // meets zero couplings.
+                    uint32_t msk = 0;
 #pragma unroll
-                    for (int j = 0; j < kChunk; ++j)
-                        if (j < nlive) put_spin_byte<OP>(sb + (size_t)(col0 + j) * L.Kbytes, 0, xn[j] >= 0.0f);
+                    for (int j = 0; j < kChunk; ++j) {
+                        const uint32_t mj = __ballot_sync(0xffffffffu, xn[j] >= 0.0f);
+                        if ((lane >> 2) == j) msk = mj;
+                    }
+                    const int jr = lane >> 2, part = lane & 3;
+                    if (jr < ncol - col0) {
+                        constexpr int kPer = OP == kOpE4M3 ? 8 : 4;   // spins per 8-byte store
+#pragma unroll
+                        for (int h = 0; h < 8 / kPer; ++h) {
+                            const int sp = part * kPer + h * 4 * kPer;     // first spin (of the warp's 32)
+                            // words wholly past N stay out (for bf16 they could pass the row's end)
+                            if (m * kBM + q4 * 32 + sp >= N) continue;
+                            uint8_t *dst = swarp + (size_t)(col0 + jr) * L.Kbytes + (size_t)sp * ESZ;
+                            *reinterpret_cast<uint64_t *>(dst) = spin_word<OP>(msk, sp);
+                        }
+                    }
                 }
                 *reinterpret_cast<float4 *>(L.V + off) = make_float4(vs[0], vs[1], vs[2], vs[3]);
                 *reinterpret_cast<float4 *>(L.V + off + grp_stride) = make_float4(vs[4], vs[5], vs[6], vs[7]);
+                if (ld_next) tmem_ld_wait_x8(accn);
             }
             // Accumulator b is free for the tile after next.
             tc_fence_before();
@@ -483,10 +559,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             m_cur = m_nxt;
             n_cur = n_nxt;
         }
-        cp_async_wait<0>();
+        if constexpr (RING) cp_async_wait<0>();
     }
     tc_fence_before();
     __syncthreads();
+    // No CTA of a cluster leaves while another may still multicast into it or arrive on
+    // its barriers.
+    if constexpr (CL > 1) cluster_sync_all();
     if (tid == 0) {
         if (sh->timed_out) atomicExch(a.err, 1);
         iter_ctl_finish(L.ctl);
@@ -614,9 +693,9 @@ bool make_map(CUtensorMap *m, const void *base, int op, uint64_t inner_elems, ui
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int OP, int BN>
+template <int OP, int BN, int CL, bool RING>
 cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, int *launches, int sms) {
-    constexpr size_t kSmem = Tile<BN>::kSmemBytes;
+    constexpr size_t kSmem = Tile<BN, RING>::kSmemBytes;
     LargeArgs L;
     memset(&L, 0, sizeof L);   // the bytes key the graph cache
     L.a = a;
@@ -627,19 +706,41 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
     L.Kbytes = B.Kbytes;
     L.Rpad = B.Rpad;
     L.mtiles = B.Mpad / kBM;
-    L.ntiles = L.mtiles * ((a.R + BN - 1) / BN);
+    L.rtiles = (a.R + BN - 1) / BN;
+    L.ntiles = L.mtiles * L.rtiles;
     L.X = B.X;
     L.V = B.V;
     L.Mp = B.Mpad;
     CUtensorMap tmA, tmB;
     const int esz = OP == kOpE4M3 ? 1 : 2;
     if (!make_map(&tmA, B.Jop, OP, (uint64_t)B.Kbytes / esz, (uint64_t)B.Mpad, (uint64_t)B.Kbytes, kBM) ||
-        !make_map(&tmB, B.S, OP, (uint64_t)B.Kbytes / esz, (uint64_t)4 * B.Rpad, (uint64_t)B.Kbytes, BN))
+        !make_map(&tmB, B.S, OP, (uint64_t)B.Kbytes / esz, (uint64_t)4 * B.Rpad, (uint64_t)B.Kbytes, BN / CL))
         return cudaErrorInvalidValue;
-    auto step = tc_large_step<OP, BN>;
+    auto step = tc_large_step<OP, BN, CL, RING>;
     cudaError_t e = cudaFuncSetAttribute(step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
-    const dim3 grid((unsigned)std::min(L.ntiles, std::max(sms, 1)));
+    // Persistent grid: one CTA per SM, or as many whole clusters as can be resident at once.
+    const int ctiles = (L.mtiles / CL) * L.rtiles;
+    int clusters = std::min(ctiles, std::max(sms, 1));
+    if (CL > 1) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)(CL * std::max(sms / CL, 1)));
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = kSmem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = CL;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int resident = 0;
+        e = cudaOccupancyMaxActiveClusters(&resident, reinterpret_cast<const void *>(step), &cfg);
+        if (e != cudaSuccess) return e;
+        if (resident < 1) return cudaErrorInvalidConfiguration;
+        clusters = std::min(ctiles, resident);
+    }
+    const dim3 grid((unsigned)(clusters * CL));
     e = cudaMemsetAsync(B.Epart, 0, 2 * (size_t)B.Rpad * sizeof(int64_t), st);   // energy sums start at 0
     if (e != cudaSuccess) return e;
     const int64_t RN = (int64_t)a.R * a.N;
@@ -649,7 +750,10 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
         L.a.nsteps = 1;
         L.a.T_total = 1;
         tc_large_field_prologue<OP><<<eg, 256, 0, st>>>(L);
-        step<<<grid, kThreads, kSmem, st>>>(tmA, tmB, L);
+        void *args[3] = {&tmA, &tmB, &L};
+        e = launch_steps(nullptr, reinterpret_cast<const void *>(step), grid, dim3(kThreads), kSmem, args, nullptr, 0,
+                         1, st, CL);
+        if (e != cudaSuccess) return e;
         tc_large_field_out<<<(a.R + 255) / 256, 256, 0, st>>>(L);
         n += 3;
         if (launches) *launches += n;
@@ -672,7 +776,7 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
         memcpy(key + sizeof tmA, &tmB, sizeof tmB);
         memcpy(key + 2 * sizeof tmA, &Ls, sizeof Ls);
         e = launch_steps(B.graphs, reinterpret_cast<const void *>(step), grid, dim3(kThreads), kSmem, args, key,
-                         sizeof key, a.nsteps, st);
+                         sizeof key, a.nsteps, st, CL);
         if (e != cudaSuccess) return e;
         n += (int)a.nsteps;
     }
@@ -691,6 +795,24 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
     return cudaGetLastError();
 }
 
+template <int OP, int BN>
+cudaError_t run_variant(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, int *launches, int sms) {
+    const int mtiles = B.Mpad / kBM;
+    int v = a.large_variant;
+    if (v == 0) v = kDefaultLargeVariant;
+    // A cluster needs the spin tiles to split evenly among its CTAs.
+    if (v == 6 && mtiles % 4 != 0) v = 5;
+    if (v == 5 && mtiles % 2 != 0) v = 1;
+    if (v == 4 && mtiles % 4 != 0) v = 3;
+    if (v == 3 && mtiles % 2 != 0) v = 2;
+    if (v == 6) return run_large<OP, BN, 4, true>(B, a, st, launches, sms);
+    if (v == 5) return run_large<OP, BN, 2, true>(B, a, st, launches, sms);
+    if (v == 4) return run_large<OP, BN, 4, false>(B, a, st, launches, sms);
+    if (v == 3) return run_large<OP, BN, 2, false>(B, a, st, launches, sms);
+    if (v == 2) return run_large<OP, BN, 1, false>(B, a, st, launches, sms);
+    return run_large<OP, BN, 1, true>(B, a, st, launches, sms);
+}
+
 }  // namespace
 
 cudaError_t launch_tc_large(const LargeBuffers &B, const RunArgs &a, int op, cudaStream_t st, int *launches) {
@@ -698,11 +820,12 @@ cudaError_t launch_tc_large(const LargeBuffers &B, const RunArgs &a, int op, cud
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    if (a.large_variant < 0 || a.large_variant > 6) return cudaErrorInvalidValue;
     // 256-replica tiles when they still give every SM one, else 128-replica tiles.
     const bool wide = (int64_t)(B.Mpad / kBM) * ((a.R + 255) / 256) >= sms;
     if (op == kOpE4M3)
-        return wide ? run_large<kOpE4M3, 256>(B, a, st, launches, sms) : run_large<kOpE4M3, 128>(B, a, st, launches, sms);
-    return wide ? run_large<kOpBF16, 256>(B, a, st, launches, sms) : run_large<kOpBF16, 128>(B, a, st, launches, sms);
+        return wide ? run_variant<kOpE4M3, 256>(B, a, st, launches, sms) : run_variant<kOpE4M3, 128>(B, a, st, launches, sms);
+    return wide ? run_variant<kOpBF16, 256>(B, a, st, launches, sms) : run_variant<kOpBF16, 128>(B, a, st, launches, sms);
 }
 
 }  // namespace phia

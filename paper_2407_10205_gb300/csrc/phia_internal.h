@@ -45,6 +45,8 @@ struct RunArgs {
     int32_t coupling_mem;                // tensor-core small path: 1 = J in shared, 2 = in tensor memory
     int64_t wait_ns;                     // per-iteration kernel: bound of each device wait (0 = kWaitTimeoutNs)
     int32_t stall_producer;              // per-iteration kernel, testing: the TMA producer issues nothing
+    int32_t large_variant;               // per-iteration kernel: 0 auto, 1 x/v ring, 2 x/v in registers,
+                                         // 3 / 4 registers + spin tiles multicast over 2 / 4 CTAs
     int32_t accept_test;                 // Table 3 state 4: 1 = Metropolis test on H at trajectory ends
     int64_t *proposed, *accepted;        // [R] per-replica counts of the test (accept_test = 1)
 };
@@ -91,9 +93,10 @@ void step_graphs_free(StepGraphCache *c);
 // `steps` launches of `func` with the argument list `args` (each launch identical): full
 // chunks replay one cached graph of up to 100 launches, the rest launch directly.  With
 // no cache every launch is direct.  The cache key is the kernel, its launch shape and
-// the argument bytes `key` (`key_bytes` of them).
+// the argument bytes `key` (`key_bytes` of them).  cluster > 1: thread-block clusters of
+// that many CTAs along x.
 cudaError_t launch_steps(StepGraphCache *cache, const void *func, dim3 grid, dim3 block, size_t smem, void **args,
-                         const void *key, size_t key_bytes, int64_t steps, cudaStream_t st);
+                         const void *key, size_t key_bytes, int64_t steps, cudaStream_t st, unsigned cluster = 1);
 constexpr int kOpE4M3 = 1;
 constexpr int kOpBF16 = 2;
 

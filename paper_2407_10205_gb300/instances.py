@@ -71,6 +71,125 @@ def sk_pm1(n: int, seed: int) -> Dense:
     return Dense(_symmetric_from_upper(n, up), np.zeros(n, dtype=np.int32), 0)
 
 
+# ------------------------------------------------------------------ Table 2 families
+#
+# The paper's benchmark instances (from its reference [Hamerly 2019]) are not available;
+# these generators draw instances of the same families and coefficient types (Table 2).
+# Readings: Table 2 lists the problems' own weights w; a graph problem whose weights are
+# non-negative with h = 0 would, taken as Ising couplings with the sign of Eq. 2, be a
+# ferromagnet whose ground state is all spins aligned, so for maxcut_dense, maxcut_d3,
+# sk_bool and sk_uniform the couplings are J = -w (minimising Eq. 2 then maximises the
+# weighted cut).  Fractional coefficients are fixed point with 7 fractional bits
+# (k = round(127 u)).
+
+def maxcut_dense(n: int, seed: int, p: float = 0.5) -> Dense:
+    """Max-cut of an unweighted G(n, p) graph (p = 1/2): J_ij = -1 on edges, h = 0."""
+    g = _rng(seed)
+    m = n * (n - 1) // 2
+    up = np.where(g.random(m) < p, -1, 0).astype(np.int8)
+    return Dense(_symmetric_from_upper(n, up), np.zeros(n, dtype=np.int32), 0)
+
+
+def maxcut_d3(n: int, seed: int) -> Dense:
+    """Max-cut of a random 3-regular simple graph (n even; configuration model, redrawn
+    until it has no loop or repeated edge): J_ij = -1 on edges, h = 0."""
+    if n % 2 or n < 4:
+        raise ValueError("a 3-regular graph needs an even n >= 4")
+    g = _rng(seed)
+    for _ in range(10000):
+        stubs = g.permutation(np.repeat(np.arange(n), 3))
+        a, b = stubs[0::2], stubs[1::2]
+        if np.any(a == b):
+            continue
+        lo, hi = np.minimum(a, b), np.maximum(a, b)
+        if np.unique(lo * n + hi).size != lo.size:
+            continue
+        k = np.zeros((n, n), dtype=np.int8)
+        k[lo, hi] = -1
+        k[hi, lo] = -1
+        return Dense(k, np.zeros(n, dtype=np.int32), 0)
+    raise RuntimeError("no simple 3-regular graph drawn")
+
+
+def sk_bool(n: int, seed: int) -> Dense:
+    """SK model with weights w_ij uniform in {0, 1}: J_ij = -w_ij, h = 0."""
+    g = _rng(seed)
+    m = n * (n - 1) // 2
+    up = -(g.random(m) < 0.5).astype(np.int8)
+    return Dense(_symmetric_from_upper(n, up), np.zeros(n, dtype=np.int32), 0)
+
+
+def sk_uniform(n: int, seed: int) -> Dense:
+    """SK model with weights 0 or U(0, 1) (each with probability 1/2), fixed point
+    k = round(127 u) with 7 fractional bits: J_ij = -k_ij 2^-7, h = 0."""
+    g = _rng(seed)
+    m = n * (n - 1) // 2
+    on = g.random(m) < 0.5
+    u = g.random(m)
+    up = -np.where(on, np.rint(127.0 * u), 0.0).astype(np.int8)
+    return Dense(_symmetric_from_upper(n, up), np.zeros(n, dtype=np.int32), 7)
+
+
+def spin_model(n: int, seed: int) -> Dense:
+    """Ising model with J_ij and h_i uniform in (-1, 1), fixed point k = round(127 u)
+    with 7 fractional bits."""
+    g = _rng(seed)
+    m = n * (n - 1) // 2
+    up = np.rint(127.0 * g.uniform(-1.0, 1.0, size=m)).astype(np.int8)
+    kh = np.rint(127.0 * g.uniform(-1.0, 1.0, size=n)).astype(np.int32)
+    return Dense(_symmetric_from_upper(n, up), kh, 7)
+
+
+@dataclass
+class Planted(Dense):
+    """An instance with a known optimum energy (units of q)."""
+    optimum_k: int = 0
+
+
+def nae_3_sat(n: int, seed: int, alpha: float = 2.1) -> Planted:
+    """Planted not-all-equal 3-SAT with m = round(alpha n) clauses as an Ising model.  A
+    clause on variables (a, b, c) with literal signs (sa, sb, sc) is satisfied when the
+    three y = s sigma are not all equal; y_a y_b + y_a y_c + y_b y_c is then -1, else 3.
+    Summed over clauses this is Eq. 2 with J_ab = -sum over clauses of sa sb (integer
+    couplings), h = 0, and every energy is >= -m.  Each clause draws its variables and
+    signs so that a hidden random assignment satisfies it, so the optimum is exactly -m."""
+    g = _rng(seed)
+    z = np.where(g.random(n) < 0.5, -1, 1)
+    m = int(round(alpha * n))
+    rows, cols, vals = [], [], []
+    for _ in range(m):
+        v = g.choice(n, size=3, replace=False)
+        while True:
+            sg = np.where(g.random(3) < 0.5, -1, 1)
+            y = sg * z[v]
+            if not (y[0] == y[1] == y[2]):
+                break
+        for a, b in ((0, 1), (0, 2), (1, 2)):
+            rows.append(v[a]); cols.append(v[b]); vals.append(-int(sg[a] * sg[b]))
+    k = np.zeros((n, n), dtype=np.int32)
+    np.add.at(k, (np.array(rows), np.array(cols)), np.array(vals))
+    k = k + k.T
+    if np.abs(k).max() > 127:
+        raise ValueError("coupling outside int8")
+    return Planted(k.astype(np.int8), np.zeros(n, dtype=np.int32), 0, -m)
+
+
+FAMILIES = {"maxcut_dense": maxcut_dense, "maxcut_d3": maxcut_d3, "sk_bool": sk_bool, "sk_ising": None,
+            "sk_uniform": sk_uniform, "nae_3_sat": nae_3_sat, "spin_model": spin_model}
+
+
+def tts_seed(family: str, n: int, k: int, base_seed: int = 9) -> int:
+    """Seed of instance k of a family at size n in the time-to-solution study."""
+    return base_seed * 100_003 + sorted(FAMILIES).index(family) * 10_000_019 + n * 1000 + k
+
+
+def family_instance(name: str, n: int, seed: int) -> Dense:
+    """An instance of one of the Table 2 families."""
+    if name == "sk_ising":
+        return sk_pm1(n, seed)
+    return FAMILIES[name](n, seed)
+
+
 def dense_int(n: int, kmax: int, hmax: int, seed: int, frac_bits: int = 0) -> Dense:
     """Dense integer couplings: k_ij uniform in [-kmax, kmax], kh_i uniform in [-hmax, hmax]."""
     g = _rng(seed)

@@ -36,7 +36,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("operand", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("instance_id", ctypes.c_uint32), ("stream", ctypes.c_void_p),
                 ("tile_replicas", ctypes.c_int32), ("coupling_mem", ctypes.c_int32),
-                ("tc_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tc_kernel", ctypes.c_int32), ("large_variant", ctypes.c_int32)]
 
 
 class Schedule(ctypes.Structure):
@@ -93,7 +93,7 @@ def gahmc_schedule(beta0, beta1, travel=1.5707963267948966, target=None) -> Gahm
 class TuneResult(ctypes.Structure):
     _fields_ = [("tc_kernel", ctypes.c_int32), ("tile_replicas", ctypes.c_int32), ("coupling_mem", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("best_us_per_iter", ctypes.c_float),
-                ("worst_us_per_iter", ctypes.c_float)]
+                ("worst_us_per_iter", ctypes.c_float), ("large_variant", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); every symbol include/phia.h declares
@@ -198,10 +198,10 @@ KERNEL_AUTO, KERNEL_RESIDENT, KERNEL_PER_STEP, KERNEL_IMMA, KERNEL_INCREMENTAL =
 
 
 def opts(path=PATH_AUTO, operand=OP_AUTO, device=0, instance_id=0, stream=None, tile_replicas=0,
-         coupling_mem=MEM_AUTO, tc_kernel=KERNEL_AUTO) -> Opts:
+         coupling_mem=MEM_AUTO, tc_kernel=KERNEL_AUTO, large_variant=0) -> Opts:
     s = 0 if stream is None else int(stream)
     return Opts(int(path), int(operand), int(device), int(instance_id) & 0xFFFFFFFF, ctypes.c_void_p(s or None),
-                int(tile_replicas), int(coupling_mem), int(tc_kernel), 0)
+                int(tile_replicas), int(coupling_mem), int(tc_kernel), int(large_variant))
 
 
 def create(J_k, h_k, frac_bits=0, o: Opts | None = None):
@@ -365,8 +365,8 @@ class Annealer:
 
     def __init__(self, J_k=None, h_k=None, frac_bits=0, csr=None, path=PATH_AUTO, operand=OP_AUTO,
                  device=0, instance_id=0, stream=None, tile_replicas=0, coupling_mem=MEM_AUTO,
-                 tc_kernel=KERNEL_AUTO):
-        o = opts(path, operand, device, instance_id, stream, tile_replicas, coupling_mem, tc_kernel)
+                 tc_kernel=KERNEL_AUTO, large_variant=0):
+        o = opts(path, operand, device, instance_id, stream, tile_replicas, coupling_mem, tc_kernel, large_variant)
         if csr is not None:
             row_ptr, col, val = csr
             self.n = len(row_ptr) - 1

@@ -35,8 +35,8 @@ def test_gahmc_hand_case_on_the_gpu(gpu_lib):
     g = read_golden("gahmc_two_spin.txt")
     k = np.array(g["k"].split(), dtype=np.int8).reshape(2, 2)
     kh = np.zeros(2, dtype=np.int32)
-    x = torch.tensor([_f64(g["x0"])], dtype=torch.float32, device="cuda")
-    v = torch.tensor([_f64(g["v0"])], dtype=torch.float32, device="cuda")
+    x = torch.from_numpy(_f64(g["x0"]).astype(np.float32)[None, :]).cuda()
+    v = torch.from_numpy(_f64(g["v0"]).astype(np.float32)[None, :]).cuda()
     counts = torch.zeros((1, 2), dtype=torch.int64, device="cuda")
     events = torch.full((1, 4), -(2**31), dtype=torch.int32, device="cuda")
     b = float(g["beta"])

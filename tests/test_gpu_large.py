@@ -137,3 +137,77 @@ def test_large_run_invariants(gpu_lib):
         assert o.energy_exact(P, S[r]) == be[r]
     assert res.energy_k == be.min() and o.energy_exact(P, res.spins) == res.energy_k
     assert res.stats.tc_kernel == 2 and res.stats.spin_updates == R * N * 300
+
+
+# ------------------------------------------------------------------ kernel variants
+
+VARIANTS = [1, 2, 3, 4, 5, 6]   # x/v ring in shared memory; x/v in registers; + spin-tile multicast over 2 / 4
+                                # CTAs (registers: 3, 4; ring: 5, 6)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("N,R,kmax,op", [(2000, 300, 1, 1), (1024, 4096, 16, 1), (520, 1100, 127, 2),
+                                          (384, 300, 7, 1)])
+def test_large_variants_field_bit_exact(gpu_lib, variant, N, R, kmax, op):
+    """Every variant computes the exact field and energy (N = 384: three spin tiles, which a
+    cluster of 2 or 4 cannot split, so those fall back to the unclustered form)."""
+    phia = gpu_lib
+    d = ins.dense_int(N, kmax, 31, seed=N + variant)
+    S = ins.random_spins(R, N, seed=N + R)
+    with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, operand=op, tc_kernel=phia.KERNEL_PER_STEP,
+                       large_variant=variant) as A:
+        f, e = _field(phia, A, S)
+    I, E = o.field_batch(o.Instance(d.kh, k=d.k), S)
+    assert np.array_equal(f, I) and np.array_equal(e, E)
+
+
+@pytest.mark.parametrize("N,R,op", [(1024, 600, 1), (2000, 4096, 1), (512, 700, 2)])
+def test_large_variants_bit_identical_runs(gpu_lib, N, R, op):
+    """The variants change where x, v and the spin operand travel, not the arithmetic per
+    replica: records and final states of a run with refreshes are bit-identical across all
+    of them (and equal the oracle's energies on the returned spins)."""
+    phia = gpu_lib
+    T = 40
+    d = ins.dense_int(N, 7 if op == 1 else 90, 7, seed=N + 1)
+    sched = phia.schedule(0.01, 0.2, 0.1, 2.0, refresh=15)
+    outs = []
+    for variant in VARIANTS:
+        with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, operand=op, tc_kernel=phia.KERNEL_PER_STEP,
+                           large_variant=variant) as A:
+            x = torch.empty((R, N), device="cuda"); v = torch.empty((R, N), device="cuda")
+            phia.init_state(A.h, R, 4, x, v)
+            phia.run(A.h, sched, R, 0, T, T, 4, x, v)
+            outs.append((phia.replica_results(A.h, R, N), x.cpu().numpy(), v.cpu().numpy()))
+    for rec, x, v in outs[1:]:
+        for u, w in zip(outs[0][0], rec):
+            assert np.array_equal(u, w)
+        assert np.array_equal(outs[0][1], x) and np.array_equal(outs[0][2], v)
+    P = o.Instance(d.kh, k=d.k)
+    S = phia.unpack_bits(outs[0][0][3], N)
+    for r in range(0, R, max(1, R // 16)):
+        assert o.energy_exact(P, S[r]) == outs[0][0][0][r]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_large_variants_single_step_matches_oracle(gpu_lib, variant):
+    phia = gpu_lib
+    N, R, eps, gamma, beta = 1024, 520, 0.1, 2.0, 0.05
+    d = ins.dense_int(N, 7, 7, seed=13)
+    P = o.Instance(d.kh, k=d.k)
+    x, v = ins.random_state(R, N, seed=14)
+    xn = x.astype(np.float64) + eps * v.astype(np.float64)
+    bad = np.abs(xn) < 1e-3
+    x[bad] = np.where(xn[bad] >= 0, 0.01, -0.01).astype(np.float32)
+    v[bad] = 0.0
+    with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, tc_kernel=phia.KERNEL_PER_STEP, large_variant=variant) as A:
+        xt, vt = torch.from_numpy(x).cuda(), torch.from_numpy(v).cuda()
+        phia.run(A.h, phia.schedule(beta, beta, eps, gamma), R, 0, 1, 1, 5, xt, vt)
+        be, bs, _, bits = phia.replica_results(A.h, R, N)
+        xg, vg = xt.cpu().numpy(), vt.cpu().numpy()
+    S = phia.unpack_bits(bits, N)
+    for r in range(0, R, 13):
+        xo, vo, so, Io, eo = o.step(P, x[r].astype(np.float64), v[r].astype(np.float64), beta, eps, gamma)
+        assert np.array_equal(S[r], so) and be[r] == eo and bs[r] == 0
+        assert np.allclose(xg[r], xo, rtol=1e-6, atol=1e-7)
+        scale = np.abs(v[r]) + eps * (beta * gamma * np.abs(Io) + np.abs(xo))
+        assert np.all(np.abs(vg[r] - vo) <= 1e-5 * np.maximum(scale, 1e-3))
