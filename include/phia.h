@@ -177,7 +177,10 @@ int phia_create_from_device(phia_t **out, const int8_t *J_k, const int32_t *h_k,
 /* Create a sparse instance in CSR form (host arrays): row_ptr[N+1], col[nnz]
  * (0 <= col < N, no self loops), val_k[nnz] int8; the pattern and values must be
  * symmetric.  Stored zeros are allowed.  Runs on the CSR path (a batch of one); its
- * replicas run in groups of 256, smaller counts padded with unreported replicas. */
+ * replicas run in groups of 256, smaller counts padded with unreported replicas.  One
+ * launch per iteration (opts->tc_kernel = 1: one persistent launch for the run instead;
+ * that cooperative launch assumes no other persistent launch runs on the device at the
+ * same time, and reports PHIA_ETIMEOUT rather than waiting without end if one does). */
 int phia_create_csr(phia_t **out, const int32_t *row_ptr, const int32_t *col,
                     const int8_t *val_k, const int32_t *h_k, int32_t N, int32_t frac_bits,
                     const phia_opts *opts);
@@ -342,10 +345,18 @@ int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N, int32_t f
                      int32_t reset_best, void *stream);
 
 /* ---------------------------------------------------------------- batches
- * Many independent instances of uneven N annealed together: one launch per iteration
- * covers every instance (the sparse CSR path; dense descriptors are converted to CSR).
- * Each instance keeps its own couplings, replicas, records and Philox instance id, so
- * its result does not depend on the rest of the batch. */
+ * Many independent instances of uneven N annealed together.  Dense descriptors with
+ * N <= 384 and every |k| <= 16, or N <= 256, run on the resident tcgen05 kernel over a
+ * table of CTAs (8 replicas each): every such instance, all iterations, one launch per
+ * (operand, number of 128-spin tiles) group.  The other instances run on the sparse CSR
+ * path (larger dense descriptors converted to CSR): by default one persistent cooperative
+ * launch covers every iteration of every CSR instance (blocks take 64-row x 256-replica
+ * work units from a counter, the grid meets at a bounded barrier between iterations);
+ * phia_opts.tc_kernel = 2 at creation gives one launch per iteration instead (replayed as
+ * CUDA graphs), and phia_batch_autotune picks the faster.  Each instance keeps its own
+ * couplings, replicas, records and Philox instance id, so its result does not depend on
+ * the rest of the batch or on the path, and equals the same instance run alone on that
+ * path. */
 typedef struct phia_instance_desc {
     int32_t N;                 /* spins */
     int32_t frac_bits;         /* J = k 2^-f, h = kh 2^-f */
@@ -362,7 +373,8 @@ typedef struct phia_instance_desc {
 typedef struct phia_batch_s phia_batch_t;
 
 /* Validate and upload `count` instances (copied; the caller keeps its arrays).  opts
- * may be NULL; opts->path must be PHIA_PATH_AUTO or PHIA_PATH_CSR. */
+ * may be NULL; opts->path must be PHIA_PATH_AUTO or PHIA_PATH_CSR; opts->tc_kernel: 0 or
+ * 1 = the CSR instances in one persistent launch, 2 = one launch per iteration. */
 int phia_batch_create(phia_batch_t **out, int32_t count, const phia_instance_desc *descs,
                       const phia_opts *opts);
 
@@ -379,6 +391,13 @@ int phia_batch_best(phia_batch_t *b, int32_t instance, int64_t *energy_k, int8_t
 int phia_batch_replica_results(phia_batch_t *b, int32_t instance, int32_t replicas,
                                int64_t *best_energy_k, int64_t *best_step, int64_t *hit_step,
                                uint32_t *best_bits);
+
+/* Autotuner of a batch: times probe runs (probe_iters iterations, `replicas` replicas per
+ * instance) of the CSR instances in one persistent launch and in one launch per
+ * iteration, keeps the faster for the batch; out->tc_kernel reports it (1 persistent,
+ * 2 per iteration) with the times per iteration.  The probes overwrite the records. */
+int phia_batch_autotune(phia_batch_t *b, const phia_schedule *sched, int32_t replicas, int32_t probe_iters,
+                        phia_tune_result *out);
 
 /* Statistics of the last batch run: spin_updates counts every instance; the best and
  * hit fields describe instance 0. */

@@ -578,7 +578,12 @@ int phia_create_csr(phia_t **out, const int32_t *row_ptr, const int32_t *col, co
     d.N = N; d.frac_bits = frac_bits; d.row_ptr = row_ptr; d.col = col; d.val_k = val_k; d.h_k = h_k;
     d.instance_id = o.instance_id;
     phia_batch_s *b = nullptr;
-    rc = batch_create(&b, 1, &d, &o);
+    // A single CSR instance runs one launch per iteration (graph-replayed) unless the
+    // persistent launch is asked for (tc_kernel = 1): several such handles often run at
+    // once on their own streams, and a cooperative launch wants the device to itself.
+    phia_opts ob = o;
+    ob.tc_kernel = o.tc_kernel == 1 ? 1 : 2;
+    rc = batch_create(&b, 1, &d, &ob);
     if (rc) return rc;
     phia_t *p = new phia_t();
     p->device = o.device;

@@ -1,6 +1,9 @@
-// batch.cu -- batched multi-instance runs on the sparse path (phia_batch_* of the C ABI):
-// instance validation and packing, the work list of 64-row blocks, per-replica state of
-// every instance, one launch per iteration over the whole batch.
+// batch.cu -- batched multi-instance runs (phia_batch_* of the C ABI): instance validation
+// and packing, per-replica state of every instance.  Small dense instances (N <= 384 with
+// every |k| <= 16, N <= 256 otherwise) run on the resident tcgen05 kernel with a table of
+// CTAs, all their iterations in one launch per (operand, spin tiles) group; the rest run
+// on the CSR path (dense ones converted to CSR): 64-row blocks, one launch per iteration
+// or one persistent launch over all iterations.
 #include <algorithm>
 #include <atomic>
 #include <climits>
@@ -22,9 +25,21 @@ using namespace phia;
 struct phia_batch_s {
     int device = 0;
     cudaStream_t stream = nullptr;
-    int count = 0;
-    std::vector<CsrInst> inst;          // host copy (offsets for replicas set per run)
-    std::vector<int> N, frac;
+    int count = 0;                      // instances (public indices 0 .. count-1)
+    std::vector<CsrInst> inst;          // CSR members only (offsets for replicas set per run)
+    std::vector<int> csr_pub;           // CSR member -> public index
+    std::vector<int> N, frac;           // per public instance
+    std::vector<uint32_t> inst_id;
+    std::vector<int64_t> h_off;         // into d_hk
+    // small dense members: resident tcgen05 kernel over a table of CTAs
+    std::vector<int> dense_pub;         // public indices
+    std::vector<int64_t> dense_joff;    // offset of each member's J in d_dJ
+    std::vector<int> dense_op;          // kOpE4M3 / kOpBF16
+    int8_t *d_dJ = nullptr;
+    SmallCta *d_small = nullptr;
+    size_t small_cap = 0;
+    std::vector<SmallCta> small_host;
+    std::vector<int64_t> bits_pub;      // per public instance: offset of its best states
     std::vector<long long> targets;     // per instance, LLONG_MIN = none
     std::vector<CsrBlock> blocks;
     int64_t total_rows = 0, total_nnz = 0;
@@ -48,6 +63,8 @@ struct phia_batch_s {
     uint64_t *d_start_ns = nullptr;     // %globaltimer when the run's records were reset
     int32_t *d_err = nullptr;
     IterCtl *d_ctl = nullptr;               // iteration control of the step kernel
+    unsigned *d_sync = nullptr;             // barrier and work counters of the persistent launch
+    int csr_mode = 1;                       // 1 persistent CSR launch, 2 one launch per iteration
     StepGraphCache *graphs = nullptr;       // its step launches as replayable graphs
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool ran = false;
@@ -97,17 +114,25 @@ void free_state(phia_batch_s *b) {
 
 int64_t words_of(int n) { return (n + 31) / 32; }
 
-// Per-replica offsets for R replicas per instance.
+// Per-replica offsets for R replicas per instance: records and best states by public
+// index (instance k's records start at k R), CSR state over the CSR members only.
 void layout(phia_batch_s *b, int R) {
-    int64_t x = 0, xin = 0, s = 0, rec = 0, bits = 0;
+    b->bits_pub.assign((size_t)b->count, 0);
+    int64_t bits = 0;
     for (int k = 0; k < b->count; ++k) {
-        CsrInst &in = b->inst[k];
-        in.x_off = x; in.xin_off = xin; in.s_off = s; in.rec_off = rec; in.bits_off = bits;
+        b->bits_pub[(size_t)k] = bits;
+        bits += (int64_t)R * words_of(b->N[(size_t)k]);
+    }
+    int64_t x = 0, xin = 0, s = 0;
+    for (size_t c = 0; c < b->inst.size(); ++c) {
+        CsrInst &in = b->inst[c];
+        const int k = b->csr_pub[c];
+        in.x_off = x; in.xin_off = xin; in.s_off = s;
+        in.rec_off = (int64_t)k * R;
+        in.bits_off = b->bits_pub[(size_t)k];
         x += (int64_t)in.N * R;
         xin += (int64_t)in.N * b->R_real;
         s += (int64_t)in.N * (R / 32);
-        rec += R;
-        bits += (int64_t)R * words_of(in.N);
     }
 }
 
@@ -155,6 +180,7 @@ struct PackedInst {
     std::vector<int32_t> rp, col;
     std::vector<int8_t> val;
     int64_t nnz_real = 0;
+    int small_op = 0;       // small dense member: its tensor-core operand (no CSR built)
 };
 
 void pack_error(PackedInst &out, int code, const char *fmt, ...) {
@@ -190,6 +216,22 @@ void pack_instance(const phia_instance_desc &x, int k, PackedInst &out) {
     std::vector<int32_t> &rp = out.rp;
     rp.assign((size_t)n + 1, 0);
     if (x.J_k) {
+        // Small enough for the resident tensor-core kernel: checked here, kept dense.
+        int maxk = 0;
+        for (int i = 0; i < n; ++i) {
+            if (x.J_k[(size_t)i * n + i] != 0) return pack_error(out, PHIA_EINVAL, "instance %d: nonzero diagonal", k);
+            for (int j = i + 1; j < n; ++j) {
+                const int a = x.J_k[(size_t)i * n + j];
+                if (a != x.J_k[(size_t)j * n + i])
+                    return pack_error(out, PHIA_EINVAL, "instance %d: J_k is not symmetric at (%d, %d)", k, i, j);
+                maxk = std::max(maxk, std::abs(a));
+            }
+        }
+        const int op = maxk <= 16 ? kOpE4M3 : kOpBF16;
+        if (n <= tc_small_max_n(op)) {
+            out.small_op = op;
+            return;
+        }
         for (int i = 0; i < n; ++i) {
             if (x.J_k[(size_t)i * n + i] != 0) return pack_error(out, PHIA_EINVAL, "instance %d: nonzero diagonal", k);
             for (int j = 0; j < n; ++j) {
@@ -243,7 +285,9 @@ int batch_create(phia_batch_s **out, int32_t count, const phia_instance_desc *d,
     if (opts) o = *opts;
     if (o.path != PHIA_PATH_AUTO && o.path != PHIA_PATH_CSR)
         return bfail(PHIA_ENOTSUP, "batches run on the CSR path");
+    if (o.tc_kernel < 0 || o.tc_kernel > 2) return bfail(PHIA_EINVAL, "batches: tc_kernel must be 0, 1 or 2");
     phia_batch_s *b = new phia_batch_s();
+    b->csr_mode = o.tc_kernel == 2 ? 2 : 1;
     auto cleanup = [&](int code) { phia_batch_destroy(b); return code; };
     b->count = count;
     // Instances are checked and converted independently, on every host core (a batch of
@@ -261,22 +305,39 @@ int batch_create(phia_batch_s **out, int32_t count, const phia_instance_desc *d,
         work();
         for (std::thread &t : workers) t.join();
     }
-    size_t tot_rp = 0, tot_nz = 0, tot_h = 0;
+    size_t tot_rp = 0, tot_nz = 0, tot_h = 0, tot_dj = 0;
     for (int k = 0; k < count; ++k) {
         if (packed[(size_t)k].code != PHIA_OK)
             return cleanup(bfail(packed[(size_t)k].code, "%s", packed[(size_t)k].msg.c_str()));
         tot_rp += packed[(size_t)k].rp.size();
         tot_nz += packed[(size_t)k].col.size();
         tot_h += (size_t)d[k].N;
+        if (packed[(size_t)k].small_op) tot_dj += (size_t)d[k].N * d[k].N;
     }
     std::vector<int32_t> rowptr, col, hk;
-    std::vector<int8_t> val;
-    rowptr.reserve(tot_rp); col.reserve(tot_nz); val.reserve(tot_nz); hk.reserve(tot_h);
+    std::vector<int8_t> val, dj;
+    rowptr.reserve(tot_rp); col.reserve(tot_nz); val.reserve(tot_nz); hk.reserve(tot_h); dj.reserve(tot_dj);
     int64_t row_base = 0, nnz_real = 0;
     for (int k = 0; k < count; ++k) {
         const phia_instance_desc &x = d[k];
         PackedInst &pk = packed[(size_t)k];
         const int n = x.N;
+        b->N.push_back(n);
+        b->frac.push_back(x.frac_bits);
+        b->inst_id.push_back(x.instance_id);
+        b->h_off.push_back((int64_t)hk.size());
+        b->targets.push_back(x.has_target ? (long long)x.target_k : LLONG_MIN);
+        b->any_target |= x.has_target != 0;
+        b->max_words = std::max<int>(b->max_words, (int)words_of(n));
+        if (pk.small_op) {
+            b->dense_pub.push_back(k);
+            b->dense_joff.push_back((int64_t)dj.size());
+            b->dense_op.push_back(pk.small_op);
+            dj.insert(dj.end(), x.J_k, x.J_k + (size_t)n * n);
+            hk.insert(hk.end(), x.h_k, x.h_k + n);
+            continue;
+        }
+        b->csr_pub.push_back(k);
         CsrInst in{};
         in.N = n;
         in.inst_id = x.instance_id;
@@ -294,13 +355,8 @@ int batch_create(phia_batch_s **out, int32_t count, const phia_instance_desc *d,
         std::vector<int8_t>().swap(pk.val);
         hk.insert(hk.end(), x.h_k, x.h_k + n);
         b->inst.push_back(in);
-        b->N.push_back(n);
-        b->frac.push_back(x.frac_bits);
-        b->targets.push_back(x.has_target ? (long long)x.target_k : LLONG_MIN);
-        b->any_target |= x.has_target != 0;
-        for (int i0 = 0; i0 < n; i0 += 64) b->blocks.push_back(CsrBlock{k, i0});
+        for (int i0 = 0; i0 < n; i0 += 64) b->blocks.push_back(CsrBlock{(int32_t)(b->inst.size() - 1), i0});
         row_base += n;
-        b->max_words = std::max<int>(b->max_words, (int)words_of(n));
     }
     b->total_rows = row_base;
     b->total_nnz = nnz_real;
@@ -323,13 +379,16 @@ int batch_create(phia_batch_s **out, int32_t count, const phia_instance_desc *d,
     up((void **)&b->d_hk, hk.data(), hk.size() * 4);
     up((void **)&b->d_blocks, b->blocks.data(), b->blocks.size() * sizeof(CsrBlock));
     up((void **)&b->d_targets, b->targets.data(), b->targets.size() * sizeof(long long));
-    if (ok && cudaMalloc((void **)&b->d_inst, sizeof(CsrInst) * count) != cudaSuccess) ok = false;
+    up((void **)&b->d_dJ, dj.data(), dj.size());
+    if (ok && cudaMalloc((void **)&b->d_inst, sizeof(CsrInst) * std::max<size_t>(b->inst.size(), 1)) != cudaSuccess)
+        ok = false;
     if (ok && cudaMalloc((void **)&b->d_min_hit, 8) != cudaSuccess) ok = false;
     if (ok && cudaMalloc((void **)&b->d_start_ns, 8) != cudaSuccess) ok = false;
     if (ok && cudaMemset(b->d_start_ns, 0, 8) != cudaSuccess) ok = false;
     if (ok && cudaMalloc((void **)&b->d_iters, 8) != cudaSuccess) ok = false;
     if (ok && cudaMalloc((void **)&b->d_err, 4) != cudaSuccess) ok = false;
     if (ok && cudaMalloc((void **)&b->d_ctl, sizeof(IterCtl)) != cudaSuccess) ok = false;
+    if (ok && cudaMalloc((void **)&b->d_sync, 4 * sizeof(unsigned)) != cudaSuccess) ok = false;
     if (ok) b->graphs = step_graphs_new();
     if (ok && (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess)) ok = false;
     if (!ok) {
@@ -364,7 +423,12 @@ int batch_run(phia_batch_s *b, const phia_schedule *sched, int32_t R_real, int64
     if (rc) return rc;
     b->R_real = R_real;
     layout(b, R);
-    BCU(cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(CsrInst) * b->count, cudaMemcpyHostToDevice, b->stream));
+    const int ncsr = (int)b->inst.size();
+    if (field_mode && !b->dense_pub.empty()) return bfail(PHIA_ENOTSUP, "field-only runs take CSR instances");
+    if ((x_in || x_out) && !b->dense_pub.empty())
+        return bfail(PHIA_ENOTSUP, "runs from a given state take CSR instances");
+    if (ncsr > 0)
+        BCU(cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(CsrInst) * ncsr, cudaMemcpyHostToDevice, b->stream));
     const int64_t reps = (int64_t)R * b->count;
     int64_t nbits = 0;
     for (int k = 0; k < b->count; ++k) nbits += (int64_t)R * words_of(b->N[k]);
@@ -398,7 +462,7 @@ int batch_run(phia_batch_s *b, const phia_schedule *sched, int32_t R_real, int64
     a.best_e = b->d_best_e; a.best_step = b->d_best_step; a.hit_step = b->d_hit;
     a.hit_ns = b->d_hit_ns;
     a.min_hit = b->d_min_hit; a.replica_iters = b->d_iters; a.err = b->d_err;
-    C.inst = b->d_inst; C.count = b->count;
+    C.inst = b->d_inst; C.count = ncsr;
     C.blocks = b->d_blocks; C.nblocks = (int32_t)b->blocks.size();
     C.row_ptr = b->d_rowptr; C.col = b->d_col; C.val = b->d_val; C.hk = b->d_hk;
     C.X = b->d_X; C.V = b->d_V;
@@ -407,11 +471,14 @@ int batch_run(phia_batch_s *b, const phia_schedule *sched, int32_t R_real, int64
     C.total_swords = b->total_rows * (R / 32);
     C.Esum = b->d_Esum; C.flags = b->d_flags; C.total_reps = reps;
     C.best_bits = b->d_bits;
-    // per-instance targets: the instance's own, else the schedule's
-    if (!field_mode && (b->any_target)) {
-        std::vector<long long> tg(b->count);
-        for (int k = 0; k < b->count; ++k)
-            tg[k] = b->targets[k] != LLONG_MIN ? b->targets[k] : (sched->has_target ? sched->target_k : LLONG_MIN);
+    // per-instance targets: the instance's own, else the schedule's (CSR members, by CSR index)
+    auto target_of = [&](int k) {
+        return b->targets[(size_t)k] != LLONG_MIN ? b->targets[(size_t)k]
+                                                  : (sched->has_target ? (long long)sched->target_k : LLONG_MIN);
+    };
+    if (!field_mode && (b->any_target) && ncsr > 0) {
+        std::vector<long long> tg((size_t)ncsr);
+        for (int c = 0; c < ncsr; ++c) tg[(size_t)c] = target_of(b->csr_pub[(size_t)c]);
         BCU(cudaMemcpyAsync(b->d_targets, tg.data(), tg.size() * sizeof(long long), cudaMemcpyHostToDevice, b->stream));
         BCU(cudaStreamSynchronize(b->stream));
         C.targets = b->d_targets;
@@ -419,10 +486,73 @@ int batch_run(phia_batch_s *b, const phia_schedule *sched, int32_t R_real, int64
     C.R = R; C.R_real = R_real;
     C.max_words = b->max_words;
     C.total_rows = b->total_rows;
+    // Small dense members: a table of CTAs (8 replicas each) per (operand, spin tiles)
+    // group, every instance's own couplings, field, scale, Philox id, target and records.
+    std::vector<std::pair<size_t, size_t>> groups;   // [begin, end) in small_host
+    std::vector<std::pair<int, int>> group_key;      // (operand, spin tiles)
+    std::vector<int> group_kpad;
+    if (!b->dense_pub.empty()) {
+        b->small_host.clear();
+        for (int op : {kOpE4M3, kOpBF16})
+            for (int mt = 1; mt <= 3; ++mt) {
+                const size_t beg = b->small_host.size();
+                int nmax = 0;
+                for (size_t m = 0; m < b->dense_pub.size(); ++m) {
+                    const int k = b->dense_pub[m], n = b->N[(size_t)k];
+                    if (b->dense_op[m] != op || (n + 127) / 128 != mt) continue;
+                    nmax = std::max(nmax, n);
+                    for (int r0 = 0; r0 < R_real; r0 += 8) {
+                        SmallCta c{};
+                        c.Jk = b->d_dJ + b->dense_joff[m];
+                        c.hk = b->d_hk + b->h_off[(size_t)k];
+                        c.N = n;
+                        c.W = (int32_t)words_of(n);
+                        c.inst = b->inst_id[(size_t)k];
+                        c.q = ldexpf(1.0f, -b->frac[(size_t)k]);
+                        c.rbase = r0;
+                        c.rec_off = (int64_t)k * R;
+                        c.bits_off = b->bits_pub[(size_t)k];
+                        c.target = target_of(k);
+                        b->small_host.push_back(c);
+                    }
+                }
+                if (b->small_host.size() > beg) {
+                    groups.emplace_back(beg, b->small_host.size());
+                    group_key.emplace_back(op, mt);
+                    group_kpad.push_back(op == kOpE4M3 ? (nmax + 31) / 32 * 32 : (nmax + 15) / 16 * 16);
+                }
+            }
+        if (b->small_host.size() > b->small_cap) {
+            cudaFree(b->d_small);
+            b->d_small = nullptr;
+            if (cudaMalloc((void **)&b->d_small, b->small_host.size() * sizeof(SmallCta)) != cudaSuccess)
+                return bfail(PHIA_ENOMEM, "CTA table allocation failed");
+            b->small_cap = b->small_host.size();
+        }
+        BCU(cudaMemcpyAsync(b->d_small, b->small_host.data(), b->small_host.size() * sizeof(SmallCta),
+                            cudaMemcpyHostToDevice, b->stream));
+    }
     BCU(cudaEventRecord(b->ev0, b->stream));
     C.ctl = b->d_ctl;
-    cudaError_t e = launch_csr(C, b->graphs, b->stream, &launches);
-    if (e != cudaSuccess) return bfail(PHIA_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    C.sync = b->d_sync;
+    C.persistent = (b->csr_mode == 1 && !field_mode) ? 1 : 0;
+    if (ncsr > 0) {
+        cudaError_t e = launch_csr(C, b->graphs, b->stream, &launches);
+        if (e != cudaSuccess) return bfail(PHIA_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    }
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        RunArgs ad = a;
+        ad.R = R_real;
+        ad.best_bits = b->d_bits;        // the CSR path keeps its best states in C.best_bits
+        if (!ad.best_e || !ad.best_step || !ad.hit_step || !ad.hit_ns || !ad.best_bits || !ad.replica_iters || !ad.err)
+            return bfail(PHIA_ECUDA, "internal: a record array of the dense launch is missing");
+        ad.small_cta = b->d_small + groups[gi].first;
+        ad.small_ctas = (int32_t)(groups[gi].second - groups[gi].first);
+        ad.has_target = b->any_target || sched->has_target;
+        cudaError_t e = launch_tc_small_batch(ad, group_key[gi].first, group_key[gi].second, group_kpad[gi], b->stream);
+        if (e != cudaSuccess) return bfail(PHIA_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+        ++launches;
+    }
     BCU(cudaEventRecord(b->ev1, b->stream));
     if (!field_mode) {
         b->ran = true;
@@ -540,7 +670,7 @@ int batch_stats(phia_batch_s *b, int inst, phia_stats *out) {
         if (t_hit >= t_start && t_start != 0) out->hit_ns = (int64_t)(t_hit - t_start);
     }
     out->device_ms = ms;
-    out->path = PHIA_PATH_CSR;
+    out->path = b->inst.empty() ? PHIA_PATH_TC : PHIA_PATH_CSR;   // the sparse path whenever it runs
     out->kernel_launches = b->last_launches;
     (void)iters;
     return PHIA_OK;
@@ -575,6 +705,37 @@ int phia_batch_stats_get(phia_batch_t *b, phia_stats *out) {
     return batch_stats(b, -1, out);
 }
 
+int phia_batch_autotune(phia_batch_t *b, const phia_schedule *sched, int32_t replicas, int32_t probe_iters,
+                        phia_tune_result *out) {
+    if (!b || !sched) return bfail(PHIA_EINVAL, "NULL argument");
+    if (replicas < 1 || probe_iters < 1) return bfail(PHIA_EINVAL, "need replicas >= 1 and probe_iters >= 1");
+    float best_ms = 1e30f, worst_ms = 0.f;
+    int best_mode = b->csr_mode;
+    const int saved = b->csr_mode;
+    for (int mode : {1, 2}) {
+        b->csr_mode = mode;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {   // the first run warms up
+            int rc = batch_run(b, sched, replicas, 0, probe_iters, probe_iters, 1, nullptr, nullptr, nullptr, nullptr, 1,
+                               nullptr, nullptr, nullptr);
+            if (rc) { b->csr_mode = saved; return rc; }
+            BCU(cudaEventSynchronize(b->ev1));
+            BCU(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+        }
+        if (ms < best_ms) { best_ms = ms; best_mode = mode; }
+        worst_ms = std::max(worst_ms, ms);
+    }
+    b->csr_mode = best_mode;
+    if (out) {
+        memset(out, 0, sizeof *out);
+        out->tc_kernel = best_mode;
+        out->candidates = 2;
+        out->best_us_per_iter = 1000.f * best_ms / probe_iters;
+        out->worst_us_per_iter = 1000.f * worst_ms / probe_iters;
+    }
+    return PHIA_OK;
+}
+
 int phia_batch_sync(phia_batch_t *b) {
     if (!b) return bfail(PHIA_EINVAL, "batch is NULL");
     BCU(cudaSetDevice(b->device));
@@ -589,6 +750,7 @@ void phia_batch_destroy(phia_batch_t *b) {
     free_state(b);
     cudaFree(b->d_inst); cudaFree(b->d_blocks); cudaFree(b->d_rowptr); cudaFree(b->d_col); cudaFree(b->d_val);
     cudaFree(b->d_hk); cudaFree(b->d_targets); cudaFree(b->d_min_hit); cudaFree(b->d_start_ns); cudaFree(b->d_iters); cudaFree(b->d_err);
+    cudaFree(b->d_dJ); cudaFree(b->d_small); cudaFree(b->d_sync);
     cudaFree(b->d_ctl);
     step_graphs_free(b->graphs);
     if (b->ev0) cudaEventDestroy(b->ev0);

@@ -15,6 +15,8 @@
 // Records are lagged as in the dense per-iteration kernel: the launch for iteration t
 // settles t-1 (block 0 of each instance) and copies the spins of t-2 for the replicas
 // that improved then (every block, its 64 rows).
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "phia_internal.h"
 
@@ -55,18 +57,16 @@ __device__ __forceinline__ const uint32_t *spin_buf(const CsrArgs &C, const CsrI
     return C.S + (size_t)(tt & 3) * C.total_swords + in.s_off;
 }
 
-__global__ void __launch_bounds__(32 * kWarps, 4) csr_step(const CsrArgs C) {
-    __shared__ int32_t part[kWarps][kGroup];
-    __shared__ uint32_t sbits[kRowsPerBlock][kGroup / 32];
-
+// One work unit of iteration t: 64 rows (block `bi` of the list) x 256 replicas (group g).
+// Uses the block's shared arrays; every thread of the block calls it.
+__device__ __forceinline__ void csr_unit(const CsrArgs &C, int bi, int g, int64_t t, int64_t t_first, int64_t t_end,
+                                         int32_t (*part)[kGroup], uint32_t (*sbits)[kGroup / 32]) {
     const RunArgs &a = C.a;
-    const CsrBlock blk = C.blocks[blockIdx.x];
+    const CsrBlock blk = C.blocks[bi];
     const CsrInst in = C.inst[blk.inst];
     const int b = blk.inst;
-    const int g = blockIdx.y;                     // replica group of 256
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = in.N, R = C.R, RW = R / 32;
-    const int64_t t = C.ctl->t, t_first = C.ctl->t_first, t_end = C.ctl->t_end;
 
     // (a) records of iteration t-1 (block 0 of each instance).
     if (blk.i0 == 0 && t - 1 >= t_first) settle_csr(C, in, b, g * kGroup + tid, t - 1);
@@ -202,8 +202,70 @@ __global__ void __launch_bounds__(32 * kWarps, 4) csr_step(const CsrArgs C) {
                       g * kGroup + tid,
                   (unsigned long long)s);
     }
+    __syncthreads();   // the shared arrays are free for the next unit
+}
+
+// One launch per iteration: a block per work unit; the iteration comes from C.ctl.
+__global__ void __launch_bounds__(32 * kWarps, 4) csr_step(const CsrArgs C) {
+    __shared__ int32_t part[kWarps][kGroup];
+    __shared__ uint32_t sbits[kRowsPerBlock][kGroup / 32];
+    const int64_t t = C.ctl->t, t_first = C.ctl->t_first, t_end = C.ctl->t_end;
+    csr_unit(C, blockIdx.x, blockIdx.y, t, t_first, t_end, part, sbits);
+    if (threadIdx.x == 0) iter_ctl_finish(C.ctl);
+}
+
+// Grid-wide barrier of a cooperative launch (every block resident): bar[0] counts the
+// blocks arrived, bar[1] is the generation.  The wait is bounded; false when it expired.
+__device__ bool grid_barrier(unsigned *bar, uint64_t timeout_ns) {
     __syncthreads();
-    if (tid == 0) iter_ctl_finish(C.ctl);
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const uint64_t t_start = globaltimer_ns();
+            while (*gen == g0) {
+                if (globaltimer_ns() - t_start > timeout_ns) { ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+// All iterations of the run in one cooperative launch: per iteration every block takes
+// work units from a counter (units of uneven cost balance themselves), then the grid
+// meets at a barrier.  ctr[t & 1] hands out iteration t's units; the last block to reach
+// the barrier after iteration t clears it for t + 2.
+__global__ void __launch_bounds__(32 * kWarps, 4) csr_persistent(const CsrArgs C, unsigned *bar, unsigned *ctr) {
+    __shared__ int32_t part[kWarps][kGroup];
+    __shared__ uint32_t sbits[kRowsPerBlock][kGroup / 32];
+    __shared__ int unit;
+    const int64_t t_first = C.a.t0, t_end = C.a.t0 + C.a.nsteps;
+    const int groups = C.R / kGroup, units = C.nblocks * groups;
+    for (int64_t t = t_first; t < t_end; ++t) {
+        for (;;) {
+            if (threadIdx.x == 0) unit = (int)atomicAdd(&ctr[t & 1], 1u);
+            __syncthreads();
+            const int u = unit;
+            __syncthreads();
+            if (u >= units) break;
+            csr_unit(C, u % C.nblocks, u / C.nblocks, t, t_first, t_end, part, sbits);
+        }
+        // The counter of iteration t is cleared once every block has left it: the barrier
+        // below waits for all; block 0 clears it after the barrier, before iteration t + 2.
+        if (!grid_barrier(bar, kWaitTimeoutNs)) {
+            if (threadIdx.x == 0) atomicExch(C.a.err, 1);
+            return;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctr[t & 1] = 0u;
+    }
 }
 
 // Initial state (or given, [R][N] per instance), refresh at t0, first position update,
@@ -348,7 +410,27 @@ cudaError_t launch_csr(const CsrArgs &Cin, StepGraphCache *graphs, cudaStream_t 
     csr_prologue<<<(unsigned)((pw + 255) / 256), 256, 0, st>>>(C);
     ++n;
     const dim3 grid(C.nblocks, C.R / kGroup);
-    {
+    if (C.persistent) {
+        // Every iteration in one cooperative launch: as many blocks as can be resident.
+        int per_sm = 0, dev = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_persistent, 32 * kWarps, 0);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        const int units = C.nblocks * (C.R / kGroup);
+        const unsigned blocks = (unsigned)std::max(1, std::min(units, per_sm * sms));
+        e = cudaMemsetAsync(C.sync, 0, 4 * sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
+        CsrArgs Cp = C;
+        Cp.x_in = Cp.v_in = nullptr;
+        Cp.x_out = Cp.v_out = nullptr;
+        unsigned *bar = C.sync, *ctr = C.sync + 2;
+        void *args[3] = {&Cp, &bar, &ctr};
+        e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(csr_persistent), dim3(blocks),
+                                        dim3(32 * kWarps), args, 0, st);
+        if (e != cudaSuccess) return e;
+        ++n;
+    } else {
         // The step kernel reads its iteration from C.ctl: every launch is the same, and
         // the arguments leave out what only the prologue and the export read.
         CsrArgs Cs = C;

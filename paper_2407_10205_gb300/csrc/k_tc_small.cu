@@ -14,6 +14,8 @@
 // E = -1/2 sum s (I + h) (Eq. 2) -> v update (Eqs. 5, 8) -> optional momentum refresh
 // -> x update and sign of the next iteration, written into B -> best-state keeping
 // (Table 3, state 5).
+#include <algorithm>
+
 #include <cuda_fp8.h>
 #include <cuda_bf16.h>
 
@@ -149,7 +151,7 @@ __device__ __forceinline__ void tmem_ld2_sync(uint32_t t0, uint32_t t1, float (&
 // second barrier the epilogue warps put rejected positions back to the trajectory start,
 // draw the momentum d = t + 1, keep the new start and its sums, and write the next spins;
 // the next field MMAs go out after a third barrier.
-template <int MT, int OP, int CH, int RPT, bool AT, int DERIV, bool METRO>
+template <int MT, int OP, int CH, int RPT, bool AT, int DERIV, bool METRO, bool BATCHED = false>
 __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_small_kernel(const RunArgs a, int Kpad) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
     constexpr int RL = CH * RPT;
@@ -164,6 +166,22 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
     const uint32_t A_COLS = AT ? (uint32_t)(Kbytes / 4) : 0u;   // TMEM columns per output tile of A
     const uint32_t TCOLS = pow2_cols(ACC_COLS + MT * A_COLS);
 
+    // The instance of this CTA: the run's own, or in a batched run of small dense
+    // instances the CTA's entry of the instance table (couplings, field, size, Philox id,
+    // scale, first replica, record offsets, target).
+    SmallCta ic;
+    if constexpr (BATCHED) {
+        ic = a.small_cta[blockIdx.x];
+    } else {
+        ic = SmallCta{a.Jk, a.hk, a.N, a.W, a.inst, a.q, (int32_t)blockIdx.x * RL, 0, 0, a.target};
+    }
+    int64_t *const rec_best_e = a.best_e + ic.rec_off;
+    int64_t *const rec_best_step = a.best_step + ic.rec_off;
+    int64_t *const rec_hit_step = a.hit_step + ic.rec_off;
+    uint64_t *const rec_hit_ns = a.hit_ns ? a.hit_ns + ic.rec_off : nullptr;
+    uint32_t *const rec_best_bits = a.best_bits + ic.bits_off;
+    int64_t *const rec_proposed = a.proposed ? a.proposed + ic.rec_off : nullptr;
+    int64_t *const rec_accepted = a.accepted ? a.accepted + ic.rec_off : nullptr;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sA = smem;
     uint8_t *sB = AT ? smem : sA + MT * 128 * Kbytes;
@@ -176,10 +194,10 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
     const int q4 = warp & 3;               // TMEM lane quadrant this warp may access
     const int mt = (warp >> 2) % MT;       // output-spin tile
     const int ch = warp / (4 * MT);        // which RPT of the RL replicas
-    const int N = a.N;
+    const int N = ic.N;
     const int i = mt * 128 + q4 * 32 + lane;
     const bool live_i = !ctl && i < N;
-    const int rbase = blockIdx.x * RL;
+    const int rbase = ic.rbase;
 
     if (warp == 0) {
         tmem_alloc(&sm->tmem_base, TCOLS);
@@ -193,7 +211,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
     if constexpr (!AT) {
         for (int idx = tid; idx < MT * 128 * Kpad; idx += blockDim.x) {
             const int row = idx / Kpad, col = idx - row * Kpad;
-            const float val = (row < N && col < N) ? (float)a.Jk[(size_t)row * N + col] : 0.0f;
+            const float val = (row < N && col < N) ? (float)ic.Jk[(size_t)row * N + col] : 0.0f;
             put_operand<OP>(sA, row, col, SBO, val);
         }
     }
@@ -204,10 +222,10 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
         sm->improved[0][tid] = 0;
         sm->improved[1][tid] = 0;
         const bool rec = !a.field_mode && tid < RL && r < a.R;
-        sm->best_e[tid] = rec ? a.best_e[r] : LLONG_MAX;
-        sm->best_step[tid] = rec ? a.best_step[r] : -1;
-        sm->hit[tid] = rec ? a.hit_step[r] : -1;
-        sm->hit_ns[tid] = (rec && a.hit_ns) ? a.hit_ns[r] : 0ull;
+        sm->best_e[tid] = rec ? rec_best_e[r] : LLONG_MAX;
+        sm->best_step[tid] = rec ? rec_best_step[r] : -1;
+        sm->hit[tid] = rec ? rec_hit_step[r] : -1;
+        sm->hit_ns[tid] = (rec && rec_hit_ns) ? rec_hit_ns[r] : 0ull;
         if constexpr (METRO) {
             ms->has_start[tid] = 0;
             ms->revert[tid] = 0;
@@ -232,7 +250,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
 #pragma unroll
                     for (int b = 0; b < 4 / ESZ; ++b) {
                         const int col = (c8 * 32 + q * 4) / ESZ + b;
-                        const float val = (live_i && col < N) ? (float)a.Jk[(size_t)i * N + col] : 0.0f;
+                        const float val = (live_i && col < N) ? (float)ic.Jk[(size_t)i * N + col] : 0.0f;
                         uint32_t enc;
                         if constexpr (OP == kOpE4M3) enc = __nv_fp8_e4m3(val).__x;
                         else enc = __bfloat16_as_ushort(__float2bfloat16_rn(val));
@@ -248,7 +266,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
 
     // This thread's spin slots in B: replica c = ch*RPT + k sits at row c, column i.
     uint8_t *my_b = operand_ptr<OP>(sB, ctl ? 0 : ch * RPT, live_i ? i : 0, SBO);
-    const int32_t hki = live_i ? a.hk[i] : 0;
+    const int32_t hki = live_i ? ic.hk[i] : 0;
     float x[RPT], v[RPT];
     float xs[RPT];     // METRO: positions at the current trajectory's start
 #pragma unroll
@@ -271,11 +289,11 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
             x[k] = r < a.R ? a.x_in[(size_t)r * N + i] : 0.0f;
             v[k] = r < a.R ? a.v_in[(size_t)r * N + i] : 0.0f;
         } else {
-            const U4 o = draw_raw(a.seed, a.inst, (uint32_t)r, (uint32_t)i, 0u);
+            const U4 o = draw_raw(a.seed, ic.inst, (uint32_t)r, (uint32_t)i, 0u);
             x[k] = box_muller(o.x, o.y);
             v[k] = box_muller(o.z, o.w);
         }
-        if (refresh_at(a.t0, a.refresh)) v[k] = draw_v(a.seed, a.inst, (uint32_t)r, (uint32_t)i, (uint32_t)a.t0);
+        if (refresh_at(a.t0, a.refresh)) v[k] = draw_v(a.seed, ic.inst, (uint32_t)r, (uint32_t)i, (uint32_t)a.t0);
         x[k] = x[k] + a.eps * v[k];                 // position half of Eq. A7
         const bool plus = x[k] >= 0.0f;             // sgn with sgn(0) = +1
         put_spin<OP>(my_b + k * 16, plus);
@@ -291,7 +309,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
 
     const int nit = a.field_mode ? 1 : (int)a.nsteps;
     const float inv_tm1 = inv_tm1_of(a.T_total);
-    const float eps = a.eps, gamma = a.gamma, gq = a.gamma * a.q;
+    const float eps = a.eps, gamma = a.gamma, gq = a.gamma * ic.q;
     int rc = a.refresh > 0 ? (int)((a.t0 + 1) % a.refresh) : 1;   // (t + 1) mod refresh
     uint32_t phase = 0, prv = 0;
     bool timed_out = false, stopped = false;
@@ -396,7 +414,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
                     if (a.refresh > 0 && rc == 0) {
 #pragma unroll
                         for (int k = 0; k < RPT; ++k)
-                            v[k] = draw_v(a.seed, a.inst, (uint32_t)(rbase + ch * RPT + k), (uint32_t)i, (uint32_t)(t + 1));
+                            v[k] = draw_v(a.seed, ic.inst, (uint32_t)(rbase + ch * RPT + k), (uint32_t)i, (uint32_t)(t + 1));
                     }
 #pragma unroll
                     for (int k = 0; k < RPT; ++k) {
@@ -434,10 +452,10 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
                         sm->best_step[c] = t;
                         imp = 1;
                     }
-                    if (a.has_target && sm->hit[c] < 0 && E <= a.target) {
+                    if (a.has_target && sm->hit[c] < 0 && E <= ic.target) {
                         sm->hit[c] = t;
                         sm->hit_ns[c] = globaltimer_ns();
-                        if (a.stop_at_target) atomicMin(a.min_hit, (unsigned long long)t);
+                        if (a.stop_at_target && !BATCHED) atomicMin(a.min_hit, (unsigned long long)t);
                     }
                     if (tested) {
                         // Table 3, state 4: H = beta E + x.x/2 + v.v/2 (Eq. 4) of the end point
@@ -457,10 +475,10 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
                                 sv += ms->sv[(c / RPT) * 4 * MT + j][c % RPT];
                             }
                             const float beta = beta_at(t, inv_tm1, a.beta0, a.beta1);
-                            const float dH = beta * a.q * (float)(E - ms->e_start[c]) + 0.5f * (xx - sx) +
+                            const float dH = beta * ic.q * (float)(E - ms->e_start[c]) + 0.5f * (xx - sx) +
                                              0.5f * (vv - sv);
                             ms->prop[c] += 1;
-                            if (metropolis_accept(dH, accept_uniform(a.seed, a.inst, (uint32_t)r, (uint32_t)(t + 1)))) {
+                            if (metropolis_accept(dH, accept_uniform(a.seed, ic.inst, (uint32_t)r, (uint32_t)(t + 1)))) {
                                 ms->acc[c] += 1;
                                 ms->e_start[c] = E;
                             } else {
@@ -476,7 +494,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
                 sm->improved[it & 1][c] = imp;
             }
             if (cw == 0 && lane == 0)
-                sm->stop[it & 1] = (a.stop_at_target && !a.field_mode)
+                sm->stop[it & 1] = (a.stop_at_target && !a.field_mode && !BATCHED)
                                        ? (*(volatile unsigned long long *)a.min_hit <= (unsigned long long)t)
                                        : 0;
         } else if (it > 0) {
@@ -486,7 +504,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
                 const int c = ch * RPT + k;
                 if (sm->improved[(it - 1) & 1][c]) {
                     const uint32_t bits = __ballot_sync(0xffffffffu, live_i && ((prv >> k) & 1u));
-                    if (lane == 0 && word < a.W) a.best_bits[(size_t)(rbase + c) * a.W + word] = bits;
+                    if (lane == 0 && word < ic.W) rec_best_bits[(size_t)(rbase + c) * ic.W + word] = bits;
                 }
             }
         }
@@ -502,7 +520,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
                         const int c = ch * RPT + k;
                         if (live_i) {
                             if (ms->revert[c]) x[k] = xs[k];
-                            v[k] = draw_v(a.seed, a.inst, (uint32_t)(rbase + c), (uint32_t)i, (uint32_t)(t + 1));
+                            v[k] = draw_v(a.seed, ic.inst, (uint32_t)(rbase + c), (uint32_t)i, (uint32_t)(t + 1));
                             xs[k] = x[k];
                         }
                         float px = live_i ? x[k] * x[k] : 0.0f, pv = live_i ? v[k] * v[k] : 0.0f;
@@ -546,7 +564,7 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
                 const int c = ch * RPT + k;
                 if (last >= 0 && sm->improved[last & 1][c]) {
                     const uint32_t bits = __ballot_sync(0xffffffffu, live_i && ((prv >> k) & 1u));
-                    if (lane == 0 && word < a.W) a.best_bits[(size_t)(rbase + c) * a.W + word] = bits;
+                    if (lane == 0 && word < ic.W) rec_best_bits[(size_t)(rbase + c) * ic.W + word] = bits;
                 }
             }
         }
@@ -564,13 +582,13 @@ __global__ void __launch_bounds__(128 * MT * CH + 64 * MT, CH == 1 ? 2 : 1) tc_s
     if (ctl && cw == 0 && lane < RL && !a.field_mode) {
         const int r = rbase + lane;
         if (r < a.R) {
-            a.best_e[r] = sm->best_e[lane];
-            a.best_step[r] = sm->best_step[lane];
-            a.hit_step[r] = sm->hit[lane];
-            if (a.hit_ns) a.hit_ns[r] = sm->hit_ns[lane];
+            rec_best_e[r] = sm->best_e[lane];
+            rec_best_step[r] = sm->best_step[lane];
+            rec_hit_step[r] = sm->hit[lane];
+            if (rec_hit_ns) rec_hit_ns[r] = sm->hit_ns[lane];
             if constexpr (METRO) {
-                a.proposed[r] = ms->prop[lane];
-                a.accepted[r] = ms->acc[lane];
+                rec_proposed[r] = ms->prop[lane];
+                rec_accepted[r] = ms->acc[lane];
             }
         }
     }
@@ -643,6 +661,38 @@ cudaError_t launch_mt(const RunArgs &a, int Kpad, cudaStream_t st) {
 }  // namespace
 
 int tc_small_max_n(int op) { return op == kOpE4M3 ? 384 : 256; }
+
+namespace {
+
+template <int MT, int OP>
+cudaError_t launch_batch_mt(const RunArgs &a, int Kpad, cudaStream_t st) {
+    // Every instance of the launch shares MT and the operand; K is padded for the group's
+    // largest N (Kpad), so that one shared-memory layout serves all of them (the couplings
+    // and spins past an instance's N are zero).
+    constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
+    const size_t smem = (size_t)(MT * 128 + kNB) * Kpad * ESZ + sizeof(SmallShared) + 16;
+    auto kern = a.deriv == 1 ? tc_small_kernel<MT, OP, 2, 4, false, 1, false, true>
+                             : tc_small_kernel<MT, OP, 2, 4, false, 0, false, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<a.small_ctas, 128 * MT * 2 + 64 * MT, smem, st>>>(a, Kpad);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tc_small_batch(const RunArgs &a, int op, int mt, int kpad, cudaStream_t st) {
+    if (a.small_ctas < 1) return cudaSuccess;
+    if (op == kOpE4M3) {
+        if (mt == 1) return launch_batch_mt<1, kOpE4M3>(a, kpad, st);
+        if (mt == 2) return launch_batch_mt<2, kOpE4M3>(a, kpad, st);
+        if (mt == 3) return launch_batch_mt<3, kOpE4M3>(a, kpad, st);
+    } else {
+        if (mt == 1) return launch_batch_mt<1, kOpBF16>(a, kpad, st);
+        if (mt == 2) return launch_batch_mt<2, kOpBF16>(a, kpad, st);
+    }
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_tc_small(const RunArgs &a, int op, cudaStream_t st, int *launches) {
     const int MT = (a.N + 127) / 128;

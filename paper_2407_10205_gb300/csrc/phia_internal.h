@@ -6,6 +6,21 @@
 
 namespace phia {
 
+// One CTA's instance in a batched run of small dense instances (the resident tcgen05
+// kernel with an instance table): where its couplings and field are, its size, Philox
+// instance id and fixed-point scale, its first replica, and where its records start.
+struct SmallCta {
+    const int8_t *Jk;       // [N][N]
+    const int32_t *hk;      // [N]
+    int32_t N, W;           // spins, ceil(N / 32)
+    uint32_t inst;
+    float q;
+    int32_t rbase;          // first replica of this CTA (within the instance)
+    int64_t rec_off;        // into the per-replica record arrays
+    int64_t bits_off;       // into the bit-packed best states
+    int64_t target;         // target energy (units of q)
+};
+
 // Everything one run of the hot path needs.  Replica-state arrays are [R][N]
 // row-major FP32; per-replica records persist across resumable calls.
 struct RunArgs {
@@ -49,6 +64,8 @@ struct RunArgs {
                                          // 3 / 4 registers + spin tiles multicast over 2 / 4 CTAs
     int32_t accept_test;                 // Table 3 state 4: 1 = Metropolis test on H at trajectory ends
     int64_t *proposed, *accepted;        // [R] per-replica counts of the test (accept_test = 1)
+    const SmallCta *small_cta;           // batched small dense runs: one entry per CTA
+    int32_t small_ctas;                  // its length
 };
 
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;  // 2 s bound on every device-side wait
@@ -104,6 +121,10 @@ constexpr int kOpBF16 = 2;
 int tc_small_max_n(int op);
 int tc_small_tile_replicas(int R, int requested);
 cudaError_t launch_tc_small(const RunArgs &a, int op, cudaStream_t st, int *launches);
+// The same kernel over a table of CTAs (a.small_cta, a.small_ctas entries, 8 live replicas
+// each) of small dense instances of one operand and one number of 128-spin tiles (mt):
+// all iterations of every instance in one launch; no early stop at a target.
+cudaError_t launch_tc_small_batch(const RunArgs &a, int op, int mt, int kpad, cudaStream_t st);
 
 // tcgen05 per-iteration kernel for dense instances of any size (TMA-staged J and spins).
 struct LargeBuffers {
@@ -170,6 +191,9 @@ struct CsrArgs {
     int32_t max_words;      // max ceil(N/32)
     int64_t total_rows;
     IterCtl *ctl;           // iteration control
+    int32_t persistent;     // 1: every iteration in one cooperative launch (grid barrier per iteration)
+    int32_t pad1;
+    unsigned *sync;         // 4 words of device memory for that launch's barrier and work counters
 };
 cudaError_t launch_csr(const CsrArgs &C, StepGraphCache *graphs, cudaStream_t st, int *launches);
 

@@ -124,6 +124,7 @@ SIGNATURES = {
     "phia_batch_best": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "phia_batch_replica_results": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P]),
     "phia_batch_stats_get": (ctypes.c_int, [_P, _P]),
+    "phia_batch_autotune": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "phia_batch_sync": (ctypes.c_int, [_P]),
     "phia_batch_destroy": (None, [_P]),
     "phia_server_create": (ctypes.c_int, [ctypes.POINTER(_P), _P]),
@@ -408,7 +409,7 @@ class Batch:
     ``row_ptr``/``col``/``val`` (CSR), e.g. from ``instances.py``.  ``targets``: optional
     per-instance target energies (units of q) or None entries."""
 
-    def __init__(self, instances, instance_ids=None, targets=None, device=0, stream=None):
+    def __init__(self, instances, instance_ids=None, targets=None, device=0, stream=None, csr_mode=0):
         self._keep = []
         descs = (InstanceDesc * len(instances))()
         self.n = []
@@ -434,7 +435,7 @@ class Batch:
             d.has_target = 0 if tg is None else 1
             d.target_k = 0 if tg is None else int(tg)
             self.n.append(int(d.N))
-        o = opts(path=PATH_AUTO, device=device, stream=stream)
+        o = opts(path=PATH_AUTO, device=device, stream=stream, tc_kernel=csr_mode)
         self.h = ctypes.c_void_p()
         _check(load().phia_batch_create(ctypes.byref(self.h), len(instances), descs, ctypes.byref(o)))
         self._keep = None
@@ -442,6 +443,11 @@ class Batch:
     def anneal(self, sched: Schedule, replicas: int, steps: int, seed: int):
         _check(load().phia_batch_anneal(self.h, ctypes.byref(sched), int(replicas), int(steps),
                                         int(seed) & (2**64 - 1)))
+
+    def autotune(self, sched: Schedule, replicas: int, probe_iters: int = 50) -> TuneResult:
+        r = TuneResult()
+        _check(load().phia_batch_autotune(self.h, ctypes.byref(sched), int(replicas), int(probe_iters), ctypes.byref(r)))
+        return r
 
     def best(self, k: int):
         e = ctypes.c_int64()
