@@ -234,7 +234,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int my_tiles = cid < ctiles ? (ctiles - 1 - cid) / Gc + 1 : 0;
     auto tile_m = [&](int lt) { return ((cid + lt * Gc) % mgroups) * CL + crank; };
     auto tile_n = [&](int lt) { return (cid + lt * Gc) / mgroups; };
-    const int64_t t = L.ctl->t, t_first = L.ctl->t_first, t_end = L.ctl->t_end;
     const int KB = L.Kbytes / kBKB;
     const int N = a.N, R = a.R;
     const uint64_t kWaitNs = a.wait_ns > 0 ? (uint64_t)a.wait_ns : kWaitTimeoutNs;
@@ -261,6 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     if constexpr (CL > 1) cluster_sync_all();   // every CTA's barriers exist before any multicast
     const uint32_t tmem = sh->tmem_base;
+    const int64_t t = L.ctl->t, t_first = L.ctl->t_first, t_end = L.ctl->t_end;
 
     if (warp == 0) {
         // TMA producer: the k-blocks of every tile of this CTA through one ring.  With
@@ -381,21 +381,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool more = t + 1 < t_end;
         const bool refresh_next = more && refresh_at(t + 1, a.refresh);
         uint8_t *Sn = L.S + (size_t)((t + 1) & 3) * L.Rpad * L.Kbytes;
-        int slot = 0;                                   // ring slot of the current chunk
+        // Records of earlier iterations for every tile of this CTA, done while the first
+        // tile's MMAs run (they read nothing this launch writes):
+        // (a) records of iteration t-1 for each replica tile (output row 0 only);
+        // (b) best spins of iteration t-2 for the replicas that improved then: lane l packs
+        //     the 32 spins of this warp's quadrant for replica rb + l.
         for (int lt = 0; lt < my_tiles; ++lt) {
-            const int m = m_cur, n = n_cur;
-            const int b = lt & 1;
-            const bool has_nxt = lt + 1 < my_tiles;
-            const int m_nxt = tile_m(lt + 1), n_nxt = tile_n(lt + 1);
-            const int i = m * kBM + q4 * 32 + lane;
-            const bool live_i = i < N;
-            // (a) records of iteration t-1 for this replica tile (output row 0 only).
+            const int m = tile_m(lt), n = tile_n(lt);
             if (m == 0 && t - 1 >= t_first && et < BN) {
                 const int r = n * BN + et;
                 if (r < R) settle_replica(L, r, t - 1);
             }
-            // (b) best spins of iteration t-2 for the replicas that improved then: lane l
-            // packs the 32 spins of this warp's quadrant for replica rb + l.
             if (t - 2 >= t_first) {
                 const int rb = n * BN + cg * kColsPerWarp;
                 const int8_t *F = L.flags + (size_t)((t - 2) & 1) * L.Rpad;
@@ -412,6 +408,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
             }
+        }
+        int slot = 0;                                   // ring slot of the current chunk
+        for (int lt = 0; lt < my_tiles; ++lt) {
+            const int m = m_cur, n = n_cur;
+            const int b = lt & 1;
+            const bool has_nxt = lt + 1 < my_tiles;
+            const int m_nxt = tile_m(lt + 1), n_nxt = tile_n(lt + 1);
+            const int i = m * kBM + q4 * 32 + lane;
+            const bool live_i = i < N;
             // (c) the field of this iteration and the update.
             const int32_t hki = live_i ? a.hk[i] : 0;
             const int rc0 = n * BN + cg * kColsPerWarp;          // first replica of this warp's columns
