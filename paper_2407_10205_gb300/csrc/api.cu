@@ -80,7 +80,9 @@ struct phia_s {
     int Mpad = 0, Kbytes = 0;
     uint8_t *d_S = nullptr;             // [4][Rpad][Kbytes]
     int64_t *d_Epart = nullptr;
-    int8_t *d_flags = nullptr;
+    int8_t *d_flags = nullptr;          // [4][Rpad] improved flags
+    uint32_t *d_ready = nullptr;        // [2][Rpad/128] tile counters of the overlapped variant
+    uint32_t *d_sbits = nullptr;        // [4][Rpad][Mpad/32] packed spins of the overlapped variant
     float *d_X = nullptr, *d_V = nullptr;
     int N = 0, frac_bits = 0, W = 0;
     bool csr = false;
@@ -120,6 +122,7 @@ struct phia_s {
     int last_stop = 0;
     int large_variant = 0;              // per-iteration kernel variant requested (0 = automatic)
     int tuned_variant = 0;              // the autotuner's choice for it
+    bool tuned_coop = false;            // this handle's own autotune chose the cooperative variant
     int64_t wait_ns = 0;                // testing aid (phia_debug_wait): device wait bound, 0 = default
     int stall_producer = 0;             // testing aid: the per-iteration kernel's TMA producer issues nothing
 };
@@ -163,7 +166,9 @@ void pool_free(void *ptr, cudaStream_t st) {
 }
 
 void free_replicas(phia_t *p) {
-    for (void *b : {(void *)p->d_S, (void *)p->d_Epart, (void *)p->d_flags, (void *)p->d_X, (void *)p->d_V,
+    for (void *b : {(void *)p->d_S, (void *)p->d_Epart, (void *)p->d_flags, (void *)p->d_ready, (void *)p->d_sbits,
+                    (void *)p->d_X,
+                    (void *)p->d_V,
                     (void *)p->d_x, (void *)p->d_v, (void *)p->d_s0, (void *)p->d_s1, (void *)p->d_eacc,
                     (void *)p->d_best_e, (void *)p->d_best_step, (void *)p->d_hit, (void *)p->d_bits,
                     (void *)p->d_hit_ns, (void *)p->d_prop, (void *)p->d_acc, (void *)p->d_xstart,
@@ -171,7 +176,8 @@ void free_replicas(phia_t *p) {
         pool_free(b, p->stream);
     p->d_prop = p->d_acc = nullptr; p->d_xstart = nullptr; p->d_elast = p->d_estart = nullptr;
     p->d_xxs = p->d_vvs = nullptr; p->d_hass = nullptr;
-    p->d_S = nullptr; p->d_Epart = nullptr; p->d_flags = nullptr; p->d_X = p->d_V = nullptr;
+    p->d_S = nullptr; p->d_Epart = nullptr; p->d_flags = nullptr; p->d_ready = nullptr; p->d_sbits = nullptr;
+    p->d_X = p->d_V = nullptr;
     p->d_x = p->d_v = nullptr; p->d_s0 = p->d_s1 = nullptr; p->d_eacc = nullptr;
     p->d_best_e = p->d_best_step = p->d_hit = nullptr; p->d_bits = nullptr; p->d_hit_ns = nullptr;
     p->R_cap = 0;
@@ -200,8 +206,10 @@ int ensure_replicas(phia_t *p, int R) {
         const size_t Rp = (size_t)large_rpad(R);
         al((void **)&p->d_S, 4 * Rp * p->Kbytes);
         al((void **)&p->d_Epart, 2 * Rp * 8);
-        al((void **)&p->d_flags, 2 * Rp);
+        al((void **)&p->d_flags, 4 * Rp);
+        al((void **)&p->d_ready, 2 * (Rp / 128) * sizeof(uint32_t));
         const size_t Mp = (size_t)round_up(p->N, 128);   // x, v in the interleaved [Rp/4][Mp][4] layout
+        al((void **)&p->d_sbits, 4 * Rp * (Mp / 32) * sizeof(uint32_t));
         al((void **)&p->d_X, Rp * Mp * 4); al((void **)&p->d_V, Rp * Mp * 4);
     }
     al((void **)&p->d_eacc, (size_t)R * 8);
@@ -220,7 +228,7 @@ int ensure_replicas(phia_t *p, int R) {
     if (p->large) {
         const size_t Rp = (size_t)large_rpad(R);
         CU(cudaMemsetAsync(p->d_S, 0, 4 * Rp * p->Kbytes, p->stream));   // K and replica padding stay 0
-        CU(cudaMemsetAsync(p->d_flags, 0, 2 * Rp, p->stream));
+        CU(cudaMemsetAsync(p->d_flags, 0, 4 * Rp, p->stream));
         CU(cudaMemsetAsync(p->d_Epart, 0, 2 * Rp * 8, p->stream));
     }
     p->R_cap = R;
@@ -284,6 +292,8 @@ struct TuneChoice {
     bool imma;
     bool inc;
     int lvar;        // per-iteration kernel variant (large only)
+    int lvar_alt;    // when lvar is the cooperative variant 7: the fastest of 1..6, which
+                     // other handles with the same key take (they may run concurrently)
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune;
@@ -318,14 +328,15 @@ int apply_tuned(phia_t *p, int R) {
     p->inc = c.inc;
     p->tile_rl = c.tile_rl;
     p->coupling_mem = c.coupling_mem;
-    p->tuned_variant = c.large ? c.lvar : 0;
+    p->tuned_variant = c.large ? (c.lvar == 7 && !p->tuned_coop ? c.lvar_alt : c.lvar) : 0;
     return PHIA_OK;
 }
 
 cudaError_t launch_path(phia_t *p, const RunArgs &a, int *launches) {
     if (p->path == PHIA_PATH_TC && p->large) {
         LargeBuffers B;
-        B.Jop = p->d_Jop; B.S = p->d_S; B.Epart = p->d_Epart; B.flags = p->d_flags;
+        B.Jop = p->d_Jop; B.S = p->d_S; B.Epart = p->d_Epart; B.flags = p->d_flags; B.ready = p->d_ready;
+        B.sbits = p->d_sbits;
         B.X = p->d_X; B.V = p->d_V; B.Kbytes = p->Kbytes; B.Mpad = p->Mpad; B.Rpad = large_rpad(a.R);
         B.ctl = p->d_ctl; B.graphs = p->graphs;
         return launch_tc_large(B, a, p->op, p->stream, launches);
@@ -489,7 +500,7 @@ int create_dense(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N,
     }
     if (o.tc_kernel == 3 && N > imma_small_max_n())
         return fail(PHIA_ENOTSUP, "the int8 mma.sync kernel handles N <= %d (N = %d)", imma_small_max_n(), N);
-    if (o.large_variant < 0 || o.large_variant > 6) return fail(PHIA_EINVAL, "large_variant must be 0..6");
+    if (o.large_variant < 0 || o.large_variant > 7) return fail(PHIA_EINVAL, "large_variant must be 0..7");
     int dev_count = 0;
     if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
         return fail(PHIA_ECUDA, "no CUDA device available");
@@ -671,21 +682,23 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
     std::vector<TuneChoice> cands;
     if (p->N <= tc_small_max_n(p->op)) {
         for (int tile : {4, 8, 16})
-            for (int mem : {1, 2}) cands.push_back(TuneChoice{false, tile, mem, false, false, 0});
+            for (int mem : {1, 2}) cands.push_back(TuneChoice{false, tile, mem, false, false, 0, 0});
     }
     if (p->N <= imma_small_max_n()) {
-        cands.push_back(TuneChoice{false, 8, 0, true, false, 0});
-        cands.push_back(TuneChoice{false, 16, 0, true, false, 0});
+        cands.push_back(TuneChoice{false, 8, 0, true, false, 0, 0});
+        cands.push_back(TuneChoice{false, 16, 0, true, false, 0, 0});
     }
     if (p->N <= std::min(inc_small_max_n(), tc_small_max_n(p->op))) {
         for (int tile : {4, 8, 16})
-            if (inc_small_tile_replicas(p->N, tile) == tile) cands.push_back(TuneChoice{false, tile, 0, false, true, 0});
+            if (inc_small_tile_replicas(p->N, tile) == tile)
+                cands.push_back(TuneChoice{false, tile, 0, false, true, 0, 0});
     }
-    for (int lv = 1; lv <= 6; ++lv) cands.push_back(TuneChoice{true, 0, 0, false, false, lv});
+    for (int lv = 1; lv <= 7; ++lv) cands.push_back(TuneChoice{true, 0, 0, false, false, lv, 0});
     const bool saved_auto = p->auto_tile;
     p->auto_tile = false;
-    float best_ms = 1e30f, worst_ms = 0.f;
+    float best_ms = 1e30f, worst_ms = 0.f, alt_ms = 1e30f;
     TuneChoice best = cands[0];
+    int best_alt = 1;   // fastest non-cooperative per-iteration variant
     for (const TuneChoice &c : cands) {
         if (c.large) {
             int rc = ensure_operand(p);
@@ -705,6 +718,7 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
             CU(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
         }
         if (ms < best_ms) { best_ms = ms; best = c; }
+        if (c.large && c.lvar != 7 && ms < alt_ms) { alt_ms = ms; best_alt = c.lvar; }
         worst_ms = std::max(worst_ms, ms);
     }
     p->large = best.large;
@@ -713,7 +727,9 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
     p->tile_rl = best.tile_rl;
     p->coupling_mem = best.coupling_mem;
     p->tuned_variant = best.lvar;
+    p->tuned_coop = best.large && best.lvar == 7;
     p->auto_tile = saved_auto;
+    best.lvar_alt = best_alt;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune[TuneKey{p->N, replicas, p->op}] = best;

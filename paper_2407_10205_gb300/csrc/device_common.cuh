@@ -351,6 +351,40 @@ __device__ __forceinline__ void cp_async_wait() {
 __device__ __forceinline__ void named_barrier_sync(uint32_t id, uint32_t threads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
+// Arrive without waiting; the thread's earlier memory accesses are performed for the
+// threads that wait on the barrier.
+__device__ __forceinline__ void named_barrier_arrive(uint32_t id, uint32_t threads) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// GPU-scope acquire load and release store of a 32-bit counter in global memory.
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Order this thread's earlier generic-proxy accesses of global memory before its later
+// async-proxy ones (TMA reads of data other CTAs wrote with ordinary stores).
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Bounded wait until the counter at p reaches v (acquire); false after `timeout_ns` of
+// wall time or once *abort is set.
+__device__ __forceinline__ bool wait_counter_at_least(const uint32_t *p, uint32_t v, uint64_t timeout_ns,
+                                                      const volatile int32_t *abort) {
+    if (ld_acquire_gpu(p) >= v) return true;
+    const uint64_t t_start = globaltimer_ns();
+    for (;;) {
+        __nanosleep(32);
+        if (ld_acquire_gpu(p) >= v) return true;
+        if (*abort || globaltimer_ns() - t_start > timeout_ns) return false;
+    }
+}
 
 // 32 lanes x 32 bits, 16 consecutive columns per thread, then the wait for the load.
 __device__ __forceinline__ void tmem_ld_x16_sync(uint32_t taddr, float (&v)[16]) {

@@ -70,6 +70,9 @@ struct LargeShared {
     uint32_t tmem_base;
     int32_t timed_out;
     int32_t part[2][4][kMaxBN];   // per lane-quadrant warp sums of s_i (I_i + h_i), by accumulator
+    int64_t rec_settled;          // overlapped variant: last iteration the records warp settled
+    int64_t rec_copied;           // ... and whose best spins it copied
+    uint64_t tiledone[2];         // ... the epilogue warps finished the tile in accumulator b
 };
 
 // Tile shape: 128 output spins x BN replicas.  BN = 256 halves the coupling-operand
@@ -99,6 +102,10 @@ struct LargeArgs {
     int32_t Kbytes, Rpad, mtiles, ntiles, Mp;
     int32_t rtiles;     // replica tiles (ntiles = mtiles * rtiles)
     IterCtl *ctl;       // iteration of the launch and range of the run
+    uint32_t *ready;    // overlapped variant: [rtiles] output tiles finished per replica tile,
+                        // then [rtiles] iterations settled per replica tile (null otherwise)
+    uint32_t *sbits;    // overlapped variant: [4][Rpad][Mp/32] packed spins by iteration slot
+    int64_t f0, f1;     // overlapped variant: this launch's iterations [f0, f1) of the call's
 };
 
 template <int OP>
@@ -177,10 +184,68 @@ __device__ __forceinline__ void tmem_ld_chunk(uint32_t taddr, float (&v)[C]) {
     else tmem_ld_x4_sync(taddr, v);
 }
 
+// Epilogue arithmetic of one chunk (one output spin i, kChunk replica columns): the field
+// I = J s + h from the accumulator (Eq. 6; exact integers in FP32), the energy terms
+// s (I + h) of the live columns (Eq. 2 through Eq. 6; 0 elsewhere) and the momentum
+// update at the new position (Eqs. 5, 8, A7).
+__device__ __forceinline__ void chunk_field_momentum(const float (&acc)[kChunk], const float (&xs)[kChunk],
+                                                     float (&vs)[kChunk], int32_t hki, int nlive, int deriv,
+                                                     float eps, float bgq, float gamma, int32_t (&p)[kChunk]) {
+    float If[kChunk];
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) {
+        const int32_t Ik = __float2int_rn(acc[j]) + hki;
+        const int32_t e = Ik + hki;
+        p[j] = j < nlive ? (xs[j] >= 0.0f ? e : -e) : 0;
+        If[j] = (float)Ik;
+    }
+    if (deriv == 1) {
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) vs[j] = momentum_quad(vs[j], xs[j], If[j], eps, bgq, gamma);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) vs[j] = momentum_exact(vs[j], xs[j], If[j], eps, bgq, gamma);
+    }
+}
+
+// Next iteration's spins of one chunk into the B operand: one sign mask per replica
+// column over the warp's 32 spins (rows row0 .. row0 + 31); lane l writes replica l / 4,
+// spins 8 (l % 4) .. (e4m3: 8 bytes) or 4 (l % 4) .. (bf16: 8 bytes) of them.  `col` is
+// the chunk's first replica row, `live` its live columns.  Spins past N land in K
+// padding, which meets zero couplings; words wholly past N stay out (for bf16 they could
+// pass the row's end).
+// With `bits` (the overlapped variant) lane j < live also stores column j's mask, the
+// packed spins of rows row0 .. row0 + 31, at bits[j * bits_stride].
+template <int OP>
+__device__ __forceinline__ void chunk_store_spins(const float (&xn)[kChunk], int lane, int live, uint8_t *col,
+                                                  int Kbytes, int row0, int N, uint32_t *bits = nullptr,
+                                                  int bits_stride = 0) {
+    constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
+    uint32_t msk = 0, own = 0;
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) {
+        const uint32_t mj = __ballot_sync(0xffffffffu, xn[j] >= 0.0f);
+        if ((lane >> 2) == j) msk = mj;
+        if (lane == j) own = mj;
+    }
+    if (bits && lane < live && lane < kChunk && row0 < N) bits[(size_t)lane * bits_stride] = own;
+    const int jr = lane >> 2, part = lane & 3;
+    if (jr < live) {
+        constexpr int kPer = OP == kOpE4M3 ? 8 : 4;   // spins per 8-byte store
+#pragma unroll
+        for (int h = 0; h < 8 / kPer; ++h) {
+            const int sp = part * kPer + h * 4 * kPer;     // first spin (of the warp's 32)
+            if (row0 + sp >= N) continue;
+            uint8_t *dst = col + (size_t)jr * Kbytes + (size_t)sp * ESZ;
+            *reinterpret_cast<uint64_t *>(dst) = spin_word<OP>(msk, sp);
+        }
+    }
+}
+
 // Record step for replica r at iteration tt (Table 3, state 5): E from the sum the
 // output tiles accumulated, best/target records, improved flag; the sum slot is cleared
 // for iteration tt + 2.
-__device__ __forceinline__ void settle_replica(const LargeArgs &L, int r, int64_t tt) {
+__device__ __forceinline__ void settle_replica(const LargeArgs &L, int r, int64_t tt, int flag_mask = 1) {
     const RunArgs &a = L.a;
     unsigned long long *slot = reinterpret_cast<unsigned long long *>(L.Epart) + (size_t)(tt & 1) * L.Rpad + r;
     const long long twice = (long long)*slot;
@@ -197,7 +262,74 @@ __device__ __forceinline__ void settle_replica(const LargeArgs &L, int r, int64_
         a.hit_step[r] = tt;
         if (a.hit_ns) a.hit_ns[r] = globaltimer_ns();
     }
-    L.flags[(size_t)(tt & 1) * L.Rpad + r] = (int8_t)imp;
+    L.flags[(size_t)(tt & flag_mask) * L.Rpad + r] = (int8_t)imp;
+}
+
+// The record step of settle_replica for the replicas r0 + 32 k (k < K) of one lane, with
+// every load issued before any store so that the K replicas' round trips overlap.
+template <int K>
+__device__ __forceinline__ void settle_lane(const LargeArgs &L, int r0, int64_t tt, int flag_mask) {
+    const RunArgs &a = L.a;
+    unsigned long long *slots = reinterpret_cast<unsigned long long *>(L.Epart) + (size_t)(tt & 1) * L.Rpad;
+    long long tw[K], be[K], hs[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int r = r0 + 32 * k;
+        const bool live = r < a.R;
+        tw[k] = live ? (long long)slots[r] : 0;
+        be[k] = live ? (long long)a.best_e[r] : 0;
+        hs[k] = live ? (long long)a.hit_step[r] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int r = r0 + 32 * k;
+        if (r >= a.R) continue;
+        slots[r] = 0ull;
+        const long long E = -tw[k] / 2;
+        int imp = 0;
+        if (!(a.stop_at_target && hs[k] >= 0) && E < be[k]) {
+            a.best_e[r] = E;
+            a.best_step[r] = tt;
+            imp = 1;
+        }
+        if (a.has_target && hs[k] < 0 && E <= a.target) {
+            a.hit_step[r] = tt;
+            if (a.hit_ns) a.hit_ns[r] = globaltimer_ns();
+        }
+        L.flags[(size_t)(tt & flag_mask) * L.Rpad + r] = (int8_t)imp;
+    }
+}
+
+// Best spins of iteration tt, output rows m*128 .. m*128+127, for the replicas r0 + 32 k
+// (k < K) of one lane that improved at tt (flags slot tt & 3), from the packed spins the
+// epilogue wrote (slot tt & 3, rows of Mp / 32 words): flags first, then per improved
+// replica one 16-byte load and its words.
+template <int K>
+__device__ __forceinline__ void copy_best_lane(const LargeArgs &L, int r0, int m, int64_t tt) {
+    const RunArgs &a = L.a;
+    const int8_t *F = L.flags + (size_t)(tt & 3) * L.Rpad;
+    const int Wp = L.Mp / 32;
+    const uint32_t *B = L.sbits + (size_t)(tt & 3) * L.Rpad * Wp;
+    int8_t f[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) f[k] = r0 + 32 * k < a.R ? F[r0 + 32 * k] : (int8_t)0;
+    uint4 w[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        w[k] = f[k] ? *reinterpret_cast<const uint4 *>(B + (size_t)(r0 + 32 * k) * Wp + m * 4) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (!f[k]) continue;
+        const int r = r0 + 32 * k;
+        const uint32_t ws[4] = {w[k].x, w[k].y, w[k].z, w[k].w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i0 = m * kBM + q * 32;
+            if (i0 >= a.N) break;
+            const uint32_t valid = a.N - i0 >= 32 ? 0xffffffffu : ((1u << (a.N - i0)) - 1u);
+            a.best_bits[(size_t)r * a.W + (i0 >> 5)] = ws[q] & valid;
+        }
+    }
 }
 
 template <int OP, int BN, int CL, bool RING>
@@ -484,25 +616,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int j = 0; j < kChunk; ++j) acc[j] = __uint_as_float(accn[j]);
                 const bool ld_next = c + 1 < kChunksPerTile;
                 if (ld_next) tmem_ld_x8_issue(tbase + col0 + kChunk, accn);
-                const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-                float vs[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                const float xs[kChunk] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                float vs[kChunk] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
                 const int nlive = live_i ? ncol - col0 : 0;   // live columns of this chunk for this thread
-                int32_t p[8];
-                float If[kChunk];
-#pragma unroll
-                for (int j = 0; j < kChunk; ++j) {
-                    const int32_t Ik = __float2int_rn(acc[j]) + hki;            // Eq. 6, exact
-                    const int32_t e = Ik + hki;
-                    p[j] = j < nlive ? (xs[j] >= 0.0f ? e : -e) : 0;
-                    If[j] = (float)Ik;
-                }
-                if (a.deriv == 1) {
-#pragma unroll
-                    for (int j = 0; j < kChunk; ++j) vs[j] = momentum_quad(vs[j], xs[j], If[j], eps, bgq, gamma);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < kChunk; ++j) vs[j] = momentum_exact(vs[j], xs[j], If[j], eps, bgq, gamma);
-                }
+                int32_t p[kChunk];
+                chunk_field_momentum(acc, xs, vs, hki, nlive, a.deriv, eps, bgq, gamma, p);
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j) {
                     const int32_t ps = __reduce_add_sync(0xffffffffu, p[j]);
@@ -517,33 +635,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // the array and no record reads them.
                 const size_t off = xv_offset(m, n, c);
                 if (more) {
-                    float xn[8];
+                    float xn[kChunk];
 #pragma unroll
                     for (int j = 0; j < kChunk; ++j) xn[j] = xs[j] + eps * vs[j];
                     *reinterpret_cast<float4 *>(L.X + off) = make_float4(xn[0], xn[1], xn[2], xn[3]);
                     *reinterpret_cast<float4 *>(L.X + off + grp_stride) = make_float4(xn[4], xn[5], xn[6], xn[7]);
-                    // Next iteration's spins: one sign mask per replica column over the warp's 32
-                    // spins; lane l writes replica l / 4, spins 8 (l % 4) .. (e4m3: 8 bytes) or
-                    // 4 (l % 4) .. (bf16: 8 bytes) of them.  Spins past N land in K padding, which
-                    // meets zero couplings.
-                    uint32_t msk = 0;
-#pragma unroll
-                    for (int j = 0; j < kChunk; ++j) {
-                        const uint32_t mj = __ballot_sync(0xffffffffu, xn[j] >= 0.0f);
-                        if ((lane >> 2) == j) msk = mj;
-                    }
-                    const int jr = lane >> 2, part = lane & 3;
-                    if (jr < ncol - col0) {
-                        constexpr int kPer = OP == kOpE4M3 ? 8 : 4;   // spins per 8-byte store
-#pragma unroll
-                        for (int h = 0; h < 8 / kPer; ++h) {
-                            const int sp = part * kPer + h * 4 * kPer;     // first spin (of the warp's 32)
-                            // words wholly past N stay out (for bf16 they could pass the row's end)
-                            if (m * kBM + q4 * 32 + sp >= N) continue;
-                            uint8_t *dst = swarp + (size_t)(col0 + jr) * L.Kbytes + (size_t)sp * ESZ;
-                            *reinterpret_cast<uint64_t *>(dst) = spin_word<OP>(msk, sp);
-                        }
-                    }
+                    chunk_store_spins<OP>(xn, lane, ncol - col0, swarp + (size_t)col0 * L.Kbytes, L.Kbytes,
+                                          m * kBM + q4 * 32, N);
                 }
                 *reinterpret_cast<float4 *>(L.V + off) = make_float4(vs[0], vs[1], vs[2], vs[3]);
                 *reinterpret_cast<float4 *>(L.V + off + grp_stride) = make_float4(vs[4], vs[5], vs[6], vs[7]);
@@ -575,6 +673,362 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (sh->timed_out) atomicExch(a.err, 1);
         iter_ctl_finish(L.ctl);
     }
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 2 * BN);
+    }
+}
+
+// ---------------------------------------------------------------- overlapped variant
+// All iterations of a run in one cooperative launch (variant 7).  Every CTA keeps the same
+// output tiles for the whole run, so the state it updates never moves to another CTA;
+// what crosses CTAs are the spins of a replica tile (the B operand of every output tile
+// of that replica tile) and its energy sums.  Instead of a grid-wide step boundary, a
+// per-replica-tile counter ready[n] counts the output tiles of replica tile n that have
+// finished an iteration: the TMA producer of an output tile of n starts iteration t once
+// ready[n] = mtiles (t - t0), so a replica tile whose spins are complete runs ahead
+// while other tiles still finish the previous iteration, and the MMAs of a CTA's next
+// tile overlap the epilogue of its current one across iteration boundaries too.
+//
+// Two more warps do the bookkeeping off the epilogue's path.  A signal warp waits until
+// the epilogue warps finished a tile (an mbarrier), makes their stores visible to the GPU
+// and counts the tile in ready[n].  A records warp settles the energies of iteration t of
+// the replica tiles whose first output tile (m = 0) this CTA owns (after ready[n] counts
+// iteration t complete), then publishes settled[n] = t - t0 + 1; every CTA copies the
+// best spins of iteration t of its own tiles once settled[n] says the improved flags of
+// t exist.  Reuse of the rotating buffers is guarded: the m = 0 tile is counted for
+// iteration t only after its records warp settled t - 1 (the energy sums of t - 1 share a
+// slot with t + 1), and a tile writes the spins of iteration t + 1 into the buffer of
+// t - 3 only after its records warp copied t - 3; the improved flags rotate over four
+// slots.  Every wait is bounded; a wait that runs out sets the run's error flag and the
+// CTA winds down.
+template <int OP, int BN>
+__global__ void __launch_bounds__(kThreads + 64, 1)
+    tc_flow_run(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const LargeArgs L) {
+    constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
+    constexpr uint32_t IDESC = make_idesc(OP == kOpE4M3 ? 0u : 1u, kBM, BN);
+    constexpr int kStages = Tile<BN, true>::kStages;
+    constexpr uint32_t kStageB = Tile<BN, true>::kStageB;
+    constexpr int kColsPerWarp = Tile<BN, true>::kColsPerWarp;
+    constexpr int kChunksPerTile = Tile<BN, true>::kChunksPerTile;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + kStages * kStageA;
+    float *ring_x = reinterpret_cast<float *>(sB + kStages * kStageB);
+    float *ring_v = ring_x + kRingBytes / 4;
+    LargeShared *sh = reinterpret_cast<LargeShared *>(ring_v + kRingBytes / 4);
+    volatile int32_t *tout = &sh->timed_out;
+    volatile int64_t *rec_settled = &sh->rec_settled, *rec_copied = &sh->rec_copied;
+
+    const RunArgs &a = L.a;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int G = (int)gridDim.x, cid = (int)blockIdx.x;
+    const int mt = L.mtiles;
+    const int my_tiles = cid < L.ntiles ? (L.ntiles - 1 - cid) / G + 1 : 0;
+    auto tile_m = [&](int lt) { return (cid + lt * G) % mt; };
+    auto tile_n = [&](int lt) { return (cid + lt * G) / mt; };
+    const int64_t t0 = L.f0, t_end = L.f1, t_call_end = a.t0 + a.nsteps;
+    const int64_t total = (t_end - t0) * my_tiles;      // tiles this CTA processes, g = 0 .. total - 1
+    const int KB = L.Kbytes / kBKB;
+    const int N = a.N, R = a.R;
+    const uint64_t kWaitNs = a.wait_ns > 0 ? (uint64_t)a.wait_ns : kWaitTimeoutNs;
+    uint32_t *ready = L.ready, *settled = L.ready + L.rtiles;
+
+    if (warp == 0) {
+        tmem_alloc(&sh->tmem_base, 2 * BN);
+        tmem_relinquish();
+    }
+    if (tid == 32) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&sh->full[s], 1);
+            mbar_init(&sh->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sh->accf[b], 1);
+            mbar_init(&sh->acce[b], kEpiWarps + 1);   // + the signal warp
+            mbar_init(&sh->tiledone[b], kEpiWarps);
+        }
+        mbar_init(&sh->drain, 1);
+        sh->timed_out = 0;
+        sh->rec_settled = t0 - 1;
+        sh->rec_copied = t0 - 1;
+        fence_mbarrier_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+
+    if (warp == 0) {
+        // TMA producer: tile g is iteration t0 + g / my_tiles of output tile g % my_tiles.
+        if (lane == 0 && !a.stall_producer) {
+            int64_t kg = 0;
+            bool ok = true;
+            for (int64_t g = 0; g < total && ok; ++g) {
+                const int lt = (int)(g % my_tiles);
+                const int64_t t = t0 + g / my_tiles;
+                const int m = tile_m(lt), n = tile_n(lt);
+                // the spins of iteration t of replica tile n: all its output tiles finished t - 1
+                if (!wait_counter_at_least(ready + n, (uint32_t)(mt * (t - t0)), kWaitNs, tout)) {
+                    ok = false;
+                    break;
+                }
+                fence_proxy_async_global();
+                const int ybuf = (int)(t & 3) * L.Rpad + n * BN;
+                for (int kb = 0; kb < KB; ++kb, ++kg) {
+                    const int s = (int)(kg % kStages);
+                    if (kg >= kStages &&
+                        (*tout || !mbar_wait_bounded(&sh->empty[s], (uint32_t)((kg / kStages) - 1) & 1u, kWaitNs))) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&sh->full[s], kStageA + kStageB);
+                    tma_load_2d(sA + s * kStageA, &tmA, &sh->full[s], kb * (kBKB / ESZ), m * kBM);
+                    tma_load_2d(sB + s * kStageB, &tmB, &sh->full[s], kb * (kBKB / ESZ), ybuf);
+                }
+            }
+            if (!ok) *tout = 1;
+            for (int64_t k = kg > kStages ? kg - kStages : 0; k < kg; ++k)
+                mbar_wait_bounded(&sh->full[k % kStages], (uint32_t)(k / kStages) & 1u, kWaitNs);
+        }
+    } else if (warp == 1) {
+        // MMA issuer: accumulators alternate per tile.
+        if (lane == 0) {
+            int64_t kg = 0;
+            bool ok = true;
+            for (int64_t g = 0; g < total && ok; ++g) {
+                const int b = (int)(g & 1);
+                if (g >= 2 && (*tout || !mbar_wait_bounded(&sh->acce[b], (uint32_t)((g >> 1) - 1) & 1u, kWaitNs))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)(b * BN);
+                for (int kb = 0; kb < KB; ++kb, ++kg) {
+                    const int s = (int)(kg % kStages);
+                    if (*tout || !mbar_wait_bounded(&sh->full[s], (uint32_t)(kg / kStages) & 1u, kWaitNs)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t ad = smem_desc_sw128(smem_u32(sA + s * kStageA));
+                    const uint64_t bd = smem_desc_sw128(smem_u32(sB + s * kStageB));
+#pragma unroll
+                    for (int k = 0; k < kBKB / 32; ++k) {
+                        if constexpr (OP == kOpE4M3) mma_e4m3(dt, ad + 2 * k, bd + 2 * k, IDESC, (kb | k) != 0);
+                        else mma_bf16(dt, ad + 2 * k, bd + 2 * k, IDESC, (kb | k) != 0);
+                    }
+                    mma_commit(&sh->empty[s]);
+                }
+                if (ok) mma_commit(&sh->accf[b]);
+            }
+            if (!ok) *tout = 1;
+            mma_commit(&sh->drain);
+            mbar_wait_bounded(&sh->drain, 0, kWaitNs);
+        }
+    } else if (warp < 2 + kEpiWarps) {
+        // Epilogue warps, as in the per-iteration kernel; tiles follow each other across
+        // iterations, and the x/v ring prefetches across both.
+        const int ew = warp - 2;
+        const int q4 = warp & 3;
+        const int cg = ew >> 2;
+        const int et = ew * 32 + lane;
+        const int Mp = L.Mp;
+        float4 *rx4 = reinterpret_cast<float4 *>(ring_x) + et;
+        float4 *rv4 = reinterpret_cast<float4 *>(ring_v) + et;
+        const size_t grp_stride = (size_t)Mp * 4;
+        auto xv_offset = [&](int m_, int n_, int c_) -> size_t {
+            const int grp = (n_ * BN + cg * kColsPerWarp + c_ * kChunk) >> 2;
+            return ((size_t)grp * Mp + (m_ * kBM + q4 * 32 + lane)) * 4;
+        };
+        auto issue = [&](size_t off, int slot_) {
+            cp_async_16(rx4 + (2 * slot_) * kEpiThreads, L.X + off);
+            cp_async_16(rx4 + (2 * slot_ + 1) * kEpiThreads, L.X + off + grp_stride);
+            cp_async_16(rv4 + (2 * slot_) * kEpiThreads, L.V + off);
+            cp_async_16(rv4 + (2 * slot_ + 1) * kEpiThreads, L.V + off + grp_stride);
+        };
+        if (total > 0) {
+            for (int c0 = 0; c0 < kRing - 1; ++c0) {
+                issue(xv_offset(tile_m(0), tile_n(0), c0), c0);
+                cp_async_commit();
+            }
+        }
+        const float inv_tm1 = inv_tm1_of(a.T_total);
+        int slot = 0;
+        bool ok = true;
+        for (int64_t g = 0; g < total; ++g) {
+            const int lt = (int)(g % my_tiles);
+            const int64_t t = t0 + g / my_tiles;
+            const int m = tile_m(lt), n = tile_n(lt);
+            const int b = (int)(g & 1);
+            const bool has_nxt = g + 1 < total;
+            const int lt_nxt = (int)((g + 1) % my_tiles);
+            const int m_nxt = tile_m(lt_nxt), n_nxt = tile_n(lt_nxt);
+            const int i = m * kBM + q4 * 32 + lane;
+            const bool live_i = i < N;
+            const float bgq = beta_at(t, inv_tm1, a.beta0, a.beta1) * (a.gamma * a.q);
+            const float eps = a.eps, gamma = a.gamma;
+            const bool more = t + 1 < t_call_end;
+            const bool refresh_next = more && refresh_at(t + 1, a.refresh);
+            const int32_t hki = live_i ? a.hk[i] : 0;
+            const int rc0 = n * BN + cg * kColsPerWarp;
+            const int ncol = max(0, min(kColsPerWarp, R - rc0));
+            uint8_t *swarp = L.S + (size_t)((t + 1) & 3) * L.Rpad * L.Kbytes + (size_t)rc0 * L.Kbytes +
+                             (size_t)(m * kBM + q4 * 32) * ESZ;
+            uint32_t *bwarp = L.sbits + ((size_t)((t + 1) & 3) * L.Rpad + rc0) * (Mp / 32) + m * 4 + q4;
+            // The spins of t + 1 overwrite those of t - 3: their best copy must be done.
+            if (ok && more && t - 3 >= t0) {
+                const uint64_t ts = globaltimer_ns();
+                while (*rec_copied < t - 3) {
+                    if (*tout || globaltimer_ns() - ts > kWaitNs) {
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            ok = __all_sync(0xffffffffu, ok && !*tout &&
+                                             mbar_wait_bounded(&sh->accf[b], (uint32_t)(g >> 1) & 1u, kWaitNs));
+            if (!ok) *tout = 1;
+            tc_fence_after();
+            const uint32_t tbase = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * BN + cg * kColsPerWarp);
+            uint32_t accn[kChunk];
+            if (ok) {
+                tmem_ld_x8_issue(tbase, accn);
+                tmem_ld_wait_x8(accn);
+            }
+            unsigned long long *ep = reinterpret_cast<unsigned long long *>(L.Epart) + (size_t)(t & 1) * L.Rpad;
+#pragma unroll 1
+            for (int c = 0; c < kChunksPerTile; ++c) {
+                const int col0 = c * kChunk;
+                {
+                    const int ca = c + kRing - 1;
+                    const int sa = slot + kRing - 1 >= kRing ? slot - 1 : slot + kRing - 1;
+                    if (ca < kChunksPerTile) issue(xv_offset(m, n, ca), sa);
+                    else if (has_nxt) issue(xv_offset(m_nxt, n_nxt, ca - kChunksPerTile), sa);
+                    cp_async_commit();
+                }
+                cp_async_wait<kRing - 1>();
+                const int sc = slot;
+                slot = slot + 1 == kRing ? 0 : slot + 1;
+                if (!ok) continue;
+                const float4 x0 = rx4[(2 * sc) * kEpiThreads], x1 = rx4[(2 * sc + 1) * kEpiThreads];
+                const float4 v0 = rv4[(2 * sc) * kEpiThreads], v1 = rv4[(2 * sc + 1) * kEpiThreads];
+                float acc[kChunk];
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j) acc[j] = __uint_as_float(accn[j]);
+                const bool ld_next = c + 1 < kChunksPerTile;
+                if (ld_next) tmem_ld_x8_issue(tbase + col0 + kChunk, accn);
+                const float xs[kChunk] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                float vs[kChunk] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                const int nlive = live_i ? ncol - col0 : 0;
+                int32_t p[kChunk];
+                chunk_field_momentum(acc, xs, vs, hki, nlive, a.deriv, eps, bgq, gamma, p);
+                // the warp's sum of column j lands in lane j, which adds it to the replica's total
+                int32_t mine = 0;
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j) {
+                    const int32_t ps = __reduce_add_sync(0xffffffffu, p[j]);
+                    if (lane == j) mine = ps;
+                }
+                if (lane < kChunk && mine != 0) atomicAdd(ep + rc0 + col0 + lane, (unsigned long long)(long long)mine);
+                if (refresh_next) {
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j)
+                        vs[j] = draw_v(a.seed, a.inst, (uint32_t)(rc0 + col0 + j), (uint32_t)i, (uint32_t)(t + 1));
+                }
+                const size_t off = xv_offset(m, n, c);
+                if (more) {
+                    float xn[kChunk];
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j) xn[j] = xs[j] + eps * vs[j];
+                    *reinterpret_cast<float4 *>(L.X + off) = make_float4(xn[0], xn[1], xn[2], xn[3]);
+                    *reinterpret_cast<float4 *>(L.X + off + grp_stride) = make_float4(xn[4], xn[5], xn[6], xn[7]);
+                    chunk_store_spins<OP>(xn, lane, ncol - col0, swarp + (size_t)col0 * L.Kbytes, L.Kbytes,
+                                          m * kBM + q4 * 32, N, bwarp + (size_t)col0 * (Mp / 32), Mp / 32);
+                }
+                *reinterpret_cast<float4 *>(L.V + off) = make_float4(vs[0], vs[1], vs[2], vs[3]);
+                *reinterpret_cast<float4 *>(L.V + off + grp_stride) = make_float4(vs[4], vs[5], vs[6], vs[7]);
+                if (ld_next) tmem_ld_wait_x8(accn);
+            }
+            // The tile is done: the signal warp publishes it (its arrival on tiledone carries
+            // this warp's stores), then the accumulator is released.
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh->tiledone[b]);
+            if (lane == 0) mbar_arrive(&sh->acce[b]);
+        }
+        cp_async_wait<0>();
+    } else if (warp == 2 + kEpiWarps) {
+        // Records warp.
+        constexpr int K = BN / 32;   // replicas per lane of a replica tile
+        for (int64_t t = t0; t < t_end && !*tout; ++t) {
+            bool ok = true;
+            for (int lt = 0; lt < my_tiles && ok; ++lt) {
+                const int n = tile_n(lt);
+                if (tile_m(lt) != 0) continue;
+                ok = wait_counter_at_least(ready + n, (uint32_t)(mt * (t - t0 + 1)), kWaitNs, tout);
+                if (!ok) break;
+                settle_lane<K>(L, n * BN + lane, t, 3);
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence();
+                    st_release_gpu(settled + n, (uint32_t)(t - t0 + 1));
+                }
+                __syncwarp();
+            }
+            if (lane == 0) *rec_settled = t;
+            for (int lt = 0; lt < my_tiles && ok; ++lt) {
+                const int m = tile_m(lt), n = tile_n(lt);
+                ok = wait_counter_at_least(settled + n, (uint32_t)(t - t0 + 1), kWaitNs, tout);
+                if (ok) copy_best_lane<K>(L, n * BN + lane, m, t);
+            }
+            if (!ok) {
+                *tout = 1;
+                break;
+            }
+            __syncwarp();
+            if (lane == 0) *rec_copied = t;
+        }
+    } else if (lane == 0) {
+        // Signal warp: once the epilogue warps finished tile g, make their spins and
+        // energy terms visible to the GPU and count the tile in ready[n].  The m = 0 tile
+        // of a replica tile publishes iteration t only after its energy sums of t - 1 were
+        // read out (those of t + 1 go to the same slot).
+        for (int64_t g = 0; g < total; ++g) {
+            const int b = (int)(g & 1);
+            const int lt = (int)(g % my_tiles);
+            const int64_t t = t0 + g / my_tiles;
+            const int m = tile_m(lt), n = tile_n(lt);
+            if (*tout || !mbar_wait_bounded(&sh->tiledone[b], (uint32_t)(g >> 1) & 1u, kWaitNs)) {
+                *tout = 1;
+                break;
+            }
+            mbar_arrive(&sh->acce[b]);
+            if (m == 0 && t - 1 >= t0) {
+                const uint64_t ts = globaltimer_ns();
+                bool go = true;
+                while (*rec_settled < t - 1) {
+                    if (*tout || globaltimer_ns() - ts > kWaitNs) {
+                        go = false;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                if (!go) {
+                    *tout = 1;
+                    break;
+                }
+            }
+            __threadfence();
+            atomicAdd(ready + n, 1u);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && sh->timed_out) atomicExch(a.err, 1);
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, 2 * BN);
@@ -800,11 +1254,97 @@ cudaError_t run_large(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, 
     return cudaGetLastError();
 }
 
+// Packed spins of the run's first iteration (the epilogue writes those of later ones).
+template <int OP>
+__global__ void tc_flow_pack0(const LargeArgs L) {
+    constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
+    const int Wp = L.Mp / 32, W = L.a.W;   // words past W are never read unmasked
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)L.a.R * W) return;
+    const int r = (int)(idx / W), w = (int)(idx - (int64_t)r * W);
+    const int64_t slot = L.a.t0 & 3;
+    const uint8_t *row = L.S + ((size_t)slot * L.Rpad + r) * L.Kbytes;
+    L.sbits[((size_t)slot * L.Rpad + r) * Wp + w] = plus_bits32<OP>(row + (size_t)w * 32 * ESZ);
+}
+
+// Variant 7: the whole run in cooperative launches of tc_flow_run (all CTAs resident at
+// once, as CTAs wait on each other's tiles).  Runs whose tile counters could pass 2^31 go
+// out in several launches; every launch settles and copies all of its iterations.
+template <int OP, int BN>
+cudaError_t run_flow(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, int *launches, int sms) {
+    constexpr size_t kSmem = Tile<BN, true>::kSmemBytes;
+    constexpr int kFlowThreads = kThreads + 64;
+    LargeArgs L;
+    memset(&L, 0, sizeof L);
+    L.a = a;
+    L.ctl = B.ctl;
+    L.S = B.S;
+    L.Epart = B.Epart;
+    L.flags = B.flags;
+    L.Kbytes = B.Kbytes;
+    L.Rpad = B.Rpad;
+    L.mtiles = B.Mpad / kBM;
+    L.rtiles = (a.R + BN - 1) / BN;
+    L.ntiles = L.mtiles * L.rtiles;
+    L.X = B.X;
+    L.V = B.V;
+    L.Mp = B.Mpad;
+    L.ready = B.ready;
+    L.sbits = B.sbits;
+    CUtensorMap tmA, tmB;
+    const int esz = OP == kOpE4M3 ? 1 : 2;
+    if (!make_map(&tmA, B.Jop, OP, (uint64_t)B.Kbytes / esz, (uint64_t)B.Mpad, (uint64_t)B.Kbytes, kBM) ||
+        !make_map(&tmB, B.S, OP, (uint64_t)B.Kbytes / esz, (uint64_t)4 * B.Rpad, (uint64_t)B.Kbytes, BN))
+        return cudaErrorInvalidValue;
+    auto k = tc_flow_run<OP, BN>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kFlowThreads, kSmem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const dim3 grid((unsigned)std::min(L.ntiles, std::max(sms, 1) * per_sm));
+    e = cudaMemsetAsync(B.Epart, 0, 2 * (size_t)B.Rpad * sizeof(int64_t), st);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    const int64_t RMp = (int64_t)B.Rpad * B.Mpad;
+    tc_large_prologue<OP><<<(unsigned)((RMp + 255) / 256), 256, 0, st>>>(L);
+    const int64_t RW = (int64_t)a.R * a.W;
+    tc_flow_pack0<OP><<<(unsigned)((RW + 255) / 256), 256, 0, st>>>(L);
+    n += 2;
+    const int64_t chunk = std::max<int64_t>(1, ((int64_t)1 << 31) / L.mtiles - 1);
+    for (int64_t t = a.t0; t < a.t0 + a.nsteps; t += chunk) {
+        LargeArgs Lc = L;
+        Lc.f0 = t;
+        Lc.f1 = t + std::min(chunk, a.t0 + a.nsteps - t);
+        Lc.a.x_in = Lc.a.v_in = nullptr;
+        Lc.a.x_out = Lc.a.v_out = nullptr;
+        e = cudaMemsetAsync(B.ready, 0, 2 * (size_t)L.rtiles * sizeof(uint32_t), st);
+        if (e != cudaSuccess) return e;
+        void *args[3] = {&tmA, &tmB, &Lc};
+        e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k), grid, dim3(kFlowThreads), args, kSmem, st);
+        if (e != cudaSuccess) return e;
+        ++n;
+    }
+    tc_large_count<<<1, 32, 0, st>>>(L);
+    ++n;
+    if (a.x_out || a.v_out) {
+        const int64_t RN = (int64_t)a.R * a.N;
+        tc_large_export<<<(unsigned)((RN + 255) / 256), 256, 0, st>>>(L);
+        ++n;
+    }
+    if (launches) *launches += n;
+    return cudaGetLastError();
+}
+
 template <int OP, int BN>
 cudaError_t run_variant(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, int *launches, int sms) {
     const int mtiles = B.Mpad / kBM;
     int v = a.large_variant;
     if (v == 0) v = kDefaultLargeVariant;
+    // The overlapped variant needs its tile counters (absent from the allocation-free entry).
+    if (v == 7 && (!B.ready || !B.sbits || a.field_mode)) v = 1;
+    if (v == 7) return run_flow<OP, BN>(B, a, st, launches, sms);
     // A cluster needs the spin tiles to split evenly among its CTAs.
     if (v == 6 && mtiles % 4 != 0) v = 5;
     if (v == 5 && mtiles % 2 != 0) v = 1;
@@ -825,7 +1365,7 @@ cudaError_t launch_tc_large(const LargeBuffers &B, const RunArgs &a, int op, cud
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    if (a.large_variant < 0 || a.large_variant > 6) return cudaErrorInvalidValue;
+    if (a.large_variant < 0 || a.large_variant > 7) return cudaErrorInvalidValue;
     // 256-replica tiles when they still give every SM one, else 128-replica tiles.
     const bool wide = (int64_t)(B.Mpad / kBM) * ((a.R + 255) / 256) >= sms;
     if (op == kOpE4M3)

@@ -227,6 +227,8 @@ extern "C" int phia_run_noalloc(const int8_t *J_k, const int32_t *h_k, int32_t N
     B.flags = reinterpret_cast<int8_t *>(base + Ly.off_f);
     B.ctl = reinterpret_cast<IterCtl *>(base + 64);
     B.graphs = nullptr;   // a graph would be an allocation
+    B.ready = nullptr;    // no overlapped variant here
+    B.sbits = nullptr;
     B.X = reinterpret_cast<float *>(base + Ly.off_x);
     B.V = reinterpret_cast<float *>(base + Ly.off_v);
     B.Kbytes = Ly.Kbytes; B.Mpad = Ly.Mpad; B.Rpad = Ly.Rpad;

@@ -131,10 +131,13 @@ struct LargeBuffers {
     const void *Jop;      // [Mpad][Kbytes] couplings in the operand encoding
     uint8_t *S;           // [4][Rpad][Kbytes] spin operand buffers (zero padding)
     int64_t *Epart;       // [2][Rpad], zero between uses
-    int8_t *flags;        // [2][Rpad]
+    int8_t *flags;        // [2][Rpad] ([4][Rpad] with the tile counters below)
     float *X, *V;         // [Rpad/4][Mpad][4] working state (replica groups of 4 interleaved per spin)
     IterCtl *ctl;         // iteration control
     StepGraphCache *graphs;   // or null: step launches go out one by one
+    uint32_t *ready;      // [2][Rpad/128] tile counters of the overlapped variant, or null
+                          // (then flags has [2][Rpad]; with counters [4][Rpad])
+    uint32_t *sbits;      // [4][Rpad][Mpad/32] packed spins of the overlapped variant, or null
     int32_t Kbytes, Mpad, Rpad;
 };
 cudaError_t launch_tc_large(const LargeBuffers &B, const RunArgs &a, int op, cudaStream_t st, int *launches);

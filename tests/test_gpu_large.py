@@ -141,8 +141,9 @@ def test_large_run_invariants(gpu_lib):
 
 # ------------------------------------------------------------------ kernel variants
 
-VARIANTS = [1, 2, 3, 4, 5, 6]   # x/v ring in shared memory; x/v in registers; + spin-tile multicast over 2 / 4
-                                # CTAs (registers: 3, 4; ring: 5, 6)
+VARIANTS = [1, 2, 3, 4, 5, 6, 7]   # x/v ring in shared memory; x/v in registers; + spin-tile multicast over 2 / 4
+                                   # CTAs (registers: 3, 4; ring: 5, 6); 7: the whole run in one cooperative
+                                   # launch with per-replica-tile counters (field-only calls use 1)
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -211,3 +212,59 @@ def test_large_variants_single_step_matches_oracle(gpu_lib, variant):
         assert np.allclose(xg[r], xo, rtol=1e-6, atol=1e-7)
         scale = np.abs(v[r]) + eps * (beta * gamma * np.abs(Io) + np.abs(xo))
         assert np.all(np.abs(vg[r] - vo) <= 1e-5 * np.maximum(scale, 1e-3))
+
+
+@pytest.mark.parametrize("N,R,op,T", [(2000, 4096, 1, 120), (1024, 600, 1, 200), (4000, 2048, 1, 60),
+                                      (700, 300, 2, 150), (130, 64, 1, 90)])
+def test_overlapped_variant_equals_per_iteration_launches(gpu_lib, N, R, op, T):
+    """Variant 7 (one cooperative launch per run; CTAs keep their tiles and wait on
+    per-replica-tile counters; a records warp settles energies and copies best spins) gives
+    bit for bit the records, hit steps and final x, v of one launch per iteration, with
+    refreshes and a target that some replicas reach mid-run; grids of fewer CTAs than SMs
+    (N = 1024 / 700 / 130) and CTAs with one or two tiles (N = 2000, 4000) included."""
+    phia = gpu_lib
+    d = ins.dense_int(N, 7 if op == 1 else 90, 7, seed=N + 5)
+    P = o.Instance(d.kh, k=d.k)
+    sched0 = phia.schedule(0.01, 0.2, 0.1, 2.0, refresh=25)
+    outs = []
+    for variant in (1, 7):
+        with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, operand=op, tc_kernel=phia.KERNEL_PER_STEP,
+                           large_variant=variant) as A:
+            if not outs:
+                # a target between the best energies of the replicas: reached by some, mid-run
+                phia.anneal(A.h, sched0, R, T, 9)
+                be0 = phia.replica_results(A.h, R, N)[0]
+                target = int(np.median(be0))
+            sched = phia.schedule(0.01, 0.2, 0.1, 2.0, refresh=25, target=target)
+            x = torch.empty((R, N), device="cuda"); v = torch.empty((R, N), device="cuda")
+            phia.init_state(A.h, R, 9, x, v)
+            phia.run(A.h, sched, R, 0, T, T, 9, x, v)
+            outs.append((phia.replica_results(A.h, R, N), x.cpu().numpy(), v.cpu().numpy()))
+    (rec1, x1, v1), (rec7, x7, v7) = outs
+    for u, w in zip(rec1, rec7):
+        assert np.array_equal(u, w)
+    assert np.array_equal(x1, x7) and np.array_equal(v1, v7)
+    hit = rec7[2]
+    assert (hit >= 0).any() and (hit < 0).any()
+    S = phia.unpack_bits(rec7[3], N)
+    for r in range(0, R, max(1, R // 16)):
+        assert o.energy_exact(P, S[r]) == rec7[0][r]
+
+
+def test_overlapped_variant_resumes_bit_identical(gpu_lib):
+    """A run split into calls (t0 > 0) equals the same run in one call, on variant 7."""
+    phia = gpu_lib
+    N, R, T = 1500, 1024, 90
+    d = ins.sk_pm1(N, 4)
+    sched = phia.schedule(0.01, 0.2, 0.1, 2.0, refresh=20)
+    res = []
+    for splits in ((0, T), (0, 33, 61, T)):
+        with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, tc_kernel=phia.KERNEL_PER_STEP, large_variant=7) as A:
+            x = torch.empty((R, N), device="cuda"); v = torch.empty((R, N), device="cuda")
+            phia.init_state(A.h, R, 3, x, v)
+            for k in range(len(splits) - 1):
+                phia.run(A.h, sched, R, splits[k], splits[k + 1] - splits[k], T, 3, x, v, reset_best=(k == 0))
+            res.append((phia.replica_results(A.h, R, N), x.cpu().numpy(), v.cpu().numpy()))
+    for u, w in zip(res[0][0], res[1][0]):
+        assert np.array_equal(u, w)
+    assert np.array_equal(res[0][1], res[1][1]) and np.array_equal(res[0][2], res[1][2])

@@ -19,13 +19,16 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def test_expired_waits_report_etimeout_and_the_gpu_stays_usable(gpu_lib):
+@pytest.mark.parametrize("variant", [1, 7])
+def test_expired_waits_report_etimeout_and_the_gpu_stays_usable(gpu_lib, variant):
+    """Variant 1: one launch per iteration; variant 7: one cooperative launch whose tile
+    counters and records waits must give up too."""
     phia = gpu_lib
     N, R, T = 256, 256, 3
     d = ins.dense_int(N, 7, 7, seed=13)
     P = o.Instance(d.kh, k=d.k)
     sched = phia.schedule(0.01, 0.1, 0.1, 2.0)
-    with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, tc_kernel=phia.KERNEL_PER_STEP) as A:
+    with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, tc_kernel=phia.KERNEL_PER_STEP, large_variant=variant) as A:
         phia.debug_wait(A.h, 2_000_000, stall_producer=True)
         phia.anneal(A.h, sched, R, T, 5)
         with pytest.raises(phia.PhiaError) as ei:
