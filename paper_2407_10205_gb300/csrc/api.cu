@@ -292,7 +292,7 @@ struct TuneChoice {
     bool imma;
     bool inc;
     int lvar;        // per-iteration kernel variant (large only)
-    int lvar_alt;    // when lvar is the cooperative variant 7: the fastest of 1..6, which
+    int lvar_alt;    // when lvar is a cooperative variant (7..9): the fastest of 1..6, which
                      // other handles with the same key take (they may run concurrently)
 };
 std::mutex g_tune_mu;
@@ -328,7 +328,7 @@ int apply_tuned(phia_t *p, int R) {
     p->inc = c.inc;
     p->tile_rl = c.tile_rl;
     p->coupling_mem = c.coupling_mem;
-    p->tuned_variant = c.large ? (c.lvar == 7 && !p->tuned_coop ? c.lvar_alt : c.lvar) : 0;
+    p->tuned_variant = c.large ? (c.lvar >= 7 && !p->tuned_coop ? c.lvar_alt : c.lvar) : 0;
     return PHIA_OK;
 }
 
@@ -500,7 +500,7 @@ int create_dense(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N,
     }
     if (o.tc_kernel == 3 && N > imma_small_max_n())
         return fail(PHIA_ENOTSUP, "the int8 mma.sync kernel handles N <= %d (N = %d)", imma_small_max_n(), N);
-    if (o.large_variant < 0 || o.large_variant > 7) return fail(PHIA_EINVAL, "large_variant must be 0..7");
+    if (o.large_variant < 0 || o.large_variant > 9) return fail(PHIA_EINVAL, "large_variant must be 0..9");
     int dev_count = 0;
     if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
         return fail(PHIA_ECUDA, "no CUDA device available");
@@ -693,7 +693,7 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
             if (inc_small_tile_replicas(p->N, tile) == tile)
                 cands.push_back(TuneChoice{false, tile, 0, false, true, 0, 0});
     }
-    for (int lv = 1; lv <= 7; ++lv) cands.push_back(TuneChoice{true, 0, 0, false, false, lv, 0});
+    for (int lv = 1; lv <= 9; ++lv) cands.push_back(TuneChoice{true, 0, 0, false, false, lv, 0});
     const bool saved_auto = p->auto_tile;
     p->auto_tile = false;
     float best_ms = 1e30f, worst_ms = 0.f, alt_ms = 1e30f;
@@ -718,7 +718,7 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
             CU(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
         }
         if (ms < best_ms) { best_ms = ms; best = c; }
-        if (c.large && c.lvar != 7 && ms < alt_ms) { alt_ms = ms; best_alt = c.lvar; }
+        if (c.large && c.lvar < 7 && ms < alt_ms) { alt_ms = ms; best_alt = c.lvar; }
         worst_ms = std::max(worst_ms, ms);
     }
     p->large = best.large;
@@ -727,7 +727,7 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
     p->tile_rl = best.tile_rl;
     p->coupling_mem = best.coupling_mem;
     p->tuned_variant = best.lvar;
-    p->tuned_coop = best.large && best.lvar == 7;
+    p->tuned_coop = best.large && best.lvar >= 7;
     p->auto_tile = saved_auto;
     best.lvar_alt = best_alt;
     {

@@ -104,7 +104,8 @@ struct LargeArgs {
     IterCtl *ctl;       // iteration of the launch and range of the run
     uint32_t *ready;    // overlapped variant: [rtiles] output tiles finished per replica tile,
                         // then [rtiles] iterations settled per replica tile (null otherwise)
-    uint32_t *sbits;    // overlapped variant: [4][Rpad][Mp/32] packed spins by iteration slot
+    uint32_t *sbits;    // overlapped variant: [4][Mp/32][Rpad] packed spins by iteration slot,
+                        // word-major (a word's replicas are consecutive)
     int64_t f0, f1;     // overlapped variant: this launch's iterations [f0, f1) of the call's
 };
 
@@ -215,11 +216,10 @@ __device__ __forceinline__ void chunk_field_momentum(const float (&acc)[kChunk],
 // padding, which meets zero couplings; words wholly past N stay out (for bf16 they could
 // pass the row's end).
 // With `bits` (the overlapped variant) lane j < live also stores column j's mask, the
-// packed spins of rows row0 .. row0 + 31, at bits[j * bits_stride].
+// packed spins of rows row0 .. row0 + 31, at bits[j] (consecutive replicas: one sector).
 template <int OP>
 __device__ __forceinline__ void chunk_store_spins(const float (&xn)[kChunk], int lane, int live, uint8_t *col,
-                                                  int Kbytes, int row0, int N, uint32_t *bits = nullptr,
-                                                  int bits_stride = 0) {
+                                                  int Kbytes, int row0, int N, uint32_t *bits = nullptr) {
     constexpr int ESZ = OP == kOpE4M3 ? 1 : 2;
     uint32_t msk = 0, own = 0;
 #pragma unroll
@@ -228,7 +228,7 @@ __device__ __forceinline__ void chunk_store_spins(const float (&xn)[kChunk], int
         if ((lane >> 2) == j) msk = mj;
         if (lane == j) own = mj;
     }
-    if (bits && lane < live && lane < kChunk && row0 < N) bits[(size_t)lane * bits_stride] = own;
+    if (bits && lane < live && lane < kChunk && row0 < N) bits[lane] = own;
     const int jr = lane >> 2, part = lane & 3;
     if (jr < live) {
         constexpr int kPer = OP == kOpE4M3 ? 8 : 4;   // spins per 8-byte store
@@ -302,32 +302,30 @@ __device__ __forceinline__ void settle_lane(const LargeArgs &L, int r0, int64_t 
 
 // Best spins of iteration tt, output rows m*128 .. m*128+127, for the replicas r0 + 32 k
 // (k < K) of one lane that improved at tt (flags slot tt & 3), from the packed spins the
-// epilogue wrote (slot tt & 3, rows of Mp / 32 words): flags first, then per improved
-// replica one 16-byte load and its words.
+// epilogue wrote (slot tt & 3, word-major): flags first, then per improved replica its
+// four words (each load coalesced across the warp's consecutive replicas).
 template <int K>
 __device__ __forceinline__ void copy_best_lane(const LargeArgs &L, int r0, int m, int64_t tt) {
     const RunArgs &a = L.a;
     const int8_t *F = L.flags + (size_t)(tt & 3) * L.Rpad;
     const int Wp = L.Mp / 32;
-    const uint32_t *B = L.sbits + (size_t)(tt & 3) * L.Rpad * Wp;
+    const uint32_t *B = L.sbits + (size_t)(tt & 3) * Wp * L.Rpad;
     int8_t f[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) f[k] = r0 + 32 * k < a.R ? F[r0 + 32 * k] : (int8_t)0;
-    uint4 w[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-        w[k] = f[k] ? *reinterpret_cast<const uint4 *>(B + (size_t)(r0 + 32 * k) * Wp + m * 4) : make_uint4(0, 0, 0, 0);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         if (!f[k]) continue;
         const int r = r0 + 32 * k;
-        const uint32_t ws[4] = {w[k].x, w[k].y, w[k].z, w[k].w};
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = B[(size_t)(m * 4 + q) * L.Rpad + r];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int i0 = m * kBM + q * 32;
             if (i0 >= a.N) break;
             const uint32_t valid = a.N - i0 >= 32 ? 0xffffffffu : ((1u << (a.N - i0)) - 1u);
-            a.best_bits[(size_t)r * a.W + (i0 >> 5)] = ws[q] & valid;
+            a.best_bits[(size_t)r * a.W + (i0 >> 5)] = w[q] & valid;
         }
     }
 }
@@ -702,7 +700,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // t - 3 only after its records warp copied t - 3; the improved flags rotate over four
 // slots.  Every wait is bounded; a wait that runs out sets the run's error flag and the
 // CTA winds down.
-template <int OP, int BN>
+template <int OP, int BN, int CL>
 __global__ void __launch_bounds__(kThreads + 64, 1)
     tc_flow_run(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const LargeArgs L) {
@@ -712,6 +710,8 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
     constexpr uint32_t kStageB = Tile<BN, true>::kStageB;
     constexpr int kColsPerWarp = Tile<BN, true>::kColsPerWarp;
     constexpr int kChunksPerTile = Tile<BN, true>::kChunksPerTile;
+    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
+    static_assert(CL == 1 || CL == 2 || CL == 4, "cluster of 1, 2 or 4 CTAs");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = smem;
@@ -724,11 +724,17 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
 
     const RunArgs &a = L.a;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int G = (int)gridDim.x, cid = (int)blockIdx.x;
+    // Cluster tiles: CL consecutive output tiles of one replica tile, CTA `crank` of the
+    // cluster taking the crank-th; the cluster's CTAs load one CL-th of the spin tile each
+    // and multicast it to all of them.
+    const int crank = CL > 1 ? (int)cluster_ctarank() : 0;
+    const int Gc = (int)gridDim.x / CL, cid = (int)blockIdx.x / CL;
     const int mt = L.mtiles;
-    const int my_tiles = cid < L.ntiles ? (L.ntiles - 1 - cid) / G + 1 : 0;
-    auto tile_m = [&](int lt) { return (cid + lt * G) % mt; };
-    auto tile_n = [&](int lt) { return (cid + lt * G) / mt; };
+    const int mgroups = mt / CL;
+    const int ctiles = mgroups * L.rtiles;
+    const int my_tiles = cid < ctiles ? (ctiles - 1 - cid) / Gc + 1 : 0;
+    auto tile_m = [&](int lt) { return ((cid + lt * Gc) % mgroups) * CL + crank; };
+    auto tile_n = [&](int lt) { return (cid + lt * Gc) / mgroups; };
     const int64_t t0 = L.f0, t_end = L.f1, t_call_end = a.t0 + a.nsteps;
     const int64_t total = (t_end - t0) * my_tiles;      // tiles this CTA processes, g = 0 .. total - 1
     const int KB = L.Kbytes / kBKB;
@@ -743,7 +749,7 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
     if (tid == 32) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&sh->full[s], 1);
-            mbar_init(&sh->empty[s], 1);
+            mbar_init(&sh->empty[s], CL);   // freed by the MMAs of every CTA of the cluster
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sh->accf[b], 1);
@@ -759,6 +765,7 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if constexpr (CL > 1) cluster_sync_all();   // every CTA's barriers exist before any multicast
     const uint32_t tmem = sh->tmem_base;
 
     if (warp == 0) {
@@ -786,7 +793,12 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
                     }
                     mbar_arrive_expect_tx(&sh->full[s], kStageA + kStageB);
                     tma_load_2d(sA + s * kStageA, &tmA, &sh->full[s], kb * (kBKB / ESZ), m * kBM);
-                    tma_load_2d(sB + s * kStageB, &tmB, &sh->full[s], kb * (kBKB / ESZ), ybuf);
+                    if constexpr (CL == 1) {
+                        tma_load_2d(sB + s * kStageB, &tmB, &sh->full[s], kb * (kBKB / ESZ), ybuf);
+                    } else {
+                        tma_load_2d_mc(sB + s * kStageB + crank * (BN / CL) * kBKB, &tmB, &sh->full[s],
+                                       kb * (kBKB / ESZ), ybuf + crank * (BN / CL), kMask);
+                    }
                 }
             }
             if (!ok) *tout = 1;
@@ -820,7 +832,8 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
                         if constexpr (OP == kOpE4M3) mma_e4m3(dt, ad + 2 * k, bd + 2 * k, IDESC, (kb | k) != 0);
                         else mma_bf16(dt, ad + 2 * k, bd + 2 * k, IDESC, (kb | k) != 0);
                     }
-                    mma_commit(&sh->empty[s]);
+                    if constexpr (CL == 1) mma_commit(&sh->empty[s]);
+                    else mma_commit_mc(&sh->empty[s], kMask);   // stage s free in every CTA of the cluster
                 }
                 if (ok) mma_commit(&sh->accf[b]);
             }
@@ -877,7 +890,7 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
             const int ncol = max(0, min(kColsPerWarp, R - rc0));
             uint8_t *swarp = L.S + (size_t)((t + 1) & 3) * L.Rpad * L.Kbytes + (size_t)rc0 * L.Kbytes +
                              (size_t)(m * kBM + q4 * 32) * ESZ;
-            uint32_t *bwarp = L.sbits + ((size_t)((t + 1) & 3) * L.Rpad + rc0) * (Mp / 32) + m * 4 + q4;
+            uint32_t *bwarp = L.sbits + ((size_t)((t + 1) & 3) * (Mp / 32) + m * 4 + q4) * L.Rpad + rc0;
             // The spins of t + 1 overwrite those of t - 3: their best copy must be done.
             if (ok && more && t - 3 >= t0) {
                 const uint64_t ts = globaltimer_ns();
@@ -947,7 +960,7 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
                     *reinterpret_cast<float4 *>(L.X + off) = make_float4(xn[0], xn[1], xn[2], xn[3]);
                     *reinterpret_cast<float4 *>(L.X + off + grp_stride) = make_float4(xn[4], xn[5], xn[6], xn[7]);
                     chunk_store_spins<OP>(xn, lane, ncol - col0, swarp + (size_t)col0 * L.Kbytes, L.Kbytes,
-                                          m * kBM + q4 * 32, N, bwarp + (size_t)col0 * (Mp / 32), Mp / 32);
+                                          m * kBM + q4 * 32, N, bwarp + col0);
                 }
                 *reinterpret_cast<float4 *>(L.V + off) = make_float4(vs[0], vs[1], vs[2], vs[3]);
                 *reinterpret_cast<float4 *>(L.V + off + grp_stride) = make_float4(vs[4], vs[5], vs[6], vs[7]);
@@ -995,8 +1008,8 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
     } else if (lane == 0) {
         // Signal warp: once the epilogue warps finished tile g, make their spins and
         // energy terms visible to the GPU and count the tile in ready[n].  The m = 0 tile
-        // of a replica tile publishes iteration t only after its energy sums of t - 1 were
-        // read out (those of t + 1 go to the same slot).
+        // of a replica tile is counted for iteration t only after its energy sums of t - 1
+        // were read out (those of t + 1 go to the same slot).
         for (int64_t g = 0; g < total; ++g) {
             const int b = (int)(g & 1);
             const int lt = (int)(g % my_tiles);
@@ -1028,6 +1041,9 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
     }
     tc_fence_before();
     __syncthreads();
+    // No CTA of a cluster leaves while another may still multicast into it or arrive on
+    // its barriers.
+    if constexpr (CL > 1) cluster_sync_all();
     if (tid == 0 && sh->timed_out) atomicExch(a.err, 1);
     if (warp == 0) {
         tc_fence_after();
@@ -1261,16 +1277,16 @@ __global__ void tc_flow_pack0(const LargeArgs L) {
     const int Wp = L.Mp / 32, W = L.a.W;   // words past W are never read unmasked
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)L.a.R * W) return;
-    const int r = (int)(idx / W), w = (int)(idx - (int64_t)r * W);
+    const int w = (int)(idx / L.a.R), r = (int)(idx - (int64_t)w * L.a.R);
     const int64_t slot = L.a.t0 & 3;
     const uint8_t *row = L.S + ((size_t)slot * L.Rpad + r) * L.Kbytes;
-    L.sbits[((size_t)slot * L.Rpad + r) * Wp + w] = plus_bits32<OP>(row + (size_t)w * 32 * ESZ);
+    L.sbits[((size_t)slot * Wp + w) * L.Rpad + r] = plus_bits32<OP>(row + (size_t)w * 32 * ESZ);
 }
 
 // Variant 7: the whole run in cooperative launches of tc_flow_run (all CTAs resident at
 // once, as CTAs wait on each other's tiles).  Runs whose tile counters could pass 2^31 go
 // out in several launches; every launch settles and copies all of its iterations.
-template <int OP, int BN>
+template <int OP, int BN, int CL>
 cudaError_t run_flow(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, int *launches, int sms) {
     constexpr size_t kSmem = Tile<BN, true>::kSmemBytes;
     constexpr int kFlowThreads = kThreads + 64;
@@ -1294,16 +1310,40 @@ cudaError_t run_flow(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, i
     CUtensorMap tmA, tmB;
     const int esz = OP == kOpE4M3 ? 1 : 2;
     if (!make_map(&tmA, B.Jop, OP, (uint64_t)B.Kbytes / esz, (uint64_t)B.Mpad, (uint64_t)B.Kbytes, kBM) ||
-        !make_map(&tmB, B.S, OP, (uint64_t)B.Kbytes / esz, (uint64_t)4 * B.Rpad, (uint64_t)B.Kbytes, BN))
+        !make_map(&tmB, B.S, OP, (uint64_t)B.Kbytes / esz, (uint64_t)4 * B.Rpad, (uint64_t)B.Kbytes, BN / CL))
         return cudaErrorInvalidValue;
-    auto k = tc_flow_run<OP, BN>;
+    auto k = tc_flow_run<OP, BN, CL>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kFlowThreads, kSmem);
+    // All CTAs (whole clusters) resident at once: the launch is cooperative.
+    cudaLaunchConfig_t cfg{};
+    cfg.blockDim = dim3(kFlowThreads);
+    cfg.dynamicSmemBytes = kSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    at[1].id = cudaLaunchAttributeClusterDimension;
+    at[1].val.clusterDim.x = CL;
+    at[1].val.clusterDim.y = 1;
+    at[1].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = CL > 1 ? 2 : 1;
+    const int ctiles = (L.mtiles / CL) * L.rtiles;
+    int resident = 0;
+    if (CL > 1) {
+        cudaLaunchConfig_t q = cfg;
+        q.gridDim = dim3((unsigned)(CL * std::max(sms / CL, 1)));
+        q.attrs = at + 1;
+        q.numAttrs = 1;
+        e = cudaOccupancyMaxActiveClusters(&resident, reinterpret_cast<const void *>(k), &q);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k, kFlowThreads, kSmem);
+        resident *= std::max(sms, 1);
+    }
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const dim3 grid((unsigned)std::min(L.ntiles, std::max(sms, 1) * per_sm));
+    if (resident < 1) return cudaErrorInvalidConfiguration;
+    cfg.gridDim = dim3((unsigned)(CL * std::min(ctiles, resident)));
     e = cudaMemsetAsync(B.Epart, 0, 2 * (size_t)B.Rpad * sizeof(int64_t), st);
     if (e != cudaSuccess) return e;
     int n = 0;
@@ -1322,7 +1362,13 @@ cudaError_t run_flow(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, i
         e = cudaMemsetAsync(B.ready, 0, 2 * (size_t)L.rtiles * sizeof(uint32_t), st);
         if (e != cudaSuccess) return e;
         void *args[3] = {&tmA, &tmB, &Lc};
-        e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k), grid, dim3(kFlowThreads), args, kSmem, st);
+        e = cudaLaunchKernelExC(&cfg, reinterpret_cast<const void *>(k), args);
+        if (e != cudaSuccess && CL > 1 && t == a.t0) {
+            // a cooperative launch in clusters refused: the whole call without clusters (the
+            // prologue reads only the caller's arrays, so it runs again unchanged)
+            cudaGetLastError();
+            return run_flow<OP, BN, 1>(B, a, st, launches, sms);
+        }
         if (e != cudaSuccess) return e;
         ++n;
     }
@@ -1342,9 +1388,14 @@ cudaError_t run_variant(const LargeBuffers &B, const RunArgs &a, cudaStream_t st
     const int mtiles = B.Mpad / kBM;
     int v = a.large_variant;
     if (v == 0) v = kDefaultLargeVariant;
-    // The overlapped variant needs its tile counters (absent from the allocation-free entry).
-    if (v == 7 && (!B.ready || !B.sbits || a.field_mode)) v = 1;
-    if (v == 7) return run_flow<OP, BN>(B, a, st, launches, sms);
+    // The overlapped variants need their tile counters (absent from the allocation-free
+    // entry); clusters need the output tiles to split evenly among their CTAs.
+    if (v >= 7 && (!B.ready || !B.sbits || a.field_mode)) v = 1;
+    if (v == 9 && mtiles % 4 != 0) v = 8;
+    if (v == 8 && mtiles % 2 != 0) v = 7;
+    if (v == 9) return run_flow<OP, BN, 4>(B, a, st, launches, sms);
+    if (v == 8) return run_flow<OP, BN, 2>(B, a, st, launches, sms);
+    if (v == 7) return run_flow<OP, BN, 1>(B, a, st, launches, sms);
     // A cluster needs the spin tiles to split evenly among its CTAs.
     if (v == 6 && mtiles % 4 != 0) v = 5;
     if (v == 5 && mtiles % 2 != 0) v = 1;
@@ -1365,7 +1416,7 @@ cudaError_t launch_tc_large(const LargeBuffers &B, const RunArgs &a, int op, cud
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    if (a.large_variant < 0 || a.large_variant > 7) return cudaErrorInvalidValue;
+    if (a.large_variant < 0 || a.large_variant > 9) return cudaErrorInvalidValue;
     // 256-replica tiles when they still give every SM one, else 128-replica tiles.
     const bool wide = (int64_t)(B.Mpad / kBM) * ((a.R + 255) / 256) >= sms;
     if (op == kOpE4M3)

@@ -141,9 +141,10 @@ def test_large_run_invariants(gpu_lib):
 
 # ------------------------------------------------------------------ kernel variants
 
-VARIANTS = [1, 2, 3, 4, 5, 6, 7]   # x/v ring in shared memory; x/v in registers; + spin-tile multicast over 2 / 4
-                                   # CTAs (registers: 3, 4; ring: 5, 6); 7: the whole run in one cooperative
-                                   # launch with per-replica-tile counters (field-only calls use 1)
+VARIANTS = [1, 2, 3, 4, 5, 6, 7, 8, 9]   # x/v ring in shared memory; x/v in registers; + spin-tile multicast
+                                         # over 2 / 4 CTAs (registers: 3, 4; ring: 5, 6); 7: the whole run in one
+                                         # cooperative launch with per-replica-tile counters, 8 / 9: the same with
+                                         # the multicast over 2 / 4 CTAs (field-only calls use 1)
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -214,11 +215,14 @@ def test_large_variants_single_step_matches_oracle(gpu_lib, variant):
         assert np.all(np.abs(vg[r] - vo) <= 1e-5 * np.maximum(scale, 1e-3))
 
 
+@pytest.mark.parametrize("variant", [7, 8, 9])
 @pytest.mark.parametrize("N,R,op,T", [(2000, 4096, 1, 120), (1024, 600, 1, 200), (4000, 2048, 1, 60),
                                       (700, 300, 2, 150), (130, 64, 1, 90)])
-def test_overlapped_variant_equals_per_iteration_launches(gpu_lib, N, R, op, T):
-    """Variant 7 (one cooperative launch per run; CTAs keep their tiles and wait on
-    per-replica-tile counters; a records warp settles energies and copies best spins) gives
+def test_overlapped_variant_equals_per_iteration_launches(gpu_lib, variant, N, R, op, T):
+    """Variants 7-9 (one cooperative launch per run; CTAs keep their tiles and wait on
+    per-replica-tile counters; a records warp settles energies and copies best spins; 8 / 9
+    multicast the spin tile over clusters of 2 / 4 CTAs, N = 700 / 130 falling back to
+    smaller clusters) give
     bit for bit the records, hit steps and final x, v of one launch per iteration, with
     refreshes and a target that some replicas reach mid-run; grids of fewer CTAs than SMs
     (N = 1024 / 700 / 130) and CTAs with one or two tiles (N = 2000, 4000) included."""
@@ -227,9 +231,9 @@ def test_overlapped_variant_equals_per_iteration_launches(gpu_lib, N, R, op, T):
     P = o.Instance(d.kh, k=d.k)
     sched0 = phia.schedule(0.01, 0.2, 0.1, 2.0, refresh=25)
     outs = []
-    for variant in (1, 7):
+    for lv in (1, variant):
         with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, operand=op, tc_kernel=phia.KERNEL_PER_STEP,
-                           large_variant=variant) as A:
+                           large_variant=lv) as A:
             if not outs:
                 # a target between the best energies of the replicas: reached by some, mid-run
                 phia.anneal(A.h, sched0, R, T, 9)
@@ -251,15 +255,17 @@ def test_overlapped_variant_equals_per_iteration_launches(gpu_lib, N, R, op, T):
         assert o.energy_exact(P, S[r]) == rec7[0][r]
 
 
-def test_overlapped_variant_resumes_bit_identical(gpu_lib):
-    """A run split into calls (t0 > 0) equals the same run in one call, on variant 7."""
+@pytest.mark.parametrize("variant", [7, 9])
+def test_overlapped_variant_resumes_bit_identical(gpu_lib, variant):
+    """A run split into calls (t0 > 0) equals the same run in one call, on variants 7 and 9."""
     phia = gpu_lib
     N, R, T = 1500, 1024, 90
     d = ins.sk_pm1(N, 4)
     sched = phia.schedule(0.01, 0.2, 0.1, 2.0, refresh=20)
     res = []
     for splits in ((0, T), (0, 33, 61, T)):
-        with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, tc_kernel=phia.KERNEL_PER_STEP, large_variant=7) as A:
+        with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, tc_kernel=phia.KERNEL_PER_STEP,
+                           large_variant=variant) as A:
             x = torch.empty((R, N), device="cuda"); v = torch.empty((R, N), device="cuda")
             phia.init_state(A.h, R, 3, x, v)
             for k in range(len(splits) - 1):

@@ -19,10 +19,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.mark.parametrize("variant", [1, 7])
+@pytest.mark.parametrize("variant", [1, 7, 9])
 def test_expired_waits_report_etimeout_and_the_gpu_stays_usable(gpu_lib, variant):
-    """Variant 1: one launch per iteration; variant 7: one cooperative launch whose tile
-    counters and records waits must give up too."""
+    """Variant 1: one launch per iteration; variants 7 and 9: one cooperative launch (9 in
+    clusters of 4) whose tile counters and records waits must give up too."""
     phia = gpu_lib
     N, R, T = 256, 256, 3
     d = ins.dense_int(N, 7, 7, seed=13)
