@@ -97,9 +97,11 @@ METRIC = "spin-updates/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each kernel, from the
 # committed ncu summaries under profiles/; absent once a kernel changed after its capture.
 KERNEL_TRAFFIC_BYTES = {
-    "tc_large_step": 86_755_328 + 15_568_384,      # N = 2000, 4096 replicas (one iteration)
-    "csr_step": 975_639_296 + 772_641_536,          # 256 ER instances, 256 replicas (one iteration)
-    "tc_small_kernel": 146_432,                     # N = 200, 1024 replicas (a launch is the whole run)
+    "tc_flow_run": (1_360_998_400 + 6_249_299_456) // 100,   # N = 2000, 4096 replicas: a 100-iteration launch,
+                                                             # per iteration (a launch runs all of them)
+    "tc_large_step": None,                                   # not re-captured since its last change
+    "csr_step": 975_512_832 + 774_093_056,                   # 256 ER instances, 256 replicas (one iteration)
+    "tc_small_kernel": 140_544,                              # N = 200, 1024 replicas (a launch is the whole run)
 }
 
 
@@ -347,7 +349,7 @@ def mma_probe(phia):
     return out
 
 
-def _roofline(w, kernel_ms, stats, peaks, src, probe=None):
+def _roofline(w, kernel_ms, stats, peaks, src, probe=None, large_variant=0):
     """Roofline of the dominant kernel of a dense workload.  The field (Eq. 6) is a dense
     contraction of 2 N flops per spin update (2 R N^2 per iteration): achieved = those
     flops / device time, against the e4m3 tensor peak taken as the measured bf16 burst
@@ -362,8 +364,8 @@ def _roofline(w, kernel_ms, stats, peaks, src, probe=None):
     bf16_peak = float(peaks["bf16_tflops"])
     peak = 2.0 * bf16_peak if e4m3 else bf16_peak
     achieved = 2.0 * N * su / (kernel_ms * 1e-3) / 1e12
-    kname = {1: "tc_small_kernel", 2: "tc_large_step", 3: "imma_small_kernel",
-             4: "inc_small_kernel"}.get(stats.tc_kernel, "?")
+    kname = {1: "tc_small_kernel", 2: "tc_flow_run" if large_variant >= 7 else "tc_large_step",
+             3: "imma_small_kernel", 4: "inc_small_kernel"}.get(stats.tc_kernel, "?")
     out = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
            "traffic": KERNEL_TRAFFIC_BYTES.get(kname), "kernel": kname,
            "flops_per_spin_update": 2 * N,
@@ -375,10 +377,13 @@ def _roofline(w, kernel_ms, stats, peaks, src, probe=None):
             out["probe_peak"] = mp
             out["frac_of_probe_peak"] = achieved / mp
     if stats.tc_kernel == 2:
+        # per iteration: one launch of tc_large_step; tc_flow_run runs all T in one launch,
+        # so its per-launch figures are T times these over T times the time
         launch_ms = kernel_ms / T
         bytes_per_launch = R * N * 17 + R * N + N * N
         hbm = bytes_per_launch / (launch_ms * 1e-3) / 1e9
         out["launch_ms"] = launch_ms
+        out["per"] = "iteration"
         out["hbm"] = {"achieved": hbm, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                       "frac": hbm / float(peaks["hbm_gbs"]), "algorithmic_bytes_per_launch": bytes_per_launch,
                       "peak_source": f"{src} HBM copy bandwidth"}
@@ -721,6 +726,13 @@ def run_tts(args, w):
     return 0
 
 
+def _tuned_opts(tune):
+    """Annealer options naming the kernel an autotune result chose."""
+    if tune.tc_kernel == 2:
+        return {"tc_kernel": 2, "large_variant": tune.large_variant}
+    return {"tc_kernel": tune.tc_kernel, "tile_replicas": tune.tile_replicas, "coupling_mem": tune.coupling_mem}
+
+
 def measure_dense(args, w, rank=0, world=1, local=0, with_cpu=True, dist=None):
     """One dense workload on the tensor-core path: the autotuned kernel timed over
     args.steps whole runs (after args.warmup), e2e through the C ABI, the FP32 comparator
@@ -772,12 +784,14 @@ def measure_dense(args, w, rank=0, world=1, local=0, with_cpu=True, dist=None):
     su_step = R * N * T
     value = world * su_step / (ms_per_step * 1e-3)
 
-    # e2e: public C ABI from host buffers, host<->device copies inside the timed region
+    # e2e: public C ABI from host buffers, host<->device copies inside the timed region, on
+    # the kernel the autotuner chose (named explicitly: a new automatic handle would not take
+    # a cooperative variant)
     e2e_ms = []
     for k in range(max(2, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, stream=stream.cuda_stream) as B:
+        with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, stream=stream.cuda_stream, **_tuned_opts(tune)) as B:
             phia.anneal(B.h, sched, R, T, seed)
             e, spins = phia.best(B.h, N)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
@@ -822,7 +836,7 @@ def measure_dense(args, w, rank=0, world=1, local=0, with_cpu=True, dist=None):
                    "parallelism": f"replicas sharded over {world} GPU(s), no collective"},
         "e2e": {"value": su_step / (e2e_step * 1e-3), "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
-        "roofline": _roofline(w, kernel_ms, st, peaks, src, probe),
+        "roofline": _roofline(w, kernel_ms, st, peaks, src, probe, tune.large_variant),
         "gpu_launches": launches,
         "clocks": cs.summary(),
         "comparator": {"path": "fp32 per-instance, one launch per step", "value": cmp_value, "unit": METRIC,
@@ -912,6 +926,10 @@ def main():
                     help="default workload: skip the other workloads reported under 'also'")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warmup + steps anneals of the tensor-core path and nothing else (for ncu)")
+    ap.add_argument("--large-variant", type=int, default=0, help="per-iteration kernel variant (0 = auto)")
+    ap.add_argument("--profile-iters", type=int, default=0, help="profile-only: iterations per run (0 = the workload's)")
+    ap.add_argument("--profile-gahmc", action="store_true",
+                    help="profile-only: vanilla GAHMC (phia_gahmc) on an n = 256 SK instance, 1024 replicas")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -925,12 +943,23 @@ def run_profile(args):
     from paper_2407_10205_gb300 import phia
     phia.load()
     w = WORKLOADS[args.workload]
+    iters = args.profile_iters or w["iterations"]
+    if args.profile_gahmc:
+        from paper_2407_10205_gb300 import instances as ins
+        d = ins.sk_pm1(256, 3)
+        with phia.Annealer(d.k, d.kh, path=phia.PATH_TC) as A:
+            for _ in range(args.warmup + args.steps):
+                phia.gahmc(A.h, phia.gahmc_schedule(0.02, 0.3, math.pi / 2), 1024, args.profile_iters or 200, 1)
+                phia.sync(A.h)
+            st = phia.stats_get(A.h)
+        print(json.dumps({"profile_only": True, "device_ms_last": st.device_ms, "launches_per_run": st.kernel_launches}))
+        return 0
     if w["kind"] == "batch":
         from paper_2407_10205_gb300 import instances as ins
         sched = phia.schedule(w["beta0"], w["beta1"], w["eps"], w["gamma"], refresh=w["refresh"])
-        with phia.Batch(ins.batched_er(w["count"], w["seed"])) as B:
+        with phia.Batch(ins.batched_er(w["count"], w["seed"]), csr_mode=2) as B:   # one launch per iteration
             for _ in range(args.warmup + args.steps):
-                B.anneal(sched, w["replicas"], w["iterations"], w["run_seed"])
+                B.anneal(sched, w["replicas"], iters, w["run_seed"])
                 B.sync()
             st = B.stats()
         print(json.dumps({"profile_only": True, "device_ms_last": st.device_ms, "launches_per_run": st.kernel_launches}))
@@ -938,11 +967,12 @@ def run_profile(args):
     d = _instance(w)
     sched = phia.schedule(w["beta0"], w["beta1"], w["eps"], w["gamma"], refresh=w["refresh"])
     with phia.Annealer(d.k, d.kh, path=phia.PATH_TC, tile_replicas=args.tile_replicas,
-                       coupling_mem=args.coupling_mem, tc_kernel=args.tc_kernel) as A:
+                       coupling_mem=args.coupling_mem, tc_kernel=args.tc_kernel,
+                       large_variant=args.large_variant) as A:
         if args.tile_replicas == 0 and args.tc_kernel == 0:
             phia.autotune(A.h, sched, w["replicas"], probe_iters=min(w["iterations"], 200))   # as bench.py does
         for _ in range(args.warmup + args.steps):
-            phia.anneal(A.h, sched, w["replicas"], w["iterations"], w["run_seed"])
+            phia.anneal(A.h, sched, w["replicas"], iters, w["run_seed"])
             phia.sync(A.h)
         st = phia.stats_get(A.h)
     torch.cuda.synchronize()
