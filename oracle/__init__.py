@@ -8,14 +8,18 @@ The arithmetic lives in ``phia_oracle.c`` (plain C, FP64, int64 energies);
 this module compiles it with gcc, loads it with ctypes and exposes numpy-level
 wrappers.  Passages followed (see the C file for the per-function mapping):
 Eq. 2 (energy), Eq. 6 (field), Eqs. 4, 5, 7, 8 (Hamiltonian and its tanh
-gradient), Eqs. A7-A8 (the position-then-momentum update), Table 3 state 5
-(best-state keeping) and Eq. 9 (time to solution).
+gradient), Eqs. A7-A8 (the position-then-momentum update), Table 3 state 4
+(the optional Metropolis test on H at trajectory ends) and state 5 (best-state
+keeping), Sec. 2.1 / 3.2 (vanilla GAHMC: the exact dynamics by zero crossings)
+and Eq. 9 (time to solution).
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
-(published Philox known-answer vectors, brute force, closed forms, a
-hand-worked 3-spin step, the beta = 0 discrete invariant).  The default
-hyper-parameters (eps, gamma, beta schedule) have no value in the paper and
-are therefore unpinned as *values*; the update they feed is pinned.
+(published Philox known-answer vectors, brute force, closed forms, hand-worked
+3-spin step, 2-spin Metropolis and 2-spin GAHMC cases, the beta = 0 discrete
+invariant and free rotation, exact H conservation of GAHMC).  The default
+hyper-parameters (eps, gamma, beta schedule, GAHMC travel time) have no value in
+the paper and are therefore unpinned as *values*; the updates they feed are
+pinned.
 """
 from __future__ import annotations
 
