@@ -96,9 +96,12 @@ typedef struct phia_opts {
                               all of its spins are written (per-replica-tile counters instead
                               of a launch boundary; a records warp settles the energies); its
                               CTAs wait on each other, so it wants the GPU's SMs to itself;
-                              8 / 9 = as 7 with the spin-operand multicast over clusters of
-                              2 / 4 CTAs; 0 = automatic (the autotuner's choice where it has
-                              one; a choice of 7..9 is kept by the tuned handle only, other
+                              its tile width (256, 224 or 128 replicas) is the one whose
+                              estimated iteration time is least; 8 / 9 = as 7 with 256- or
+                              128-wide tiles and the spin-operand multicast over clusters of
+                              2 / 4 CTAs; 10 / 11 / 12 = as 7 with 256- / 224- / 128-wide
+                              tiles; 0 = automatic (the autotuner's choice where it has one;
+                              a choice of 7..12 is kept by the tuned handle only, other
                               handles take the fastest of 1..6) */
 } phia_opts;
 
@@ -205,7 +208,7 @@ int phia_anneal(phia_t *p, const phia_schedule *sched, int32_t replicas, int64_t
  * kernel with 4, 8 or 16 replicas per CTA and J in shared or tensor memory, the
  * resident int8 mma.sync kernel with 8 or 16 replicas per CTA (N small enough), the
  * resident incremental-field kernel with 4, 8 or 16 replicas per CTA (N small enough),
- * and the per-iteration kernel in its nine variants (phia_opts.large_variant) -- keeps
+ * and the per-iteration kernel in its twelve variants (phia_opts.large_variant) -- keeps
  * the fastest for the handle and caches it,
  * process-wide, for (N, replicas, operand): handles created with all variant options
  * automatic use the cached choice for runs with that replica count.  The probes
@@ -219,7 +222,7 @@ typedef struct phia_tune_result {
     int32_t candidates;        /* variants timed */
     float best_us_per_iter;    /* device time per iteration of the chosen variant */
     float worst_us_per_iter;   /* of the slowest variant */
-    int32_t large_variant;     /* per-iteration kernel: the variant chosen (1..9), 0 otherwise */
+    int32_t large_variant;     /* per-iteration kernel: the variant chosen (1..12), 0 otherwise */
     int32_t reserved;          /* 0 */
 } phia_tune_result;
 

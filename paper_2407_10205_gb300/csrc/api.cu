@@ -203,7 +203,7 @@ int ensure_replicas(phia_t *p, int R) {
     al((void **)&p->d_prop, (size_t)R * 8);
     al((void **)&p->d_acc, (size_t)R * 8);
     if (p->large) {
-        const size_t Rp = (size_t)large_rpad(R);
+        const size_t Rp = (size_t)large_rpad_handle(R);
         al((void **)&p->d_S, 4 * Rp * p->Kbytes);
         al((void **)&p->d_Epart, 2 * Rp * 8);
         al((void **)&p->d_flags, 4 * Rp);
@@ -226,7 +226,7 @@ int ensure_replicas(phia_t *p, int R) {
     p->cap_large = p->large;
     CU(cudaMemsetAsync(p->d_eacc, 0, (size_t)R * 8, p->stream));
     if (p->large) {
-        const size_t Rp = (size_t)large_rpad(R);
+        const size_t Rp = (size_t)large_rpad_handle(R);
         CU(cudaMemsetAsync(p->d_S, 0, 4 * Rp * p->Kbytes, p->stream));   // K and replica padding stay 0
         CU(cudaMemsetAsync(p->d_flags, 0, 4 * Rp, p->stream));
         CU(cudaMemsetAsync(p->d_Epart, 0, 2 * Rp * 8, p->stream));
@@ -292,7 +292,7 @@ struct TuneChoice {
     bool imma;
     bool inc;
     int lvar;        // per-iteration kernel variant (large only)
-    int lvar_alt;    // when lvar is a cooperative variant (7..9): the fastest of 1..6, which
+    int lvar_alt;    // when lvar is a cooperative variant (7..12): the fastest of 1..6, which
                      // other handles with the same key take (they may run concurrently)
 };
 std::mutex g_tune_mu;
@@ -337,7 +337,7 @@ cudaError_t launch_path(phia_t *p, const RunArgs &a, int *launches) {
         LargeBuffers B;
         B.Jop = p->d_Jop; B.S = p->d_S; B.Epart = p->d_Epart; B.flags = p->d_flags; B.ready = p->d_ready;
         B.sbits = p->d_sbits;
-        B.X = p->d_X; B.V = p->d_V; B.Kbytes = p->Kbytes; B.Mpad = p->Mpad; B.Rpad = large_rpad(a.R);
+        B.X = p->d_X; B.V = p->d_V; B.Kbytes = p->Kbytes; B.Mpad = p->Mpad; B.Rpad = large_rpad_handle(a.R);
         B.ctl = p->d_ctl; B.graphs = p->graphs;
         return launch_tc_large(B, a, p->op, p->stream, launches);
     }
@@ -500,7 +500,7 @@ int create_dense(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N,
     }
     if (o.tc_kernel == 3 && N > imma_small_max_n())
         return fail(PHIA_ENOTSUP, "the int8 mma.sync kernel handles N <= %d (N = %d)", imma_small_max_n(), N);
-    if (o.large_variant < 0 || o.large_variant > 9) return fail(PHIA_EINVAL, "large_variant must be 0..9");
+    if (o.large_variant < 0 || o.large_variant > 12) return fail(PHIA_EINVAL, "large_variant must be 0..12");
     int dev_count = 0;
     if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
         return fail(PHIA_ECUDA, "no CUDA device available");
@@ -693,7 +693,7 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
             if (inc_small_tile_replicas(p->N, tile) == tile)
                 cands.push_back(TuneChoice{false, tile, 0, false, true, 0, 0});
     }
-    for (int lv = 1; lv <= 9; ++lv) cands.push_back(TuneChoice{true, 0, 0, false, false, lv, 0});
+    for (int lv = 1; lv <= 12; ++lv) cands.push_back(TuneChoice{true, 0, 0, false, false, lv, 0});
     const bool saved_auto = p->auto_tile;
     p->auto_tile = false;
     float best_ms = 1e30f, worst_ms = 0.f, alt_ms = 1e30f;

@@ -76,13 +76,15 @@ struct LargeShared {
 };
 
 // Tile shape: 128 output spins x BN replicas.  BN = 256 halves the coupling-operand
-// traffic per output against BN = 128; BN = 128 keeps more tiles when replicas are few.
+// traffic per output against BN = 128; BN = 128 keeps more tiles when replicas are few;
+// the overlapped kernel may also take BN = 224 to even out the tiles per CTA.
 // With the two-chunk x/v ring in shared memory the 256-wide tile has room for three
 // operand stages, the 128-wide one for four; with x/v prefetched into registers instead,
 // four and six.
 template <int BN, bool RING>
 struct Tile {
-    static constexpr int kStages = RING ? (BN == 256 ? 3 : 4) : (BN == 256 ? 4 : 6);
+    static constexpr int kStages = RING ? (BN >= 224 ? 3 : 4) : (BN >= 224 ? 4 : 6);
+    static constexpr uint32_t kTmemCols = 2 * BN <= 256 ? 256 : 512;   // two accumulators, a power of 2
     static constexpr uint32_t kStageB = BN * kBKB;
     static constexpr int kColsPerWarp = BN / (kEpiWarps / 4);
     static constexpr int kChunksPerTile = kColsPerWarp / kChunk;
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint64_t kWaitNs = a.wait_ns > 0 ? (uint64_t)a.wait_ns : kWaitTimeoutNs;
 
     if (warp == 0) {
-        tmem_alloc(&sh->tmem_base, 2 * BN);
+        tmem_alloc(&sh->tmem_base, Tile<BN, RING>::kTmemCols);
         tmem_relinquish();
     }
     if (tid == 32) {
@@ -673,7 +675,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * BN);
+        tmem_dealloc(tmem, Tile<BN, RING>::kTmemCols);
     }
 }
 
@@ -743,7 +745,7 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
     uint32_t *ready = L.ready, *settled = L.ready + L.rtiles;
 
     if (warp == 0) {
-        tmem_alloc(&sh->tmem_base, 2 * BN);
+        tmem_alloc(&sh->tmem_base, Tile<BN, true>::kTmemCols);
         tmem_relinquish();
     }
     if (tid == 32) {
@@ -1047,7 +1049,7 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
     if (tid == 0 && sh->timed_out) atomicExch(a.err, 1);
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * BN);
+        tmem_dealloc(tmem, Tile<BN, true>::kTmemCols);
     }
 }
 
@@ -1391,6 +1393,7 @@ cudaError_t run_variant(const LargeBuffers &B, const RunArgs &a, cudaStream_t st
     // The overlapped variants need their tile counters (absent from the allocation-free
     // entry); clusters need the output tiles to split evenly among their CTAs.
     if (v >= 7 && (!B.ready || !B.sbits || a.field_mode)) v = 1;
+    if (v >= 10) v = 7;
     if (v == 9 && mtiles % 4 != 0) v = 8;
     if (v == 8 && mtiles % 2 != 0) v = 7;
     if (v == 9) return run_flow<OP, BN, 4>(B, a, st, launches, sms);
@@ -1416,7 +1419,43 @@ cudaError_t launch_tc_large(const LargeBuffers &B, const RunArgs &a, int op, cud
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    if (a.large_variant < 0 || a.large_variant > 9) return cudaErrorInvalidValue;
+    if (a.large_variant < 0 || a.large_variant > 12) return cudaErrorInvalidValue;
+    // The overlapped kernel's tile width: variants 10 / 11 / 12 fix it at 256 / 224 / 128
+    // replicas; variant 7 takes the width whose estimated iteration time is least.  With
+    // w tiles on the busiest CTA, an epilogue of E = 0.045 us per replica column of a tile
+    // and a TMA + MMA mainloop of M = Kbytes x (128 + BN) / (90 bytes per ns) per tile
+    // (both fitted to timings at N = 1024 / 2000 / 4000), an iteration takes about
+    // max(w E, w M, E + 1.5 us + M): the epilogues or the mainloops of a CTA back to back,
+    // or, with one tile, its own epilogue, the counter round trip and its next mainloop
+    // in series (no other tile to hide them behind).
+    const int lv = a.large_variant;
+    if ((lv == 7 || lv >= 10) && B.ready && B.sbits && !a.field_mode) {
+        const int mt = B.Mpad / kBM;
+        int best_bn = 0;
+        double best_us = 0.0;
+        for (int bn : {256, 224, 128}) {
+            if (lv >= 10 && bn != (lv == 10 ? 256 : lv == 11 ? 224 : 128)) continue;
+            const int rt = (a.R + bn - 1) / bn;
+            if ((int64_t)rt * bn > B.Rpad) continue;
+            const double w = (double)(((int64_t)mt * rt + sms - 1) / sms);
+            const double E = 0.045 * bn;
+            const double M = (double)B.Kbytes * (128 + bn) / 90.0 / 1000.0;
+            const double us = std::max(std::max(w * E, w * M), E + 1.5 + M);
+            if (!best_bn || us < best_us) {
+                best_bn = bn;
+                best_us = us;
+            }
+        }
+        if (!best_bn) best_bn = 256;   // a fixed width the padding cannot hold: the standard one
+        if (op == kOpE4M3) {
+            if (best_bn == 224) return run_flow<kOpE4M3, 224, 1>(B, a, st, launches, sms);
+            if (best_bn == 128) return run_flow<kOpE4M3, 128, 1>(B, a, st, launches, sms);
+            return run_flow<kOpE4M3, 256, 1>(B, a, st, launches, sms);
+        }
+        if (best_bn == 224) return run_flow<kOpBF16, 224, 1>(B, a, st, launches, sms);
+        if (best_bn == 128) return run_flow<kOpBF16, 128, 1>(B, a, st, launches, sms);
+        return run_flow<kOpBF16, 256, 1>(B, a, st, launches, sms);
+    }
     // 256-replica tiles when they still give every SM one, else 128-replica tiles.
     const bool wide = (int64_t)(B.Mpad / kBM) * ((a.R + 255) / 256) >= sms;
     if (op == kOpE4M3)

@@ -151,6 +151,9 @@ inline int large_kbytes(int N, int op) { return ((N * (op == kOpE4M3 ? 1 : 2)) +
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 // Replica padding of the per-iteration dense path (its widest tile is 256 replicas).
 inline int large_rpad(int R) { return round_up(R, 256); }
+// Handles pad by one more 256-replica group, so that the overlapped kernel may cut the
+// replicas into 224-wide tiles (ceil(R / 224) * 224 <= this).
+inline int large_rpad_handle(int R) { return round_up(R, 256) + 256; }
 
 // Sparse batched path: many CSR instances, one launch per iteration over all of them.
 struct CsrInst {
