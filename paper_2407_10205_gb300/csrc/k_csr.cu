@@ -647,8 +647,16 @@ cudaError_t launch_csr(const CsrArgs &Cin, StepGraphCache *graphs, cudaStream_t 
         Cs.x_in = Cs.v_in = nullptr;
         Cs.x_out = Cs.v_out = nullptr;
         void *args[1] = {&Cs};
+        // Staged only with blocks enough for two per SM: a lone instance runs its 64-row
+        // units (4x the blocks; a sparse request of N = 5000 alone took twice as long to
+        // its target staged).
         const size_t ssm = csr_staged_smem(C.max_n);
-        if (C.sblocks && C.nsblocks > 0 && ssm <= kStagedSmemMax) {
+        int dev = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        if (C.sblocks && C.nsblocks > 0 && ssm <= kStagedSmemMax &&
+            (int64_t)C.nsblocks * (C.R / kGroup) >= 2 * (int64_t)sms) {
             e = cudaFuncSetAttribute(csr_step_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
             if (e != cudaSuccess) return e;
             e = launch_steps(graphs, reinterpret_cast<const void *>(csr_step_staged), dim3(C.nsblocks, C.R / kGroup),
