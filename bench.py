@@ -100,7 +100,7 @@ KERNEL_TRAFFIC_BYTES = {
     "tc_flow_run": (2_261_857_024 + 7_118_035_712) // 100,   # N = 2000, 4096 replicas: a 100-iteration launch,
                                                              # per iteration (a launch runs all of them)
     "tc_large_step": None,                                   # not re-captured since its last change
-    "csr_step_staged": 973_985_792 + 765_159_936,            # 256 ER instances, 256 replicas (one iteration)
+    "csr_step": 975_512_832 + 774_093_056,                   # 256 ER instances, 256 replicas (one iteration)
     "tc_small_kernel": 140_544,                              # N = 200, 1024 replicas (a launch is the whole run)
 }
 
@@ -468,9 +468,7 @@ def measure_batch(args, w, light=False):
     peaks, src = _peaks()
     launch_ms = float(st.device_ms) / T
     bytes_launch = float(R * Ns.sum() * (16 + 1.0 / 8) + 5 * nnz.sum() * max(1, R // 256))
-    # one launch per iteration runs the staged kernel (every instance here fits its shared
-    # memory); the persistent form runs the unstaged units
-    csr_kernel = "csr_step_staged" if tune.tc_kernel == 2 else "csr_persistent"
+    csr_kernel = "csr_step" if tune.tc_kernel == 2 else "csr_persistent"
     achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,

@@ -42,13 +42,10 @@ struct phia_batch_s {
     std::vector<int64_t> bits_pub;      // per public instance: offset of its best states
     std::vector<long long> targets;     // per instance, LLONG_MIN = none
     std::vector<CsrBlock> blocks;
-    std::vector<CsrBlock> sblocks;          // 256-row blocks of the staged step kernel
-    int max_n = 0;
     int64_t total_rows = 0, total_nnz = 0;
     int max_words = 0;
     CsrInst *d_inst = nullptr;
     CsrBlock *d_blocks = nullptr;
-    CsrBlock *d_sblocks = nullptr;
     int32_t *d_rowptr = nullptr, *d_col = nullptr, *d_hk = nullptr;
     int8_t *d_val = nullptr;
     long long *d_targets = nullptr;
@@ -359,8 +356,6 @@ int batch_create(phia_batch_s **out, int32_t count, const phia_instance_desc *d,
         hk.insert(hk.end(), x.h_k, x.h_k + n);
         b->inst.push_back(in);
         for (int i0 = 0; i0 < n; i0 += 64) b->blocks.push_back(CsrBlock{(int32_t)(b->inst.size() - 1), i0});
-        for (int i0 = 0; i0 < n; i0 += 256) b->sblocks.push_back(CsrBlock{(int32_t)(b->inst.size() - 1), i0});
-        b->max_n = std::max(b->max_n, n);
         row_base += n;
     }
     b->total_rows = row_base;
@@ -383,7 +378,6 @@ int batch_create(phia_batch_s **out, int32_t count, const phia_instance_desc *d,
     up((void **)&b->d_val, val.data(), val.size());
     up((void **)&b->d_hk, hk.data(), hk.size() * 4);
     up((void **)&b->d_blocks, b->blocks.data(), b->blocks.size() * sizeof(CsrBlock));
-    up((void **)&b->d_sblocks, b->sblocks.data(), b->sblocks.size() * sizeof(CsrBlock));
     up((void **)&b->d_targets, b->targets.data(), b->targets.size() * sizeof(long long));
     up((void **)&b->d_dJ, dj.data(), dj.size());
     if (ok && cudaMalloc((void **)&b->d_inst, sizeof(CsrInst) * std::max<size_t>(b->inst.size(), 1)) != cudaSuccess)
@@ -470,7 +464,6 @@ int batch_run(phia_batch_s *b, const phia_schedule *sched, int32_t R_real, int64
     a.min_hit = b->d_min_hit; a.replica_iters = b->d_iters; a.err = b->d_err;
     C.inst = b->d_inst; C.count = ncsr;
     C.blocks = b->d_blocks; C.nblocks = (int32_t)b->blocks.size();
-    C.sblocks = b->d_sblocks; C.nsblocks = (int32_t)b->sblocks.size(); C.max_n = b->max_n;
     C.row_ptr = b->d_rowptr; C.col = b->d_col; C.val = b->d_val; C.hk = b->d_hk;
     C.X = b->d_X; C.V = b->d_V;
     C.x_in = x_in; C.v_in = v_in; C.x_out = x_out; C.v_out = v_out;
@@ -755,7 +748,7 @@ void phia_batch_destroy(phia_batch_t *b) {
     cudaSetDevice(b->device);
     cudaStreamSynchronize(b->stream);
     free_state(b);
-    cudaFree(b->d_inst); cudaFree(b->d_blocks); cudaFree(b->d_sblocks); cudaFree(b->d_rowptr); cudaFree(b->d_col); cudaFree(b->d_val);
+    cudaFree(b->d_inst); cudaFree(b->d_blocks); cudaFree(b->d_rowptr); cudaFree(b->d_col); cudaFree(b->d_val);
     cudaFree(b->d_hk); cudaFree(b->d_targets); cudaFree(b->d_min_hit); cudaFree(b->d_start_ns); cudaFree(b->d_iters); cudaFree(b->d_err);
     cudaFree(b->d_dJ); cudaFree(b->d_small); cudaFree(b->d_sync);
     cudaFree(b->d_ctl);

@@ -28,9 +28,6 @@ constexpr int kRowsPerBlock = 64;
 constexpr int kWarps = 8;
 constexpr int kRowsPerWarp = kRowsPerBlock / kWarps;
 constexpr int kGroup = 256;          // replicas per block (8 per lane)
-// Shared memory the staged step kernel may take (its largest instance: (max - 8 KB) / 32
-// rows, 6144 spins).
-constexpr size_t kStagedSmemMax = 200 * 1024;
 
 __device__ __forceinline__ void settle_csr(const CsrArgs &C, const CsrInst &in, int b, int r, int64_t tt) {
     const RunArgs &a = C.a;
@@ -206,210 +203,6 @@ __device__ __forceinline__ void csr_unit(const CsrArgs &C, int bi, int g, int64_
                   (unsigned long long)s);
     }
     __syncthreads();   // the shared arrays are free for the next unit
-}
-
-// The staged form of a work unit: 256 rows of one instance x 256 replicas, with the
-// instance's spins of this iteration and replica group (32 bytes per row, N rows) first
-// copied into shared memory, so that the neighbour gathers of the field read shared
-// memory instead of making dependent trips to L2; a warp also copies each row's column
-// indices and couplings (up to 128 at a time) into its own shared buffer with one
-// coalesced load per lane, so a row costs two dependent memory trips (its offsets, then
-// its entries) instead of one per 8 entries.  Each block copies its instance's whole spin
-// slice; with 256-row blocks that is a few percent of the x/v stream.  Same arithmetic and
-// records as csr_unit.
-constexpr int kSRows = 256;
-constexpr int kSRowsPerWarp = kSRows / kWarps;
-constexpr int kSEnt = 128;                      // row entries per warp-buffer fill
-// One 8 KB region serves, in turn, the record step's spin bits, the warps' entry buffers
-// and the energy partials.
-constexpr size_t kSRegion = 8192;
-static_assert((size_t)kSRows * (kGroup / 32) * 4 <= kSRegion && (size_t)kWarps * kGroup * 4 <= kSRegion &&
-                  (size_t)kWarps * kSEnt * 5 <= kSRegion,
-              "staged region too small");
-
-__device__ __forceinline__ void csr_unit_staged(const CsrArgs &C, int bi, int g, int64_t t, int64_t t_first,
-                                                int64_t t_end, uint8_t *region, uint32_t *sspin) {
-    const RunArgs &a = C.a;
-    const CsrBlock blk = C.sblocks[bi];
-    const CsrInst in = C.inst[blk.inst];
-    const int b = blk.inst;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int N = in.N, R = C.R, RW = R / 32;
-
-    // (a) records of iteration t-1 (block 0 of each instance).
-    if (blk.i0 == 0 && t - 1 >= t_first) settle_csr(C, in, b, g * kGroup + tid, t - 1);
-    // (b) best spins of iteration t-2 for the replicas that improved then: this block's
-    //     256 rows of spin bits through shared memory, one thread per replica.
-    if (t - 2 >= t_first) {
-        uint32_t (*sbits)[kGroup / 32] = reinterpret_cast<uint32_t (*)[kGroup / 32]>(region);
-        const int rows = min(kSRows, N - blk.i0);
-        const uint32_t *Sb = spin_buf(C, in, t - 2);
-        // 16-byte asynchronous copies, all in flight at once (rows past N are zero)
-        for (int e = tid; e < kSRows * 2; e += 32 * kWarps) {
-            const int row = e >> 1, half = e & 1;
-            uint4 *d = reinterpret_cast<uint4 *>(&sbits[row][half * 4]);
-            if (row < rows) cp_async_16(d, Sb + (size_t)(blk.i0 + row) * RW + g * 8 + half * 4);
-            else *d = make_uint4(0, 0, 0, 0);
-        }
-        cp_async_commit();
-        cp_async_wait<0>();
-        __syncthreads();
-        const int r = g * kGroup + tid;
-        if (C.flags[(size_t)((t - 2) & 1) * C.total_reps + in.rec_off + r]) {
-            const int W = (N + 31) / 32;
-            uint32_t *dst = C.best_bits + in.bits_off + (size_t)r * W;
-            const int word0 = blk.i0 / 32;
-            for (int k = 0; k < kSRows / 32 && word0 + k < W; ++k) {
-                uint32_t wd = 0;
-#pragma unroll 8
-                for (int row = 0; row < 32; ++row)
-                    wd |= ((sbits[32 * k + row][tid >> 5] >> (tid & 31)) & 1u) << row;
-                dst[word0 + k] = wd;
-            }
-        }
-    }
-
-    // (c) the spins of iteration t, replica group g, rows 0 .. N-1 of the instance.
-    const uint32_t *Scw = spin_buf(C, in, t);
-    for (int e = tid; e < N * 2; e += 32 * kWarps) {
-        const int row = e >> 1, half = e & 1;
-        cp_async_16(reinterpret_cast<uint4 *>(sspin) + e, Scw + (size_t)row * RW + g * 8 + half * 4);
-    }
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();   // spins staged; the record step's use of the region is over
-
-    // (d) field and update, 32 rows per warp, 8 replicas per lane.
-    int32_t *wcol = reinterpret_cast<int32_t *>(region) + warp * kSEnt;
-    int8_t *wval = reinterpret_cast<int8_t *>(region + (size_t)kWarps * kSEnt * 4) + warp * kSEnt;
-    uint32_t *Snext = const_cast<uint32_t *>(spin_buf(C, in, t + 1));
-    const float bgq = beta_at(t, inv_tm1_of(a.T_total), a.beta0, a.beta1) * (a.gamma * in.q);
-    const float eps = a.eps, gamma = a.gamma;
-    const bool more = t + 1 < t_end;
-    const bool refresh_next = more && refresh_at(t + 1, a.refresh);
-    const int r0 = g * kGroup + lane * 8;
-    int32_t epart[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const uint8_t *Sl = reinterpret_cast<const uint8_t *>(sspin) + lane;   // this lane's byte of spin row 0
-    const int32_t *colp = C.col + in.nz_off;
-    const int8_t *valp = C.val + in.nz_off;
-    // Lane l holds the entry range and the field term of the warp's row l.
-    const int irow = blk.i0 + warp * kSRowsPerWarp + lane;
-    int my_beg = 0, my_end = 0, my_hk = 0;
-    if (irow < N) {
-        my_beg = C.row_ptr[in.rp_off + irow];
-        my_end = C.row_ptr[in.rp_off + irow + 1];
-        my_hk = C.hk[in.h_off + irow];
-    }
-    static_assert(kSRowsPerWarp == 32, "one row per lane");
-    for (int q = 0; q < kSRowsPerWarp; ++q) {
-        const int i = blk.i0 + warp * kSRowsPerWarp + q;
-        if (i >= N) break;
-        const size_t xo = in.x_off + (size_t)i * R + r0;
-        const float4 xa = *reinterpret_cast<const float4 *>(C.X + xo);
-        const float4 xb = *reinterpret_cast<const float4 *>(C.X + xo + 4);
-        const float4 va = *reinterpret_cast<const float4 *>(C.V + xo);
-        const float4 vb = *reinterpret_cast<const float4 *>(C.V + xo + 4);
-        const int32_t hk = __shfl_sync(0xffffffffu, my_hk, q);
-        const int p_beg = __shfl_sync(0xffffffffu, my_beg, q), p_end = __shfl_sync(0xffffffffu, my_end, q);
-        int32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        int32_t ksum = 0;
-        for (int p0 = p_beg; p0 < p_end; p0 += kSEnt) {
-            const int cnt = min(kSEnt, p_end - p0);   // a multiple of 8
-            int32_t cc[kSEnt / 32];
-            int8_t vv[kSEnt / 32];
-#pragma unroll
-            for (int u = 0; u < kSEnt / 32; ++u) {
-                const int k = lane + 32 * u;
-                cc[u] = k < cnt ? colp[p0 + k] : 0;
-                vv[u] = k < cnt ? valp[p0 + k] : (int8_t)0;
-            }
-            __syncwarp();   // the previous fill's reads are done
-#pragma unroll
-            for (int u = 0; u < kSEnt / 32; ++u) {
-                wcol[lane + 32 * u] = cc[u];
-                wval[lane + 32 * u] = vv[u];
-            }
-            __syncwarp();
-            for (int p = 0; p < cnt; p += 8) {
-                const int4 c0 = *reinterpret_cast<const int4 *>(wcol + p);
-                const int4 c1 = *reinterpret_cast<const int4 *>(wcol + p + 4);
-                const int2 kk = *reinterpret_cast<const int2 *>(wval + p);
-                const uint32_t s0 = Sl[c0.x * 32], s1 = Sl[c0.y * 32], s2 = Sl[c0.z * 32], s3 = Sl[c0.w * 32];
-                const uint32_t s4 = Sl[c1.x * 32], s5 = Sl[c1.y * 32], s6 = Sl[c1.z * 32], s7 = Sl[c1.w * 32];
-                const uint32_t B0 = __byte_perm(__byte_perm(s0, s1, 0x0040), __byte_perm(s2, s3, 0x0040), 0x5410);
-                const uint32_t B1 = __byte_perm(__byte_perm(s4, s5, 0x0040), __byte_perm(s6, s7, 0x0040), 0x5410);
-                ksum = __dp4a(kk.x, 0x01010101, ksum);
-                ksum = __dp4a(kk.y, 0x01010101, ksum);
-#pragma unroll
-                for (int rr = 0; rr < 8; ++rr) {
-                    acc[rr] = __dp4a((int)((B0 >> rr) & 0x01010101u), kk.x, acc[rr]);
-                    acc[rr] = __dp4a((int)((B1 >> rr) & 0x01010101u), kk.y, acc[rr]);
-                }
-            }
-        }
-        float xs[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
-        float vs[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
-        uint32_t nbyte = 0;
-        float If[8];
-#pragma unroll
-        for (int rr = 0; rr < 8; ++rr) {
-            const int32_t I = 2 * acc[rr] - ksum + hk;                    // Eq. 6, exact
-            epart[rr] += (xs[rr] >= 0.0f ? 1 : -1) * (I + hk);
-            If[rr] = (float)I;
-        }
-        float vn[8];
-        if (a.deriv == 1) {
-#pragma unroll
-            for (int rr = 0; rr < 8; ++rr) vn[rr] = momentum_quad(vs[rr], xs[rr], If[rr], eps, bgq, gamma);
-        } else {
-#pragma unroll
-            for (int rr = 0; rr < 8; ++rr) vn[rr] = momentum_exact(vs[rr], xs[rr], If[rr], eps, bgq, gamma);
-        }
-#pragma unroll
-        for (int rr = 0; rr < 8; ++rr) {
-            float v = vn[rr];
-            float x = xs[rr];
-            if (more) {
-                if (refresh_next) v = draw_v(a.seed, in.inst_id, (uint32_t)(r0 + rr), (uint32_t)i, (uint32_t)(t + 1));
-                x = x + eps * v;
-            }
-            xs[rr] = x;
-            vs[rr] = v;
-            nbyte |= (uint32_t)(x >= 0.0f) << rr;
-        }
-        if (more) {
-            *reinterpret_cast<float4 *>(C.X + xo) = make_float4(xs[0], xs[1], xs[2], xs[3]);
-            *reinterpret_cast<float4 *>(C.X + xo + 4) = make_float4(xs[4], xs[5], xs[6], xs[7]);
-            reinterpret_cast<uint8_t *>(Snext)[(size_t)i * (RW * 4) + g * 32 + lane] = (uint8_t)nbyte;
-        }
-        *reinterpret_cast<float4 *>(C.V + xo) = make_float4(vs[0], vs[1], vs[2], vs[3]);
-        *reinterpret_cast<float4 *>(C.V + xo + 4) = make_float4(vs[4], vs[5], vs[6], vs[7]);
-    }
-    __syncthreads();   // every warp is done with its entry buffer: the region takes the partials
-    int32_t (*part)[kGroup] = reinterpret_cast<int32_t (*)[kGroup]>(region);
-#pragma unroll
-    for (int rr = 0; rr < 8; ++rr) part[warp][lane * 8 + rr] = epart[rr];
-    __syncthreads();
-    {
-        long long s = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += part[w][tid];
-        atomicAdd(reinterpret_cast<unsigned long long *>(C.Esum) + (size_t)(t & 1) * C.total_reps + in.rec_off +
-                      g * kGroup + tid,
-                  (unsigned long long)s);
-    }
-}
-
-// Shared memory of the staged step kernel: the 8 KB region and max_n rows of 32 bytes of
-// spins.
-inline size_t csr_staged_smem(int max_n) { return kSRegion + (size_t)max_n * 32; }
-
-// One launch per iteration of the staged units (blockIdx.x: 256-row block, y: replica group).
-__global__ void __launch_bounds__(32 * kWarps, 2) csr_step_staged(const CsrArgs C) {
-    extern __shared__ __align__(16) uint8_t dsm[];
-    const int64_t t = C.ctl->t, t_first = C.ctl->t_first, t_end = C.ctl->t_end;
-    csr_unit_staged(C, blockIdx.x, blockIdx.y, t, t_first, t_end, dsm, reinterpret_cast<uint32_t *>(dsm + kSRegion));
-    if (threadIdx.x == 0) iter_ctl_finish(C.ctl);
 }
 
 // One launch per iteration: a block per work unit; the iteration comes from C.ctl.
@@ -639,32 +432,15 @@ cudaError_t launch_csr(const CsrArgs &Cin, StepGraphCache *graphs, cudaStream_t 
         ++n;
     } else {
         // The step kernel reads its iteration from C.ctl: every launch is the same, and
-        // the arguments leave out what only the prologue and the export read.  The staged
-        // kernel when the largest instance's spin slice fits in shared memory.
+        // the arguments leave out what only the prologue and the export read.
         CsrArgs Cs = C;
         Cs.a.t0 = 0;
         Cs.a.nsteps = 0;
         Cs.x_in = Cs.v_in = nullptr;
         Cs.x_out = Cs.v_out = nullptr;
         void *args[1] = {&Cs};
-        // Staged only with blocks enough for two per SM: a lone instance runs its 64-row
-        // units (4x the blocks; a sparse request of N = 5000 alone took twice as long to
-        // its target staged).
-        const size_t ssm = csr_staged_smem(C.max_n);
-        int dev = 0, sms = 0;
-        e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        if (C.sblocks && C.nsblocks > 0 && ssm <= kStagedSmemMax &&
-            (int64_t)C.nsblocks * (C.R / kGroup) >= 2 * (int64_t)sms) {
-            e = cudaFuncSetAttribute(csr_step_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
-            if (e != cudaSuccess) return e;
-            e = launch_steps(graphs, reinterpret_cast<const void *>(csr_step_staged), dim3(C.nsblocks, C.R / kGroup),
-                             dim3(32 * kWarps), ssm, args, &Cs, sizeof Cs, C.a.nsteps, st);
-        } else {
-            e = launch_steps(graphs, reinterpret_cast<const void *>(csr_step), grid, dim3(32 * kWarps), 0, args, &Cs,
-                             sizeof Cs, C.a.nsteps, st);
-        }
+        e = launch_steps(graphs, reinterpret_cast<const void *>(csr_step), grid, dim3(32 * kWarps), 0, args, &Cs,
+                         sizeof Cs, C.a.nsteps, st);
         if (e != cudaSuccess) return e;
         n += (int)C.a.nsteps;
     }

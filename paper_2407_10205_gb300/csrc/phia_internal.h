@@ -173,7 +173,7 @@ struct CsrInst {
 };
 struct CsrBlock {
     int32_t inst;
-    int32_t i0;             // first of up to 64 (or 256) rows
+    int32_t i0;             // first of up to 64 rows
 };
 struct CsrArgs {
     RunArgs a;              // run parameters; record pointers indexed by rec_off + r
@@ -200,9 +200,6 @@ struct CsrArgs {
     int32_t persistent;     // 1: every iteration in one cooperative launch (grid barrier per iteration)
     int32_t pad1;
     unsigned *sync;         // 4 words of device memory for that launch's barrier and work counters
-    const CsrBlock *sblocks;    // blocks of up to 256 rows (the staged step kernel)
-    int32_t nsblocks;
-    int32_t max_n;          // largest instance
 };
 cudaError_t launch_csr(const CsrArgs &C, StepGraphCache *graphs, cudaStream_t st, int *launches);
 

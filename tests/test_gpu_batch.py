@@ -88,28 +88,3 @@ def test_batch_autotune_picks_a_mode(gpu_lib):
         be, _, _, _ = B.replica_results(6, 256)
         assert (be < 0).any()
 
-
-def test_staged_and_unstaged_csr_kernels_agree(gpu_lib):
-    """A batch large enough for the staged CSR kernel (256-row blocks gathering from a
-    shared-memory copy of the instance's spins; taken with at least two blocks per SM):
-    one launch per iteration (staged) and the persistent launch (unstaged 64-row units)
-    give bit-identical records, and the energies equal Eq. 2 on the returned spins."""
-    phia = gpu_lib
-    insts = ins.batched_er(160, seed=9, n_lo=500, n_hi=1500)
-    R, T = 512, 60
-    assert sum((c.n + 255) // 256 for c in insts) * (R // 256) >= 2 * 152
-    sched = _sched(phia)
-    outs = []
-    for mode in (2, 1):
-        with phia.Batch(insts, csr_mode=mode) as B:
-            B.anneal(sched, R, T, seed=13)
-            outs.append([B.replica_results(k, R) for k in range(len(insts))])
-    for a, b in zip(outs[0], outs[1]):
-        for u, w in zip(a, b):
-            assert np.array_equal(u, w)
-    for k in range(0, len(insts), 31):
-        c = insts[k]
-        P = o.Instance(c.kh, row_ptr=c.row_ptr, col=c.col, val=c.val, frac_bits=c.frac_bits)
-        S = phia.unpack_bits(outs[0][k][3], c.n)
-        for r in range(0, R, 97):
-            assert o.energy_exact(P, S[r]) == outs[0][k][0][r]
