@@ -81,7 +81,7 @@ WORKLOADS = {
                 gahmc_family="sk_ising", gahmc_sizes=(8, 16, 32, 64, 128, 256), gahmc_trajectories=200,
                 name="TTS99 scaling on the Table 2 families (maxcut_dense, maxcut_d3, sk_bool, sk_ising, "
                      "sk_uniform, nae_3_sat, spin_model), n = 8..1024, 100 instances per n; 256 replicas x "
-                     "1000 max(1, n/128) iterations; optimum: exhaustive for n <= 16, planted for nae_3_sat, "
+                     "1000 max(1, n/128) max(1, n/256) iterations; optimum: exhaustive for n <= 16, planted for nae_3_sat, "
                      "else the best of the run and of 1024 replicas x 4 times as many iterations"),
     # serving stream, Poisson arrivals at 200/s over a pool of seeded instances
     "serving": dict(kind="serving", pool=32, pool_seed=5, requests=400, arrival_seed=11, rate_hz=200.0,
@@ -629,7 +629,8 @@ def run_tts(args, w):
 
     for fam in fams:
         for n in sizes:
-            T = w["iterations"] * max(1, n // 128)
+            # runs lengthen faster than n past 256 spins (n = 1024: 32x the n <= 128 length)
+            T = (args.tts_iters or w["iterations"]) * max(1, n // 128) * max(1, n // 256)
             insts = [ins.family_instance(fam, n, ins.tts_seed(fam, n, k)) for k in range(n_inst)]
             # T1: the short run alone
             d0 = insts[0]
@@ -923,6 +924,7 @@ def main():
     ap.add_argument("--tts-families", default="", help="tts: comma-separated families (default: all seven)")
     ap.add_argument("--tts-instances", type=int, default=0, help="tts: instances per (family, n)")
     ap.add_argument("--tts-jump", type=float, default=0.0, help="tts: schedule heuristic's final jump")
+    ap.add_argument("--tts-iters", type=int, default=0, help="tts: iterations per run at n <= 128 (0 = the workload's)")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload: skip the other workloads reported under 'also'")
     ap.add_argument("--profile-only", action="store_true",
