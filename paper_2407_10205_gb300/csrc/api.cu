@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -456,23 +457,56 @@ int create_dense(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N,
     } else {
         // Symmetry, zero diagonal and max |k| over the upper triangle, in 64 x 64 tiles so
         // that a tile and its mirror both stay in cache (a row-by-column walk misses on
-        // every element of the mirror for large N).
+        // every element of the mirror for large N); bands of tile rows go to the host's
+        // cores for large N, and the first mismatch in the serial order is reported.
         constexpr int kTile = 64;
         for (int i = 0; i < N; ++i)
             if (J_k[(size_t)i * N + i] != 0) return fail(PHIA_EINVAL, "nonzero diagonal J_k[%d][%d]", i, i);
-        for (int bi = 0; bi < N; bi += kTile) {
-            const int ie = std::min(N, bi + kTile);
-            for (int bj = bi; bj < N; bj += kTile) {
-                const int je = std::min(N, bj + kTile);
-                for (int i = bi; i < ie; ++i) {
-                    const int8_t *row = J_k + (size_t)i * N;
-                    for (int j = std::max(bj, i + 1); j < je; ++j) {
-                        const int a = row[j], b = J_k[(size_t)j * N + i];
-                        if (a != b) return fail(PHIA_EINVAL, "J_k is not symmetric at (%d, %d)", i, j);
-                        max_abs = std::max(max_abs, std::abs(a));
+        const int bands = (N + kTile - 1) / kTile;
+        auto scan = [&](int b0, int b1, int &mx, int64_t &bad) {
+            mx = 0;
+            bad = -1;
+            for (int bi = b0 * kTile; bi < std::min(N, b1 * kTile); bi += kTile) {
+                const int ie = std::min(N, bi + kTile);
+                for (int bj = bi; bj < N; bj += kTile) {
+                    const int je = std::min(N, bj + kTile);
+                    for (int i = bi; i < ie; ++i) {
+                        const int8_t *row = J_k + (size_t)i * N;
+                        for (int j = std::max(bj, i + 1); j < je; ++j) {
+                            const int a = row[j], b = J_k[(size_t)j * N + i];
+                            if (a != b) {
+                                bad = (int64_t)i * N + j;
+                                return;
+                            }
+                            mx = std::max(mx, std::abs(a));
+                        }
                     }
                 }
             }
+        };
+        const int nt = N >= 1024 ? std::max(1, std::min<int>(bands, (int)std::thread::hardware_concurrency())) : 1;
+        std::vector<int> mx(nt, 0);
+        std::vector<int64_t> bad(nt, -1);
+        if (nt == 1) {
+            scan(0, bands, mx[0], bad[0]);
+        } else {
+            // the triangle's work shrinks with the band: split it into equal shares of tiles
+            std::vector<int> cut(nt + 1, bands);
+            cut[0] = 0;
+            const int64_t tiles = (int64_t)bands * (bands + 1) / 2;
+            int64_t acc = 0;
+            for (int b = 0, k = 1; b < bands && k < nt; ++b) {
+                acc += bands - b;
+                if (acc * nt >= tiles * k) cut[k++] = b + 1;
+            }
+            std::vector<std::thread> th;
+            for (int k = 0; k < nt; ++k) th.emplace_back(scan, cut[k], cut[k + 1], std::ref(mx[k]), std::ref(bad[k]));
+            for (auto &x : th) x.join();
+        }
+        for (int k = 0; k < nt; ++k) {
+            if (bad[k] >= 0)
+                return fail(PHIA_EINVAL, "J_k is not symmetric at (%d, %d)", (int)(bad[k] / N), (int)(bad[k] % N));
+            max_abs = std::max(max_abs, mx[k]);
         }
     }
     if (o.tile_replicas != 0 && o.tile_replicas != 4 && o.tile_replicas != 8 && o.tile_replicas != 16)

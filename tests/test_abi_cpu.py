@@ -65,6 +65,24 @@ def test_invalid_instances_rejected(lib):
     assert "e4m3" in phia.last_error()
 
 
+def test_large_dense_check_reports_the_first_mismatch(lib):
+    """From N = 1024 the host splits the symmetry check over its cores; the mismatch it
+    reports is still the first in the serial scan (tile rows of 64, then tile columns,
+    then rows and columns), whichever thread finds a mismatch first."""
+    d = ins.dense_int(1500, 7, 7, seed=4)
+    k = d.k.copy()
+    for (i, j) in ((1400, 1450), (700, 900), (65, 1300)):   # tile rows 21, 10 and 1
+        k[i, j] = np.int8(k[j, i] + 1)
+    for _ in range(3):
+        assert _create_rc(lib, k, d.kh)[0] == phia.EINVAL
+        assert phia.last_error() == "J_k is not symmetric at (65, 1300)"
+    k2 = d.k.copy()
+    k2[5, 7] = np.int8(k2[7, 5] - 1)                      # tile row 0, tile column 0
+    k2[3, 1499] = np.int8(k2[1499, 3] + 1)                # tile row 0, a later tile column
+    assert _create_rc(lib, k2, d.kh)[0] == phia.EINVAL
+    assert phia.last_error() == "J_k is not symmetric at (5, 7)"
+
+
 def _batch_rc(lib, insts):
     import ctypes
     descs = (phia.InstanceDesc * len(insts))()
