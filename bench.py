@@ -337,10 +337,11 @@ def _peaks():
 
 
 def mma_probe(phia):
-    """Dense tcgen05 rates measured on this GPU by the library's own probe (phia_mma_peak):
-    M = 128, N = 256 MMAs from shared memory on every SM, e4m3 and bf16."""
+    """Dense rates measured on this GPU by the library's own probe (phia_mma_peak): tcgen05
+    M = 128, N = 256 MMAs from shared memory on every SM, e4m3 and bf16 (TFLOP/s); and the
+    warp-level int8 mma.sync route of the int8 resident kernel (integer TOP/s)."""
     out = {}
-    for name, op in (("e4m3", phia.OP_E4M3), ("bf16", phia.OP_BF16)):
+    for name, op in (("e4m3", phia.OP_E4M3), ("bf16", phia.OP_BF16), ("s8_mma_sync", phia.PEAK_S8_MMA_SYNC)):
         try:
             ms, tf = phia.mma_peak(op, 256, 20000)
             out[name + "_tflops"] = tf

@@ -67,6 +67,7 @@ extern "C" {
 #define PHIA_OP_AUTO 0     /* E4M3 when every |k| <= 16, else BF16 */
 #define PHIA_OP_E4M3 1     /* FP8 e4m3, exact for |k| <= 16 */
 #define PHIA_OP_BF16 2     /* BF16, exact for every int8 k */
+#define PHIA_PEAK_S8_MMA_SYNC 3   /* phia_mma_peak only: warp-level int8 mma.sync (the int8 kernel's route) */
 
 typedef struct phia_opts {
     int32_t path;          /* PHIA_PATH_* */
@@ -490,10 +491,13 @@ void phia_server_destroy(phia_server_t *s);
  * rounds x 4 tcgen05 MMAs of shape M = 128, N = n (16..256, a multiple of 16), K = one
  * 128-byte swizzle row split in four (e4m3: K = 32 per MMA, kind::f8f6f4; bf16: K = 16,
  * kind::f16) from shared memory into one FP32 tensor-memory accumulator.  operand:
- * PHIA_OP_E4M3 or PHIA_OP_BF16.  stream: cudaStream_t or NULL.  Writes the device time
- * of the timed launch (after one warm-up launch; CUDA events) to *ms and the achieved
- * dense rate, 2 * 128 * n * K flops per MMA, to *tflops (host pointers, either may be
- * NULL).  Allocates a 4-byte status word; synchronises the stream. */
+ * PHIA_OP_E4M3 or PHIA_OP_BF16; or PHIA_PEAK_S8_MMA_SYNC: 32 warps per SM, each issuing
+ * rounds x 8 warp-level mma.sync m16n8k32 s8 x s8 -> s32 into eight independent register
+ * accumulators (n is then ignored; 2 * 16 * 8 * 32 integer ops per MMA).  stream:
+ * cudaStream_t or NULL.  Writes the device time of the timed launch (after one warm-up
+ * launch; CUDA events) to *ms and the achieved dense rate (flops or integer ops per
+ * second, x 1e-12) to *tflops (host pointers, either may be NULL).  Allocates a 4-byte
+ * status word; synchronises the stream. */
 int phia_mma_peak(int32_t operand, int32_t n, int64_t rounds, void *stream, float *ms, double *tflops);
 
 /* Testing aid for the error path of bounded device waits (Sec. 2.2 gives the FPGA's

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libphia.so")
 OK, EINVAL, ERANGE, ENOMEM, ETIMEOUT, ECUDA, ESTATE, ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
 PATH_AUTO, PATH_TC, PATH_FP32, PATH_CSR = 0, 1, 2, 3
 OP_AUTO, OP_E4M3, OP_BF16 = 0, 1, 2
+PEAK_S8_MMA_SYNC = 3   # phia_mma_peak only: warp-level int8 mma.sync
 _CODES = {EINVAL: "EINVAL", ERANGE: "ERANGE", ENOMEM: "ENOMEM", ETIMEOUT: "ETIMEOUT",
           ECUDA: "ECUDA", ESTATE: "ESTATE", ENOTSUP: "ENOTSUP"}
 
@@ -334,7 +335,8 @@ def run_noalloc(J_k, h_k, frac_bits, operand, sched: Schedule, replicas, t0, ste
 
 
 def mma_peak(operand, n=256, rounds=20000, stream=None):
-    """(device ms, TFLOP/s) of the tcgen05 throughput probe (phia_mma_peak)."""
+    """(device ms, TFLOP/s or TOP/s) of the throughput probe (phia_mma_peak): tcgen05 with
+    OP_E4M3 / OP_BF16, warp-level int8 mma.sync with PEAK_S8_MMA_SYNC."""
     ms, tf = ctypes.c_float(), ctypes.c_double()
     _check(load().phia_mma_peak(int(operand), int(n), int(rounds), ctypes.c_void_p(int(stream) if stream else None),
                                 ctypes.byref(ms), ctypes.byref(tf)))
