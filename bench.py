@@ -84,7 +84,7 @@ WORKLOADS = {
                      "1000 max(1, n/128) max(1, n/256) iterations; optimum: exhaustive for n <= 16, planted for nae_3_sat, "
                      "else the best of the run and of 1024 replicas x 4 times as many iterations"),
     # serving stream, Poisson arrivals at 200/s over a pool of seeded instances
-    "serving": dict(kind="serving", pool=32, pool_seed=5, requests=400, arrival_seed=11, rate_hz=200.0,
+    "serving": dict(kind="serving", pool=32, pool_seed=5, requests=2000, arrival_seed=11, rate_hz=200.0,
                     replicas=256, step_cap=5000, max_inflight=64, budget_gb=64, chunk_iters=200,
                     cmp_requests=60, cmp_wall_s=90.0,
                     name="serving: Poisson 200/s, N log-uniform [64,8192], half dense {-1,+1}, half sparse "
@@ -626,6 +626,9 @@ def run_tts(args, w):
 
     def schedule_of(d):
         b0, b1, eps, gamma, refresh = schedules.suggest_schedule(d, jump=jump)
+        eps = args.tts_eps or eps
+        gamma = args.tts_gamma or gamma
+        refresh = args.tts_refresh or refresh
         return phia.schedule(b0, b1, eps, gamma, refresh=refresh)
 
     for fam in fams:
@@ -723,7 +726,9 @@ def run_tts(args, w):
             "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "dtype": "fp32",
             "config": {"workload": w["name"], "replicas": R,
                        "jump": jump if jump else "6 max(1, sqrt(n / 128)) (schedules.default_jump)",
-                       "reference": f"best of {Rr} replicas x {w['ref_factor']} times the iterations"},
+                       "reference": f"best of {Rr} replicas x {w['ref_factor']} times the iterations",
+                       "eps": args.tts_eps or "heuristic", "gamma": args.tts_gamma or "heuristic",
+                       "refresh": args.tts_refresh or "heuristic"},
             "table": rows, "gahmc": gam, "wall_s": time.perf_counter() - t_start}
     print(json.dumps(line))
     return 0
@@ -926,6 +931,9 @@ def main():
     ap.add_argument("--tts-instances", type=int, default=0, help="tts: instances per (family, n)")
     ap.add_argument("--tts-jump", type=float, default=0.0, help="tts: schedule heuristic's final jump")
     ap.add_argument("--tts-iters", type=int, default=0, help="tts: iterations per run at n <= 128 (0 = the workload's)")
+    ap.add_argument("--tts-eps", type=float, default=0.0, help="tts: step size eps (0 = the schedule heuristic's)")
+    ap.add_argument("--tts-gamma", type=float, default=0.0, help="tts: gamma of Eq. 7 (0 = the heuristic's)")
+    ap.add_argument("--tts-refresh", type=int, default=0, help="tts: iterations per trajectory (0 = the heuristic's)")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload: skip the other workloads reported under 'also'")
     ap.add_argument("--profile-only", action="store_true",
