@@ -78,11 +78,16 @@ WORKLOADS = {
     # ablation
     "tts": dict(kind="tts", sizes=(8, 16, 32, 64, 128, 256, 512, 1024), instances=100, replicas=256,
                 iterations=1000, ref_replicas=1024, ref_factor=4, streams=8, jump=None,
+                # 3-regular max-cut: fields of at most 3 units; a sweep of eps, gamma, the
+                # trajectory length and the final jump on 12 instances each at n = 256, 512 and
+                # 1024, scored against the best of every setting's longer run, chose these
+                family_schedule={"maxcut_d3": dict(eps=0.3, gamma=1.0, refresh=20, jump=12.0)},
                 gahmc_family="sk_ising", gahmc_sizes=(8, 16, 32, 64, 128, 256), gahmc_trajectories=200,
                 name="TTS99 scaling on the Table 2 families (maxcut_dense, maxcut_d3, sk_bool, sk_ising, "
                      "sk_uniform, nae_3_sat, spin_model), n = 8..1024, 100 instances per n; 256 replicas x "
                      "1000 max(1, n/128) max(1, n/256) iterations; optimum: exhaustive for n <= 16, planted for nae_3_sat, "
-                     "else the best of the run and of 1024 replicas x 4 times as many iterations"),
+                     "else the best of the run and of 1024 replicas x 4 times as many iterations (for maxcut_d3, "
+                     "which runs its own schedule, of such a run under each of its schedule and the heuristic's)"),
     # serving stream, Poisson arrivals at 200/s over a pool of seeded instances
     "serving": dict(kind="serving", pool=32, pool_seed=5, requests=2000, arrival_seed=11, rate_hz=200.0,
                     replicas=256, step_cap=5000, max_inflight=64, budget_gb=64, chunk_iters=200,
@@ -598,6 +603,21 @@ def _tts_optima():
         return json.load(f)["optima"]
 
 
+def tts_schedule_params(w, args, fam, d, own=True):
+    """(beta0, beta1, eps, gamma, refresh) of a run of the time-to-solution study on
+    instance d of family fam.  own: the family's entry of w["family_schedule"] where it
+    has one, else the schedule heuristic; not own: the heuristic alone (the reference's
+    second run for a family with an entry).  A nonzero args.tts_jump sets the final jump
+    of either; nonzero args.tts_eps, tts_gamma and tts_refresh override the own schedule's."""
+    from paper_2407_10205_gb300 import schedules
+    f = w.get("family_schedule", {}).get(fam, {}) if own else {}
+    b0, b1, eps, gamma, refresh = schedules.suggest_schedule(d, jump=args.tts_jump or f.get("jump") or w["jump"])
+    if not own:
+        return b0, b1, eps, gamma, refresh
+    return (b0, b1, args.tts_eps or f.get("eps") or eps, args.tts_gamma or f.get("gamma") or gamma,
+            args.tts_refresh or f.get("refresh") or refresh)
+
+
 def run_tts(args, w):
     """Time to solution (Eq. 9, 99% confidence) against n on the Table 2 families.
     Per instance: P = the fraction of the short run's replicas whose best energy reaches
@@ -624,11 +644,10 @@ def run_tts(args, w):
     rows = []
     optimum_of = {}
 
-    def schedule_of(d):
-        b0, b1, eps, gamma, refresh = schedules.suggest_schedule(d, jump=jump)
-        eps = args.tts_eps or eps
-        gamma = args.tts_gamma or gamma
-        refresh = args.tts_refresh or refresh
+    fam_sched = w.get("family_schedule", {})
+
+    def schedule_of(fam, d, own=True):
+        b0, b1, eps, gamma, refresh = tts_schedule_params(w, args, fam, d, own)
         return phia.schedule(b0, b1, eps, gamma, refresh=refresh)
 
     for fam in fams:
@@ -639,7 +658,7 @@ def run_tts(args, w):
             # T1: the short run alone
             d0 = insts[0]
             with phia.Annealer(d0.k, d0.kh, frac_bits=d0.frac_bits, path=phia.PATH_TC) as A:
-                sch = schedule_of(d0)
+                sch = schedule_of(fam, d0)
                 phia.anneal(A.h, sch, R, T, 1)
                 phia.sync(A.h)
                 phia.anneal(A.h, sch, R, T, 1)
@@ -652,7 +671,7 @@ def run_tts(args, w):
                     d = insts[k]
                     A = phia.Annealer(d.k, d.kh, frac_bits=d.frac_bits, path=phia.PATH_TC,
                                       stream=streams[j].cuda_stream)
-                    sch = schedule_of(d)
+                    sch = schedule_of(fam, d)
                     known = None
                     if n <= 16:
                         known = optima[f"{fam}/{n}"][k]
@@ -664,14 +683,22 @@ def run_tts(args, w):
                 for A, sch, known, k in hs:
                     be, _, _, _ = phia.replica_results(A.h, R, n)
                     res.append(be)
-                for (A, sch, known, k) in hs:
-                    if known is None:
-                        phia.anneal(A.h, sch, Rr, T * w["ref_factor"], 1 + k)
+                # the reference: a longer run under the family's schedule and, for a family
+                # with a schedule of its own, one under the heuristic as well
+                refs = [None] * len(hs)
+                for own in ((True, False) if fam in fam_sched else (True,)):
+                    for (A, sch, known, k) in hs:
+                        if known is None:
+                            rs = sch if own else schedule_of(fam, insts[k], own=False)
+                            phia.anneal(A.h, rs, Rr, T * w["ref_factor"], 1 + k)
+                    for j, (A, sch, known, k) in enumerate(hs):
+                        if known is None:
+                            e = int(phia.best(A.h, n)[0])
+                            refs[j] = e if refs[j] is None else min(refs[j], e)
                 for j, (A, sch, known, k) in enumerate(hs):
                     be = res[j]
                     if known is None:
-                        ref, _ = phia.best(A.h, n)
-                        opt = min(int(ref), int(be.min()))
+                        opt = min(refs[j], int(be.min()))
                         opt_src.add("best found")
                     else:
                         opt = int(known)
@@ -728,7 +755,7 @@ def run_tts(args, w):
                        "jump": jump if jump else "6 max(1, sqrt(n / 128)) (schedules.default_jump)",
                        "reference": f"best of {Rr} replicas x {w['ref_factor']} times the iterations",
                        "eps": args.tts_eps or "heuristic", "gamma": args.tts_gamma or "heuristic",
-                       "refresh": args.tts_refresh or "heuristic"},
+                       "refresh": args.tts_refresh or "heuristic", "family_schedule": w.get("family_schedule", {})},
             "table": rows, "gahmc": gam, "wall_s": time.perf_counter() - t_start}
     print(json.dumps(line))
     return 0

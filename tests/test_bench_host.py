@@ -63,3 +63,28 @@ def test_default_workload_is_the_largest_single_gpu_configuration():
 def test_tts99_matches_the_oracle(t1, p):
     a, b = bench.tts99(t1, p), o.tts(t1, p)
     assert (math.isinf(a) and math.isinf(b)) or a == pytest.approx(b, rel=1e-12)
+
+
+def _tts_args(**kw):
+    import argparse
+    a = dict(tts_jump=0.0, tts_eps=0.0, tts_gamma=0.0, tts_refresh=0)
+    a.update(kw)
+    return argparse.Namespace(**a)
+
+
+def test_tts_family_schedule_and_the_heuristic():
+    from paper_2407_10205_gb300 import instances as ins, schedules
+    w = bench.WORKLOADS["tts"]
+    d3 = ins.family_instance("maxcut_d3", 64, 3)
+    sk = ins.family_instance("sk_ising", 64, 3)
+    own = bench.tts_schedule_params(w, _tts_args(), "maxcut_d3", d3)
+    f = w["family_schedule"]["maxcut_d3"]
+    assert own[2:] == (f["eps"], f["gamma"], f["refresh"])
+    assert own[1] == pytest.approx(f["jump"] / schedules.field_scale(d3)) and own[0] == pytest.approx(own[1] / 20)
+    # the reference's second run: the heuristic alone, default final jump for n = 64
+    assert bench.tts_schedule_params(w, _tts_args(), "maxcut_d3", d3, own=False) == schedules.suggest_schedule(d3)
+    # a family without an entry runs the heuristic
+    assert bench.tts_schedule_params(w, _tts_args(), "sk_ising", sk) == schedules.suggest_schedule(sk)
+    # command-line values win over the family's
+    o = bench.tts_schedule_params(w, _tts_args(tts_eps=0.05, tts_refresh=7, tts_jump=3.0), "maxcut_d3", d3)
+    assert o[2:] == (0.05, f["gamma"], 7) and o[1] == pytest.approx(3.0 / schedules.field_scale(d3))
