@@ -337,6 +337,19 @@ __device__ __forceinline__ void cp_async_4(void *dst, const void *src, bool vali
                  "r"(valid ? 4 : 0)
                  : "memory");
 }
+// An L2 eviction-priority policy covering every access made under it: its lines are
+// evicted after normally cached ones (createpolicy, fraction 1).
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// 16-byte global store (16-byte aligned) under an L2 policy from createpolicy.
+__device__ __forceinline__ void st_global_f4_policy(float *p, float4 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w), "l"(pol)
+                 : "memory");
+}
 // Per-thread asynchronous 16-byte copy global -> shared (both 16-byte aligned), L2 only.
 __device__ __forceinline__ void cp_async_16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");

@@ -110,6 +110,8 @@ struct LargeArgs {
     uint32_t *sbits;    // overlapped variant: [4][Mp/32][Rpad] packed spins by iteration slot,
                         // word-major (a word's replicas are consecutive)
     int64_t f0, f1;     // overlapped variant: this launch's iterations [f0, f1) of the call's
+    int32_t xv_keep;    // overlapped variant: x and v stores ask L2 to keep their lines
+                        // (evict_last), set when the state exceeds half of L2
 };
 
 template <int OP>
@@ -869,6 +871,15 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
             const int grp = (n_ * BN + cg * kColsPerWarp + c_ * kChunk) >> 2;
             return ((size_t)grp * Mp + (m_ * kBM + q4 * 32 + lane)) * 4;
         };
+        // Freshly written x and v are read again next iteration; with a state larger than
+        // half of L2 their lines are kept ahead of the operand streams' (evict_last).  The
+        // cluster variants keep plain stores (their registers are tighter).
+        const bool keep = CL == 1 && L.xv_keep != 0;
+        const uint64_t xvpol = l2_evict_last_policy();
+        auto put4 = [&](float *p, float4 v) {
+            if (keep) st_global_f4_policy(p, v, xvpol);
+            else *reinterpret_cast<float4 *>(p) = v;
+        };
         auto issue = [&](size_t off, int slot_) {
             cp_async_16(rx4 + (2 * slot_) * kEpiThreads, L.X + off);
             cp_async_16(rx4 + (2 * slot_ + 1) * kEpiThreads, L.X + off + grp_stride);
@@ -971,13 +982,13 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
                     float xn[kChunk];
 #pragma unroll
                     for (int j = 0; j < kChunk; ++j) xn[j] = xs[j] + eps * vs[j];
-                    *reinterpret_cast<float4 *>(L.X + off) = make_float4(xn[0], xn[1], xn[2], xn[3]);
-                    *reinterpret_cast<float4 *>(L.X + off + grp_stride) = make_float4(xn[4], xn[5], xn[6], xn[7]);
+                    put4(L.X + off, make_float4(xn[0], xn[1], xn[2], xn[3]));
+                    put4(L.X + off + grp_stride, make_float4(xn[4], xn[5], xn[6], xn[7]));
                     chunk_store_spins<OP>(xn, lane, ncol - col0, swarp + (size_t)col0 * L.Kbytes, L.Kbytes,
                                           m * kBM + q4 * 32, N, sh->masks[ew], bwarp + col0);
                 }
-                *reinterpret_cast<float4 *>(L.V + off) = make_float4(vs[0], vs[1], vs[2], vs[3]);
-                *reinterpret_cast<float4 *>(L.V + off + grp_stride) = make_float4(vs[4], vs[5], vs[6], vs[7]);
+                put4(L.V + off, make_float4(vs[0], vs[1], vs[2], vs[3]));
+                put4(L.V + off + grp_stride, make_float4(vs[4], vs[5], vs[6], vs[7]));
                 if (ld_next) tmem_ld_wait_x8(accn);
             }
             // The tile is done: the signal warp publishes it (its arrival on tiledone carries
@@ -1321,6 +1332,11 @@ cudaError_t run_flow(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, i
     L.Mp = B.Mpad;
     L.ready = B.ready;
     L.sbits = B.sbits;
+    {
+        int dev = 0, l2 = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess)
+            L.xv_keep = (size_t)B.Rpad * (size_t)B.Mpad * 8 * 2 > (size_t)l2 ? 1 : 0;
+    }
     CUtensorMap tmA, tmB;
     const int esz = OP == kOpE4M3 ? 1 : 2;
     if (!make_map(&tmA, B.Jop, OP, (uint64_t)B.Kbytes / esz, (uint64_t)B.Mpad, (uint64_t)B.Kbytes, kBM) ||
