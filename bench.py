@@ -102,7 +102,7 @@ METRIC = "spin-updates/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each kernel, from the
 # committed ncu summaries under profiles/; absent once a kernel changed after its capture.
 KERNEL_TRAFFIC_BYTES = {
-    "tc_flow_run": (2_261_857_024 + 7_118_035_712) // 100,   # N = 2000, 4096 replicas: a 100-iteration launch,
+    "tc_flow_run": (2_078_996_000 + 4_795_566_000) // 100,   # N = 2000, 4096 replicas: a 100-iteration launch,
                                                              # per iteration (a launch runs all of them)
     "tc_large_step": None,                                   # not re-captured since its last change
     "csr_step": 975_512_832 + 774_093_056,                   # 256 ER instances, 256 replicas (one iteration)
