@@ -30,12 +30,14 @@ def _mixed():
             ins.dense_int(33, 7, 7, seed=9, frac_bits=3)]
 
 
-def test_dense_members_equal_the_resident_kernel_alone(gpu_lib):
+@pytest.mark.parametrize("csr_mode", [1, 2])
+def test_dense_members_equal_the_resident_kernel_alone(gpu_lib, csr_mode):
+    """csr_mode 1: the CSR part in one persistent launch; 2: one launch per iteration."""
     phia = gpu_lib
     insts = _mixed()
     ids = [40 + k for k in range(len(insts))]
     sched = _sched(phia)
-    with phia.Batch(insts, instance_ids=ids) as B:
+    with phia.Batch(insts, instance_ids=ids, csr_mode=csr_mode) as B:
         B.anneal(sched, R, T, seed=11)
         mix = [B.replica_results(k, R) for k in range(len(insts))]
         st = B.stats()
