@@ -329,8 +329,9 @@ int phia_philox_draws(uint64_t seed, uint32_t instance_id, uint32_t d, int32_t r
  * reserves the array's 64 MiB when the library's code is first used on it -- in practice
  * at the first call of this entry point on that device, which also looks up the array's
  * device address (cudaGetSymbolAddress) -- and holds it until the process exits.  Make
- * that first call at start-up, before the caller's own pool claims the device's memory.
- * Later calls reserve nothing more.
+ * that first call at start-up, before the caller's own pool claims the device's memory
+ * and before any stream capture begins on that device.  Later calls reserve nothing
+ * more.
  *
  * It runs the tensor-core path with one launch per iteration, exactly as phia_run does
  * on a handle created with tc_kernel = 2, and gives the same results.  All pointers are
