@@ -3,7 +3,7 @@
 Workload (one bench step = one whole PHIA run, i.e. every row of the hot path over one
 batch): the N = 2000 complete graph, J_ij uniform in {-1,+1}, h = 0 (seed 3), 4096
 replicas x 5000 iterations, beta linear 0.005 -> 0.134, eps 0.1, gamma 2, momentum
-refreshed every 50 iterations, run on the kernel the autotuner picks among the twelve
+refreshed every 50 iterations, run on the kernel the autotuner picks among the thirteen
 per-iteration tcgen05 variants (at this size the overlapped kernel, one cooperative launch
 per run).  Metric: spin updates per second = replicas * N * iterations
 / time.

@@ -97,13 +97,14 @@ typedef struct phia_opts {
                               all of its spins are written (per-replica-tile counters instead
                               of a launch boundary; a records warp settles the energies); its
                               CTAs wait on each other, so it wants the GPU's SMs to itself;
-                              its tile width (256, 224 or 128 replicas) is the one whose
+                              its tile width (256, 224, 160 or 128 replicas; 160-wide tiles
+                              with three tensor-memory accumulators) is the one whose
                               estimated iteration time is least; 8 / 9 = as 7 with 256- or
                               128-wide tiles and the spin-operand multicast over clusters of
-                              2 / 4 CTAs; 10 / 11 / 12 = as 7 with 256- / 224- / 128-wide
-                              tiles; 0 = automatic (the autotuner's choice where it has one;
-                              a choice of 7..12 is kept by the tuned handle only, other
-                              handles take the fastest of 1..6) */
+                              2 / 4 CTAs; 10 / 11 / 12 / 13 = as 7 with 256- / 224- / 128- /
+                              160-wide tiles; 0 = automatic (the autotuner's choice where it
+                              has one; a choice of 7..13 is kept by the tuned handle only,
+                              other handles take the fastest of 1..6) */
 } phia_opts;
 
 /* Annealing schedule.  No values are given in the paper; every field is explicit. */
@@ -209,7 +210,7 @@ int phia_anneal(phia_t *p, const phia_schedule *sched, int32_t replicas, int64_t
  * kernel with 4, 8 or 16 replicas per CTA and J in shared or tensor memory, the
  * resident int8 mma.sync kernel with 8 or 16 replicas per CTA (N small enough), the
  * resident incremental-field kernel with 4, 8 or 16 replicas per CTA (N small enough),
- * and the per-iteration kernel in its twelve variants (phia_opts.large_variant) -- keeps
+ * and the per-iteration kernel in its thirteen variants (phia_opts.large_variant) -- keeps
  * the fastest for the handle and caches it,
  * process-wide, for (N, replicas, operand): handles created with all variant options
  * automatic use the cached choice for runs with that replica count.  The probes
@@ -223,7 +224,7 @@ typedef struct phia_tune_result {
     int32_t candidates;        /* variants timed */
     float best_us_per_iter;    /* device time per iteration of the chosen variant */
     float worst_us_per_iter;   /* of the slowest variant */
-    int32_t large_variant;     /* per-iteration kernel: the variant chosen (1..12), 0 otherwise */
+    int32_t large_variant;     /* per-iteration kernel: the variant chosen (1..13), 0 otherwise */
     int32_t reserved;          /* 0 */
 } phia_tune_result;
 

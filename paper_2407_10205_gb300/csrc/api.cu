@@ -293,7 +293,7 @@ struct TuneChoice {
     bool imma;
     bool inc;
     int lvar;        // per-iteration kernel variant (large only)
-    int lvar_alt;    // when lvar is a cooperative variant (7..12): the fastest of 1..6, which
+    int lvar_alt;    // when lvar is a cooperative variant (7..13): the fastest of 1..6, which
                      // other handles with the same key take (they may run concurrently)
 };
 std::mutex g_tune_mu;
@@ -534,7 +534,7 @@ int create_dense(phia_t **out, const int8_t *J_k, const int32_t *h_k, int32_t N,
     }
     if (o.tc_kernel == 3 && N > imma_small_max_n())
         return fail(PHIA_ENOTSUP, "the int8 mma.sync kernel handles N <= %d (N = %d)", imma_small_max_n(), N);
-    if (o.large_variant < 0 || o.large_variant > 12) return fail(PHIA_EINVAL, "large_variant must be 0..12");
+    if (o.large_variant < 0 || o.large_variant > 13) return fail(PHIA_EINVAL, "large_variant must be 0..13");
     int dev_count = 0;
     if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
         return fail(PHIA_ECUDA, "no CUDA device available");
@@ -727,7 +727,7 @@ int phia_autotune(phia_t *p, const phia_schedule *sched, int32_t replicas, int32
             if (inc_small_tile_replicas(p->N, tile) == tile)
                 cands.push_back(TuneChoice{false, tile, 0, false, true, 0, 0});
     }
-    for (int lv = 1; lv <= 12; ++lv) cands.push_back(TuneChoice{true, 0, 0, false, false, lv, 0});
+    for (int lv = 1; lv <= 13; ++lv) cands.push_back(TuneChoice{true, 0, 0, false, false, lv, 0});
     const bool saved_auto = p->auto_tile;
     p->auto_tile = false;
     float best_ms = 1e30f, worst_ms = 0.f, alt_ms = 1e30f;

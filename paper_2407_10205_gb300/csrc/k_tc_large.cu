@@ -37,6 +37,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 
 #include "device_common.cuh"
@@ -73,8 +74,12 @@ struct LargeShared {
     int64_t rec_settled;          // overlapped variant: last iteration the records warp settled
     int64_t rec_copied;           // ... and whose best spins it copied
     uint64_t tiledone[2];         // ... the epilogue warps finished the tile in accumulator b
-    uint32_t masks[kEpiWarps][8];  // per epilogue warp: the sign masks of its current chunk
+    alignas(16) uint32_t masks[kEpiWarps][8];  // per epilogue warp: the sign masks of its current
+                                               // chunk (written as 16-byte vectors)
+    uint64_t accf2, acce2, tiledone2;          // the same three barriers of a third accumulator
+                                               // (overlapped kernel with 160-wide tiles)
 };
+static_assert(offsetof(LargeShared, masks) % 16 == 0, "mask scratch must take 16-byte stores");
 
 // Tile shape: 128 output spins x BN replicas.  BN = 256 halves the coupling-operand
 // traffic per output against BN = 128; BN = 128 keeps more tiles when replicas are few;
@@ -715,7 +720,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // t - 3 only after its records warp copied t - 3; the improved flags rotate over four
 // slots.  Every wait is bounded; a wait that runs out sets the run's error flag and the
 // CTA winds down.
-template <int OP, int BN, int CL>
+template <int OP, int BN, int CL, int NACC>
 __global__ void __launch_bounds__(kThreads + 64, 1)
     tc_flow_run(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const LargeArgs L) {
@@ -727,6 +732,8 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
     constexpr int kChunksPerTile = Tile<BN, true>::kChunksPerTile;
     constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
     static_assert(CL == 1 || CL == 2 || CL == 4, "cluster of 1, 2 or 4 CTAs");
+    static_assert((NACC == 2 || NACC == 3) && NACC * BN <= (int)Tile<BN, true>::kTmemCols,
+                  "accumulators beyond the tensor memory allocated");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = smem;
@@ -756,6 +763,10 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
     const int N = a.N, R = a.R;
     const uint64_t kWaitNs = a.wait_ns > 0 ? (uint64_t)a.wait_ns : kWaitTimeoutNs;
     uint32_t *ready = L.ready, *settled = L.ready + L.rtiles;
+    // Barriers of accumulator b (a third one sits after the first two's).
+    auto accf_of = [&](int b) -> uint64_t * { return NACC > 2 && b == 2 ? &sh->accf2 : &sh->accf[b]; };
+    auto acce_of = [&](int b) -> uint64_t * { return NACC > 2 && b == 2 ? &sh->acce2 : &sh->acce[b]; };
+    auto tiledone_of = [&](int b) -> uint64_t * { return NACC > 2 && b == 2 ? &sh->tiledone2 : &sh->tiledone[b]; };
 
     if (warp == 0) {
         tmem_alloc(&sh->tmem_base, Tile<BN, true>::kTmemCols);
@@ -766,10 +777,10 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
             mbar_init(&sh->full[s], 1);
             mbar_init(&sh->empty[s], CL);   // freed by the MMAs of every CTA of the cluster
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&sh->accf[b], 1);
-            mbar_init(&sh->acce[b], kEpiWarps + 1);   // + the signal warp
-            mbar_init(&sh->tiledone[b], kEpiWarps);
+        for (int b = 0; b < NACC; ++b) {
+            mbar_init(accf_of(b), 1);
+            mbar_init(acce_of(b), kEpiWarps + 1);   // + the signal warp
+            mbar_init(tiledone_of(b), kEpiWarps);
         }
         mbar_init(&sh->drain, 1);
         sh->timed_out = 0;
@@ -826,8 +837,9 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
             int64_t kg = 0;
             bool ok = true;
             for (int64_t g = 0; g < total && ok; ++g) {
-                const int b = (int)(g & 1);
-                if (g >= 2 && (*tout || !mbar_wait_bounded(&sh->acce[b], (uint32_t)((g >> 1) - 1) & 1u, kWaitNs))) {
+                const int b = (int)((uint64_t)g % NACC);
+                if (g >= NACC &&
+                    (*tout || !mbar_wait_bounded(acce_of(b), (uint32_t)(((uint64_t)g / NACC) - 1) & 1u, kWaitNs))) {
                     ok = false;
                     break;
                 }
@@ -850,7 +862,7 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
                     if constexpr (CL == 1) mma_commit(&sh->empty[s]);
                     else mma_commit_mc(&sh->empty[s], kMask);   // stage s free in every CTA of the cluster
                 }
-                if (ok) mma_commit(&sh->accf[b]);
+                if (ok) mma_commit(accf_of(b));
             }
             if (!ok) *tout = 1;
             mma_commit(&sh->drain);
@@ -899,7 +911,7 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
             const int lt = (int)(g % my_tiles);
             const int64_t t = t0 + g / my_tiles;
             const int m = tile_m(lt), n = tile_n(lt);
-            const int b = (int)(g & 1);
+            const int b = (int)((uint64_t)g % NACC);
             const bool has_nxt = g + 1 < total;
             const int lt_nxt = (int)((g + 1) % my_tiles);
             const int m_nxt = tile_m(lt_nxt), n_nxt = tile_n(lt_nxt);
@@ -928,7 +940,7 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
                 }
             }
             ok = __all_sync(0xffffffffu, ok && !*tout &&
-                                             mbar_wait_bounded(&sh->accf[b], (uint32_t)(g >> 1) & 1u, kWaitNs));
+                                             mbar_wait_bounded(accf_of(b), (uint32_t)((uint64_t)g / NACC) & 1u, kWaitNs));
             if (!ok) *tout = 1;
             tc_fence_after();
             const uint32_t tbase = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * BN + cg * kColsPerWarp);
@@ -995,8 +1007,8 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
             // this warp's stores), then the accumulator is released.
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&sh->tiledone[b]);
-            if (lane == 0) mbar_arrive(&sh->acce[b]);
+            if (lane == 0) mbar_arrive(tiledone_of(b));
+            if (lane == 0) mbar_arrive(acce_of(b));
         }
         cp_async_wait<0>();
     } else if (warp == 2 + kEpiWarps) {
@@ -1036,15 +1048,15 @@ __global__ void __launch_bounds__(kThreads + 64, 1)
         // of a replica tile is counted for iteration t only after its energy sums of t - 1
         // were read out (those of t + 1 go to the same slot).
         for (int64_t g = 0; g < total; ++g) {
-            const int b = (int)(g & 1);
+            const int b = (int)((uint64_t)g % NACC);
             const int lt = (int)(g % my_tiles);
             const int64_t t = t0 + g / my_tiles;
             const int m = tile_m(lt), n = tile_n(lt);
-            if (*tout || !mbar_wait_bounded(&sh->tiledone[b], (uint32_t)(g >> 1) & 1u, kWaitNs)) {
+            if (*tout || !mbar_wait_bounded(tiledone_of(b), (uint32_t)((uint64_t)g / NACC) & 1u, kWaitNs)) {
                 *tout = 1;
                 break;
             }
-            mbar_arrive(&sh->acce[b]);
+            mbar_arrive(acce_of(b));
             if (m == 0 && t - 1 >= t0) {
                 const uint64_t ts = globaltimer_ns();
                 bool go = true;
@@ -1311,7 +1323,7 @@ __global__ void tc_flow_pack0(const LargeArgs L) {
 // Variant 7: the whole run in cooperative launches of tc_flow_run (all CTAs resident at
 // once, as CTAs wait on each other's tiles).  Runs whose tile counters could pass 2^31 go
 // out in several launches; every launch settles and copies all of its iterations.
-template <int OP, int BN, int CL>
+template <int OP, int BN, int CL, int NACC = 2>
 cudaError_t run_flow(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, int *launches, int sms) {
     constexpr size_t kSmem = Tile<BN, true>::kSmemBytes;
     constexpr int kFlowThreads = kThreads + 64;
@@ -1342,7 +1354,7 @@ cudaError_t run_flow(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, i
     if (!make_map(&tmA, B.Jop, OP, (uint64_t)B.Kbytes / esz, (uint64_t)B.Mpad, (uint64_t)B.Kbytes, kBM) ||
         !make_map(&tmB, B.S, OP, (uint64_t)B.Kbytes / esz, (uint64_t)4 * B.Rpad, (uint64_t)B.Kbytes, BN / CL))
         return cudaErrorInvalidValue;
-    auto k = tc_flow_run<OP, BN, CL>;
+    auto k = tc_flow_run<OP, BN, CL, NACC>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
     // All CTAs (whole clusters) resident at once: the launch is cooperative.
@@ -1397,7 +1409,7 @@ cudaError_t run_flow(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, i
             // a cooperative launch in clusters refused: the whole call without clusters (the
             // prologue reads only the caller's arrays, so it runs again unchanged)
             cudaGetLastError();
-            return run_flow<OP, BN, 1>(B, a, st, launches, sms);
+            return run_flow<OP, BN, 1, NACC>(B, a, st, launches, sms);
         }
         if (e != cudaSuccess) return e;
         ++n;
@@ -1447,22 +1459,26 @@ cudaError_t launch_tc_large(const LargeBuffers &B, const RunArgs &a, int op, cud
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    if (a.large_variant < 0 || a.large_variant > 12) return cudaErrorInvalidValue;
-    // The overlapped kernel's tile width: variants 10 / 11 / 12 fix it at 256 / 224 / 128
-    // replicas; variant 7 takes the width whose estimated iteration time is least.  With
-    // w tiles on the busiest CTA, an epilogue of E = 0.045 us per replica column of a tile
-    // and a TMA + MMA mainloop of M = Kbytes x (128 + BN) / (90 bytes per ns) per tile
+    if (a.large_variant < 0 || a.large_variant > 13) return cudaErrorInvalidValue;
+    // The overlapped kernel's tile width: variants 10 / 11 / 12 / 13 fix it at 256 / 224 /
+    // 128 / 160 replicas; variant 7 takes the width whose estimated iteration time is least.
+    // With w tiles on the busiest CTA, an epilogue of E = 0.045 us per replica column of a
+    // tile and a TMA + MMA mainloop of M = Kbytes x (128 + BN) / (90 bytes per ns) per tile
     // (both fitted to timings at N = 1024 / 2000 / 4000), an iteration takes about
     // max(w E, w M, E + 1.5 us + M): the epilogues or the mainloops of a CTA back to back,
     // or, with one tile, its own epilogue, the counter round trip and its next mainloop
-    // in series (no other tile to hide them behind).
+    // in series (no other tile to hide them behind).  160-wide tiles leave room in tensor
+    // memory for three accumulators; where the mainloops set the pace they cut the bytes
+    // per tile at the same tiles per CTA (N = 4000, 1200 replicas: 26.2 against 30.8 us
+    // with 224-wide tiles, as the estimate has it).
     const int lv = a.large_variant;
     if ((lv == 7 || lv >= 10) && B.ready && B.sbits && !a.field_mode) {
         const int mt = B.Mpad / kBM;
+        const int want = lv == 10 ? 256 : lv == 11 ? 224 : lv == 12 ? 128 : lv == 13 ? 160 : 0;
         int best_bn = 0;
         double best_us = 0.0;
-        for (int bn : {256, 224, 128}) {
-            if (lv >= 10 && bn != (lv == 10 ? 256 : lv == 11 ? 224 : 128)) continue;
+        for (int bn : {256, 224, 160, 128}) {
+            if (want && bn != want) continue;
             const int rt = (a.R + bn - 1) / bn;
             if ((int64_t)rt * bn > B.Rpad) continue;
             const double w = (double)(((int64_t)mt * rt + sms - 1) / sms);
@@ -1477,10 +1493,12 @@ cudaError_t launch_tc_large(const LargeBuffers &B, const RunArgs &a, int op, cud
         if (!best_bn) best_bn = 256;   // a fixed width the padding cannot hold: the standard one
         if (op == kOpE4M3) {
             if (best_bn == 224) return run_flow<kOpE4M3, 224, 1>(B, a, st, launches, sms);
+            if (best_bn == 160) return run_flow<kOpE4M3, 160, 1, 3>(B, a, st, launches, sms);
             if (best_bn == 128) return run_flow<kOpE4M3, 128, 1>(B, a, st, launches, sms);
             return run_flow<kOpE4M3, 256, 1>(B, a, st, launches, sms);
         }
         if (best_bn == 224) return run_flow<kOpBF16, 224, 1>(B, a, st, launches, sms);
+        if (best_bn == 160) return run_flow<kOpBF16, 160, 1, 3>(B, a, st, launches, sms);
         if (best_bn == 128) return run_flow<kOpBF16, 128, 1>(B, a, st, launches, sms);
         return run_flow<kOpBF16, 256, 1>(B, a, st, launches, sms);
     }

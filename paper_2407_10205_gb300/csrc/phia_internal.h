@@ -61,7 +61,8 @@ struct RunArgs {
     int64_t wait_ns;                     // per-iteration kernel: bound of each device wait (0 = kWaitTimeoutNs)
     int32_t stall_producer;              // per-iteration kernel, testing: the TMA producer issues nothing
     int32_t large_variant;               // per-iteration kernel: 0 auto, 1 x/v ring, 2 x/v in registers,
-                                         // 3 / 4 registers + spin tiles multicast over 2 / 4 CTAs
+                                         // 3 / 4 registers + spin tiles multicast over 2 / 4 CTAs, 5 / 6
+                                         // ring + multicast, 7-13 overlapped (phia_opts.large_variant)
     int32_t accept_test;                 // Table 3 state 4: 1 = Metropolis test on H at trajectory ends
     int64_t *proposed, *accepted;        // [R] per-replica counts of the test (accept_test = 1)
     const SmallCta *small_cta;           // batched small dense runs: one entry per CTA

@@ -141,10 +141,11 @@ def test_large_run_invariants(gpu_lib):
 
 # ------------------------------------------------------------------ kernel variants
 
-VARIANTS = list(range(1, 13))   # x/v ring in shared memory; x/v in registers; + spin-tile multicast over
+VARIANTS = list(range(1, 14))   # x/v ring in shared memory; x/v in registers; + spin-tile multicast over
                                 # 2 / 4 CTAs (registers: 3, 4; ring: 5, 6); 7: the whole run in one cooperative
                                 # launch with per-replica-tile counters, 8 / 9: the same with the multicast over
-                                # 2 / 4 CTAs, 10-12: tile width fixed at 256 / 224 / 128 (field-only calls use 1)
+                                # 2 / 4 CTAs, 10-13: tile width fixed at 256 / 224 / 128 / 160 (160: three
+                                # accumulators; field-only calls use 1)
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -215,18 +216,19 @@ def test_large_variants_single_step_matches_oracle(gpu_lib, variant):
         assert np.all(np.abs(vg[r] - vo) <= 1e-5 * np.maximum(scale, 1e-3))
 
 
-@pytest.mark.parametrize("variant", [7, 8, 9, 10, 11, 12])
+@pytest.mark.parametrize("variant", [7, 8, 9, 10, 11, 12, 13])
 @pytest.mark.parametrize("N,R,op,T", [(2000, 4096, 1, 120), (1024, 600, 1, 200), (4000, 2048, 1, 60),
                                       (4000, 1200, 1, 40), (700, 300, 2, 150), (130, 64, 1, 90)])
 def test_overlapped_variant_equals_per_iteration_launches(gpu_lib, variant, N, R, op, T):
-    """Variants 7-12 (one cooperative launch per run; CTAs keep their tiles and wait on
+    """Variants 7-13 (one cooperative launch per run; CTAs keep their tiles and wait on
     per-replica-tile counters; a records warp settles energies and copies best spins; 8 / 9
     multicast the spin tile over clusters of 2 / 4 CTAs, N = 700 / 130 falling back to
-    smaller clusters; 10 / 11 / 12 fix the tile width at 256 / 224 / 128 replicas) give
+    smaller clusters; 10 / 11 / 12 / 13 fix the tile width at 256 / 224 / 128 / 160
+    replicas, 160 with three tensor-memory accumulators) give
     bit for bit the records, hit steps and final x, v of one launch per iteration, with
     refreshes and a target that some replicas reach mid-run; grids of fewer CTAs than SMs
     (N = 1024 / 700 / 130), CTAs with one or more tiles, and each tile width variant 7
-    picks by its estimate (224 replicas at N = 2000 x 4096 and 4000 x 1200, 256 at
+    picks by its estimate (224 replicas at N = 2000 x 4096, 160 at 4000 x 1200, 256 at
     4000 x 2048, 128 for the others) included."""
     phia = gpu_lib
     d = ins.dense_int(N, 7 if op == 1 else 90, 7, seed=N + 5)
