@@ -14,8 +14,8 @@
 //       buffers (iteration t reads buffer t % 4 and writes t+1 % 4; buffers t-1 and t-2
 //       stay intact for the lagged best-state copies).
 // D = J s accumulates in TMEM (FP32, integer-valued, exact below 2^24): lane = output
-// spin, column = replica; two accumulators, so the MMAs of a CTA's next tile run while
-// the epilogue drains the current one.
+// spin, column = replica; two accumulators (three in the overlapped kernel with 160-wide
+// tiles), so the MMAs of a CTA's next tile run while the epilogue drains the current one.
 // Warp roles: warp 0 issues TMA, warp 1 issues the MMAs (one thread each), warps 2-17 run
 // the epilogue: field + h, s (I + h) energy partials, momentum update (Eqs. 5, 8),
 // refresh, position update and the sign written as next iteration's B operand.
@@ -83,7 +83,8 @@ static_assert(offsetof(LargeShared, masks) % 16 == 0, "mask scratch must take 16
 
 // Tile shape: 128 output spins x BN replicas.  BN = 256 halves the coupling-operand
 // traffic per output against BN = 128; BN = 128 keeps more tiles when replicas are few;
-// the overlapped kernel may also take BN = 224 to even out the tiles per CTA.
+// the overlapped kernel may also take BN = 224 to even out the tiles per CTA, or BN = 160
+// (with three accumulators) to stream fewer operand bytes per tile.
 // With the two-chunk x/v ring in shared memory the 256-wide tile has room for three
 // operand stages, the 128-wide one for four; with x/v prefetched into registers instead,
 // four and six.
@@ -1320,8 +1321,8 @@ __global__ void tc_flow_pack0(const LargeArgs L) {
     L.sbits[((size_t)slot * Wp + w) * L.Rpad + r] = plus_bits32<OP>(row + (size_t)w * 32 * ESZ);
 }
 
-// Variant 7: the whole run in cooperative launches of tc_flow_run (all CTAs resident at
-// once, as CTAs wait on each other's tiles).  Runs whose tile counters could pass 2^31 go
+// Variants 7-13: the whole run in cooperative launches of tc_flow_run (all CTAs resident
+// at once, as CTAs wait on each other's tiles), with NACC TMEM accumulators.  Runs whose tile counters could pass 2^31 go
 // out in several launches; every launch settles and copies all of its iterations.
 template <int OP, int BN, int CL, int NACC = 2>
 cudaError_t run_flow(const LargeBuffers &B, const RunArgs &a, cudaStream_t st, int *launches, int sms) {
